@@ -1,0 +1,260 @@
+/*
+ * gpulsm.h - C ABI of the GB300-native GPU LSM dictionary.
+ *
+ * The data structure is the GPU LSM of Ashkiani, Li, Farach-Colton, Amenta and
+ * Owens ("GPU LSM: A Dynamic Dictionary Data Structure for the GPU", arXiv
+ * 1707.05354): a dictionary of 31-bit keys and 32-bit values, updated in
+ * batches of a fixed size b, stored as sorted levels of b * 2^i elements that
+ * fill and empty like the bits of a binary counter (§III-B).
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ *  - Pointers named d_* are caller-owned DEVICE memory on the handle's device
+ *    (for instance torch.Tensor.data_ptr()); the library never frees or keeps
+ *    them after the call's work has run.  Pointers named h_* are host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is enqueued on it; outputs are valid once the stream has
+ *    reached that point.  Calls that must read a device value on the host
+ *    (documented below) synchronise with the stream before returning.
+ *  - Keys are 32-bit unsigned integers; user keys must be < 2^31 - 1.  The key
+ *    2^31 - 1 is reserved for the placebo tombstones written by cleanup (§IV-E).
+ *    Values are arbitrary 32-bit unsigned integers.
+ *  - Inside the structure a key is stored as the "key variable"
+ *    (key << 1) | status, status 1 = regular element, 0 = tombstone (§IV-A).
+ *  - Errors: a call that returns anything but LSM_OK has changed nothing in
+ *    the dictionary (all or nothing), unless its description says otherwise.
+ *  - A handle is not thread-safe; distinct handles are independent.
+ *  - Batch semantics (§III-A): batches apply in call order; within a batch a
+ *    delete of a key beats every insert of it (rule 6) and among several
+ *    inserts of one key the last in input order wins (the library's reading
+ *    of rule 4, which lets the choice be arbitrary).
+ */
+#ifndef GPULSM_H
+#define GPULSM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lsm_t lsm_t; /* opaque; owned by the library */
+
+typedef enum {
+  LSM_OK = 0,
+  LSM_ERR_ARG = 1,        /* null handle/pointer, b = 0, n > b for update, ... */
+  LSM_ERR_KEY_RANGE = 2,  /* an update key is >= 2^31 - 1                      */
+  LSM_ERR_FULL = 3,       /* the batch would need a level beyond the capacity  */
+  LSM_ERR_OOM = 4,        /* a device or pinned allocation failed              */
+  LSM_ERR_BUDGET = 5,     /* the allocation would exceed the handle's budget   */
+  LSM_ERR_CAPACITY = 6,   /* range output does not fit in the caller's buffer  */
+  LSM_ERR_CUDA = 7,       /* a CUDA runtime call or kernel launch failed       */
+  LSM_ERR_TIMEOUT = 8     /* a bounded device-side wait gave up                */
+} lsm_status;
+
+/* Human-readable name of a status code (static string). */
+const char* lsm_status_str(lsm_status s);
+
+/*
+ * lsm_create - allocate an empty dictionary with batch size b (§III-A rule 1).
+ *   out           receives the handle.
+ *   b             batch size, 1 <= b <= 2^26.
+ *   max_elements  resident elements (counting stale ones and tombstones) to
+ *                 provide room for: the library allocates the smallest number
+ *                 of levels L with b * (2^L - 1) >= max_elements (at least 1),
+ *                 and at most 2^31 elements in all.
+ *   device        CUDA device ordinal; the handle's memory lives there and every
+ *                 later call must run with that device's streams.
+ * Device memory: 8 bytes per element of every level, plus scratch of about
+ * 16 * b bytes for the batch sort.  Levels are laid out in one array, level i
+ * after level i - 1 (§IV-A, Fig. 3), each level's start rounded up to a
+ * multiple of 32 elements.
+ * Errors: LSM_ERR_ARG, LSM_ERR_OOM, LSM_ERR_CUDA.
+ */
+lsm_status lsm_create(lsm_t** out, uint32_t b, uint64_t max_elements, int device);
+
+/* lsm_destroy - release every allocation of the handle (NULL is accepted).
+ * Waits for the handle's outstanding work first. */
+void lsm_destroy(lsm_t* h);
+
+/*
+ * lsm_insert_batch - insert n (key, value) pairs (§III-B, Fig. 2(a), Fig. 3).
+ *   d_keys, d_vals  n keys and n values, device memory, read-only.
+ *   n               any count; the ops are applied as ceil(n / b) consecutive
+ *                   batches of b ops, a final short batch padded with copies of
+ *                   its last op (§IV-A).  n = 0 is a no-op.
+ * Each batch is sorted on the full key variable and cascade-merged into level
+ * ffz(r), r the number of resident batches.  Keys are checked on the device;
+ * the call waits for that check (not for the merge) and returns
+ * LSM_ERR_KEY_RANGE with nothing applied if any key is >= 2^31 - 1.
+ * Errors: LSM_ERR_ARG, LSM_ERR_KEY_RANGE, LSM_ERR_FULL, LSM_ERR_CUDA.
+ */
+lsm_status lsm_insert_batch(lsm_t* h, const uint32_t* d_keys, const uint32_t* d_vals,
+                            uint64_t n, void* stream);
+
+/*
+ * lsm_delete_batch - delete n keys by inserting tombstones (§III-C).
+ * Same batching, padding, checks and errors as lsm_insert_batch; tombstones
+ * carry the value 0.
+ */
+lsm_status lsm_delete_batch(lsm_t* h, const uint32_t* d_keys, uint64_t n, void* stream);
+
+/*
+ * lsm_update_batch - one mixed batch of n <= b inserts and deletes (§III-A
+ * rule 2).  d_is_delete[i] != 0 makes op i a delete (its value is ignored).
+ * n < b is padded with copies of op n - 1.
+ * Errors: LSM_ERR_ARG (n > b), LSM_ERR_KEY_RANGE, LSM_ERR_FULL, LSM_ERR_CUDA.
+ */
+lsm_status lsm_update_batch(lsm_t* h, const uint32_t* d_keys, const uint32_t* d_vals,
+                            const uint8_t* d_is_delete, uint64_t n, void* stream);
+
+/*
+ * lsm_lookup - point queries (§III-D, §IV-B, Fig. 2(b)).
+ *   d_q       nq query keys (any 32-bit value; keys >= 2^31 - 1 are never found).
+ *   d_val     nq outputs: the value, or 0 when not found.
+ *   d_found   nq outputs: 1 when the key is present, else 0.
+ * Full levels are searched from the newest (smallest) to the oldest; the first
+ * element of the key found decides: regular -> found, tombstone -> absent.
+ * nq = 0 is a no-op.  Asynchronous.
+ */
+lsm_status lsm_lookup(lsm_t* h, const uint32_t* d_q, uint64_t nq, uint32_t* d_val,
+                      uint8_t* d_found, void* stream);
+
+/*
+ * lsm_count - number of live keys k with k1[i] <= k <= k2[i] (§III-E, §IV-C,
+ * Fig. 2(c)).  Bounds are inclusive; k1 > k2 gives 0; k2 >= 2^31 - 1 is treated
+ * as 2^31 - 2.  d_count receives nq counts.  Asynchronous.
+ */
+lsm_status lsm_count(lsm_t* h, const uint32_t* d_k1, const uint32_t* d_k2, uint64_t nq,
+                     uint32_t* d_count, void* stream);
+
+/*
+ * lsm_range - every live (key, value) with k1[i] <= key <= k2[i] (§III-E,
+ * §IV-D, Fig. 2(d)), as compressed rows:
+ *   d_offsets  nq + 1 device uint64: query i owns output slots
+ *              [d_offsets[i], d_offsets[i+1]).
+ *   d_keys, d_vals  output keys (original 31-bit keys, ascending within a
+ *              query) and their values; room for `capacity` entries.
+ *   total_out  host pointer receiving the total number of results.
+ * The call synchronises with the stream to learn the total.  If the total
+ * exceeds `capacity`, d_offsets and *total_out are written, nothing else is,
+ * and LSM_ERR_CAPACITY is returned (retry with a larger buffer).
+ */
+lsm_status lsm_range(lsm_t* h, const uint32_t* d_k1, const uint32_t* d_k2, uint64_t nq,
+                     uint64_t* d_offsets, uint32_t* d_keys, uint32_t* d_vals,
+                     uint64_t capacity, uint64_t* total_out, void* stream);
+
+/*
+ * lsm_cleanup - remove every stale element and tombstone and rebuild the
+ * levels (§III-F, §IV-E).  Afterwards r = ceil(n' / b) for n' live keys; the
+ * sorted live pairs fill the set bits of r in ascending level order (smaller
+ * keys in smaller levels) and r * b - n' placebo tombstones of key 2^31 - 1
+ * (value 0) end the largest level.  Query results are unchanged.
+ * Needs a scratch of 8 bytes per resident element, allocated on first use and
+ * kept.  Synchronises with the stream (the host must learn n').
+ * Errors: LSM_ERR_OOM, LSM_ERR_CUDA, LSM_ERR_TIMEOUT.
+ */
+lsm_status lsm_cleanup(lsm_t* h, void* stream);
+
+/*
+ * lsm_stats - host-side state: r = resident batches, resident = r * b
+ * elements, b = batch size, levels = number of allocated levels.  Any output
+ * pointer may be NULL.  Does not touch the device.
+ */
+lsm_status lsm_stats(const lsm_t* h, uint64_t* r, uint64_t* resident, uint32_t* b,
+                     uint32_t* levels);
+
+/*
+ * lsm_level_offset - element offset and size of level i inside the level
+ * array (0 size when the level is not allocated).  For tests and tools.
+ */
+lsm_status lsm_level_offset(const lsm_t* h, uint32_t i, uint64_t* offset, uint64_t* size);
+
+/*
+ * lsm_dump_levels - copy every FULL level to host memory at the same element
+ * offsets it has on the device (see lsm_level_offset); other positions are
+ * left untouched.  h_keys/h_vals need lsm_capacity() elements.  Synchronises.
+ */
+lsm_status lsm_dump_levels(const lsm_t* h, uint32_t* h_keys, uint32_t* h_vals, void* stream);
+
+/*
+ * lsm_reset - drop every element (r = 0).  Host-side only, no device work; the
+ * level memory is reused by later batches.  Waits for nothing.
+ */
+lsm_status lsm_reset(lsm_t* h);
+
+/* Number of elements in the level array (all allocated levels, with padding). */
+uint64_t lsm_capacity(const lsm_t* h);
+
+/*
+ * lsm_sort_pairs - the library's batch sort as a stand-alone call: stable LSD
+ * radix sort of n (key, value) pairs on the full 32-bit key, 8 bits per pass
+ * (§IV-A sorts each batch with a radix sort over the whole key variable).
+ * d_keys_in/d_vals_in are read, d_keys_out/d_vals_out receive the sorted
+ * pairs (they must not overlap the inputs).  Uses the handle's scratch, so
+ * n <= b.  Asynchronous.  Used by tests of the sort in isolation.
+ */
+lsm_status lsm_sort_pairs(lsm_t* h, const uint32_t* d_keys_in, const uint32_t* d_vals_in,
+                          uint32_t* d_keys_out, uint32_t* d_vals_out, uint64_t n,
+                          void* stream);
+
+/*
+ * lsm_set_option / lsm_get_option - tuning knobs (integers):
+ *   LSM_OPT_LOOKUP_MODE  0 = automatic, 1 = one search per query in input
+ *                        order, 2 = sort the queries first (§IV-B "bulk").
+ *   LSM_OPT_DEVICE_ERROR read-only: sticky device error bits seen so far
+ *                        (1 = bad key, 2 = wait timeout); reading clears them.
+ */
+typedef enum {
+  LSM_OPT_LOOKUP_MODE = 1,
+  LSM_OPT_DEVICE_ERROR = 2
+} lsm_option;
+
+lsm_status lsm_set_option(lsm_t* h, lsm_option opt, int64_t value);
+lsm_status lsm_get_option(lsm_t* h, lsm_option opt, int64_t* value);
+
+/*
+ * Kernel profiler (tracing aid).  While enabled, the library brackets each of
+ * its kernel groups with CUDA events on the call's stream and accumulates, per
+ * group, the number of launches, their total device time and the ALGORITHMIC
+ * bytes they had to move (the bytes an ideal implementation reads and writes
+ * in HBM; scratch traffic excluded):
+ *   LSM_PROF_SORT       batch sort (histogram + 4 passes), 16 B per element
+ *   LSM_PROF_PARTITION  fold co-rank search, 0 B (pure overhead)
+ *   LSM_PROF_MERGE      fold merge into level k, 16 * 2^k * b B
+ *   LSM_PROF_LOOKUP     lookup kernels, 9 B per query + 32 B per level probed
+ *                       (upper bound: every level) + 4 B per query found
+ *   LSM_PROF_COUNT      count / range window kernels, 12 B + 64 B per level
+ *   LSM_PROF_EMIT       range output, 8 B per result + 8 B per query
+ *   LSM_PROF_CLEANUP    cleanup merge + distribute, 8 B read per resident
+ *                       element + 8 B written per element of r' * b
+ * lsm_profile(h, 1) enables and zeroes the counters, lsm_profile(h, 0)
+ * disables.  lsm_profile_read synchronises the device and fills `out`
+ * (LSM_PROF_COUNT_ entries).  Profiling adds two event records per group.
+ */
+typedef enum {
+  LSM_PROF_SORT = 0,
+  LSM_PROF_PARTITION = 1,
+  LSM_PROF_MERGE = 2,
+  LSM_PROF_LOOKUP = 3,
+  LSM_PROF_COUNT = 4,
+  LSM_PROF_EMIT = 5,
+  LSM_PROF_CLEANUP = 6,
+  LSM_PROF_COUNT_ = 7
+} lsm_prof_group;
+
+typedef struct {
+  uint64_t launches;
+  double ms;
+  double bytes;
+} lsm_profile_entry;
+
+lsm_status lsm_profile(lsm_t* h, int enable);
+lsm_status lsm_profile_read(lsm_t* h, lsm_profile_entry* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPULSM_H */

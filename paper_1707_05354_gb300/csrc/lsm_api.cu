@@ -1,0 +1,636 @@
+// Host orchestrator and C ABI of the GPU LSM (include/gpulsm.h).
+//
+// The host owns the binary counter r (§III-B): level i is full iff bit i of r
+// is set, and an update batch lands in level ffz(r).  All device work is
+// enqueued on the caller's stream; the host waits only where the interface
+// says so (the key check of an update, the totals of range and cleanup).
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gpulsm.h"
+#include "lsm_kernels.h"
+
+using namespace gpulsm;
+
+struct lsm_t {
+  int device = 0;
+  uint32_t b = 0;
+  uint32_t L = 0;
+  uint64_t r = 0;
+  uint64_t level_off[kMaxLevels + 1] = {};
+  uint64_t capacity = 0;
+  uint32_t* d_keys = nullptr;
+  uint32_t* d_vals = nullptr;
+  uint32_t* d_bk = nullptr;  // sorted batch (b + slack)
+  uint32_t* d_bv = nullptr;
+  uint32_t* d_tk = nullptr;  // sort ping-pong (b + slack)
+  uint32_t* d_tv = nullptr;
+  SortWorkspace sws{};
+  uint32_t* d_part = nullptr;
+  uint64_t part_words = 0;
+  uint32_t* d_misc = nullptr;  // [0] sticky errors [1] key check [2] tile ctr [3] tile ctr
+  uint64_t* d_u64 = nullptr;   // [0] cleanup count
+  uint32_t* h_status = nullptr;
+  uint64_t* h_u64 = nullptr;
+  cudaEvent_t ev = nullptr;
+  // cleanup scratch (allocated on first cleanup)
+  uint32_t* d_ck = nullptr;
+  uint32_t* d_cv = nullptr;
+  uint64_t* d_clb = nullptr;
+  uint64_t clean_cap = 0;
+  // query scratch (grown on demand)
+  unsigned char* d_q = nullptr;
+  size_t q_bytes = 0;
+  // sorted-lookup workspace (grown on demand)
+  SortWorkspace qsws{};
+  uint32_t* d_qctl = nullptr;
+  int lookup_mode = 0;
+  // kernel profiler
+  bool prof = false;
+  struct ProfRec {
+    int group;
+    cudaEvent_t a, b;
+    double bytes;
+  };
+  std::vector<ProfRec> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  lsm_profile_entry prof_acc[LSM_PROF_COUNT_] = {};
+};
+
+namespace {
+
+enum { kMiscSticky = 0, kMiscCheck = 1, kMiscCtrA = 2, kMiscCtrB = 3, kMiscWords = 8 };
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+lsm_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return LSM_OK;
+  cudaGetLastError();  // clear non-sticky errors
+  return e == cudaErrorMemoryAllocation ? LSM_ERR_OOM : LSM_ERR_CUDA;
+}
+
+#define LSM_TRY(expr)                              \
+  do {                                             \
+    lsm_status _s = cuda_status(expr);             \
+    if (_s != LSM_OK) return _s;                   \
+  } while (0)
+
+uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+int ffz(uint64_t r) {
+  int i = 0;
+  while ((r >> i) & 1u) ++i;
+  return i;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, uint64_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (count ? count : 1));
+}
+
+void free_all(lsm_t* h) {
+  void* dptrs[] = {h->d_keys, h->d_vals, h->d_bk, h->d_bv, h->d_tk, h->d_tv, h->sws.ctl, h->sws.lookback,
+                   h->d_part, h->d_misc, h->d_u64, h->d_ck, h->d_cv, h->d_clb, h->d_q, h->qsws.lookback,
+                   h->d_qctl};
+  for (void* p : dptrs)
+    if (p) cudaFree(p);
+  if (h->h_status) cudaFreeHost(h->h_status);
+  if (h->h_u64) cudaFreeHost(h->h_u64);
+  if (h->ev) cudaEventDestroy(h->ev);
+  for (auto& p : h->prof_pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
+}
+
+// Brackets a kernel group with timing events while the profiler is on.
+struct ProfScope {
+  lsm_t* h;
+  int group;
+  double bytes;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  static cudaEvent_t get(lsm_t* h) {
+    if (!h->prof_pool.empty()) {
+      cudaEvent_t e = h->prof_pool.back();
+      h->prof_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  ProfScope(lsm_t* h_, int g, double by, cudaStream_t s) : h(h_), group(g), bytes(by), st(s) {
+    if (h->prof && (a = get(h))) cudaEventRecord(a, st);
+  }
+  ~ProfScope() {
+    if (!h->prof || !a) return;
+    cudaEvent_t b = get(h);
+    if (!b) return;
+    cudaEventRecord(b, st);
+    h->prof_pending.push_back({group, a, b, bytes});
+  }
+};
+
+uint32_t* level_keys(lsm_t* h, int i) { return h->d_keys + h->level_off[i]; }
+uint32_t* level_vals(lsm_t* h, int i) { return h->d_vals + h->level_off[i]; }
+
+LevelSet full_levels(lsm_t* h) {
+  LevelSet ls{};
+  for (uint32_t i = 0; i < h->L; ++i) {
+    if (!((h->r >> i) & 1u)) continue;
+    ls.keys[ls.count] = level_keys(h, i);
+    ls.vals[ls.count] = level_vals(h, i);
+    ls.n[ls.count] = uint32_t(uint64_t(h->b) << i);
+    ++ls.count;
+  }
+  return ls;
+}
+
+cudaError_t ensure_q(lsm_t* h, size_t bytes) {
+  if (bytes <= h->q_bytes) return cudaSuccess;
+  if (h->d_q) {
+    cudaError_t e = cudaFree(h->d_q);
+    h->d_q = nullptr;
+    h->q_bytes = 0;
+    if (e != cudaSuccess) return e;
+  }
+  const size_t want = round_up(bytes + bytes / 4, 1 << 20);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&h->d_q), want);
+  if (e == cudaSuccess) h->q_bytes = want;
+  return e;
+}
+
+// One batch of n_in <= b ops into level ffz(r).  With `checked`, waits for
+// the device key check of this batch and leaves r alone if it failed (the
+// batch only ever wrote the empty level ffz(r) and scratch).
+lsm_status apply_batch(lsm_t* h, int mode, const uint32_t* keys, const uint32_t* vals, const uint8_t* del,
+                       uint64_t n_in, cudaStream_t st, bool checked) {
+  const int k = ffz(h->r);
+  if (k >= int(h->L)) return LSM_ERR_FULL;
+  SortArgs a{};
+  a.mode = mode;
+  a.in_keys = keys;
+  a.in_vals = vals;
+  a.in_del = del;
+  a.n_in = n_in;
+  a.n = h->b;
+  a.out_keys = k == 0 ? level_keys(h, 0) : h->d_bk;
+  a.out_vals = k == 0 ? level_vals(h, 0) : h->d_bv;
+  a.tmp_keys = h->d_tk;
+  a.tmp_vals = h->d_tv;
+  {
+    ProfScope ps(h, LSM_PROF_SORT, 16.0 * h->b, st);
+    LSM_TRY(sort_launch(a, h->sws, st, checked ? h->h_status : nullptr, h->ev));
+  }
+  if (k > 0) {
+    FoldArgs f{};
+    f.src.count = k + 1;
+    f.src.keys[0] = h->d_bk;
+    f.src.vals[0] = h->d_bv;
+    f.src.n[0] = h->b;
+    for (int i = 0; i < k; ++i) {
+      f.src.keys[i + 1] = level_keys(h, i);
+      f.src.vals[i + 1] = level_vals(h, i);
+      f.src.n[i + 1] = uint32_t(uint64_t(h->b) << i);
+    }
+    f.total = uint64_t(h->b) << k;
+    f.out_keys = level_keys(h, k);
+    f.out_vals = level_vals(h, k);
+    f.part = h->d_part;
+    f.status = h->d_misc + kMiscSticky;
+    f.cleanup = false;
+    {
+      ProfScope ps(h, LSM_PROF_PARTITION, 0.0, st);
+      LSM_TRY(fold_partition_launch(f, st));
+    }
+    ProfScope ps(h, LSM_PROF_MERGE, 16.0 * double(f.total), st);
+    LSM_TRY(fold_merge_launch(f, st));
+  }
+  if (checked) {
+    LSM_TRY(cudaEventSynchronize(h->ev));
+    if (*h->h_status & kErrBadKey) return LSM_ERR_KEY_RANGE;
+  }
+  h->r += 1;
+  return LSM_OK;
+}
+
+// insert / delete: ceil(n / b) batches.  One batch: the check is fused into
+// the sort.  Several: all keys are checked first so that the call stays all
+// or nothing.
+lsm_status apply_call(lsm_t* h, int mode, const uint32_t* keys, const uint32_t* vals, uint64_t n,
+                      cudaStream_t st) {
+  if (!h || (n && !keys) || (n && mode == kSortInsert && !vals)) return LSM_ERR_ARG;
+  if (n == 0) return LSM_OK;
+  DeviceGuard g(h->device);
+  const uint64_t nb = (n + h->b - 1) / h->b;
+  const uint64_t limit = (h->L >= 64) ? ~0ull : ((1ull << h->L) - 1);
+  if (h->r + nb > limit) return LSM_ERR_FULL;
+  if (nb == 1) return apply_batch(h, mode, keys, vals, nullptr, n, st, true);
+  LSM_TRY(cudaMemsetAsync(h->d_misc + kMiscCheck, 0, sizeof(uint32_t), st));
+  LSM_TRY(check_keys_launch(keys, n, h->d_misc + kMiscCheck, st));
+  LSM_TRY(cudaMemcpyAsync(h->h_status, h->d_misc + kMiscCheck, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  LSM_TRY(cudaStreamSynchronize(st));
+  if (*h->h_status & kErrBadKey) return LSM_ERR_KEY_RANGE;
+  for (uint64_t c = 0; c < nb; ++c) {
+    const uint64_t off = c * h->b;
+    const uint64_t m = (n - off) < h->b ? (n - off) : h->b;
+    lsm_status s = apply_batch(h, mode, keys + off, vals ? vals + off : nullptr, nullptr, m, st, false);
+    if (s != LSM_OK) return s;
+  }
+  return LSM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lsm_status_str(lsm_status s) {
+  switch (s) {
+    case LSM_OK: return "LSM_OK";
+    case LSM_ERR_ARG: return "LSM_ERR_ARG";
+    case LSM_ERR_KEY_RANGE: return "LSM_ERR_KEY_RANGE";
+    case LSM_ERR_FULL: return "LSM_ERR_FULL";
+    case LSM_ERR_OOM: return "LSM_ERR_OOM";
+    case LSM_ERR_BUDGET: return "LSM_ERR_BUDGET";
+    case LSM_ERR_CAPACITY: return "LSM_ERR_CAPACITY";
+    case LSM_ERR_CUDA: return "LSM_ERR_CUDA";
+    case LSM_ERR_TIMEOUT: return "LSM_ERR_TIMEOUT";
+  }
+  return "LSM_ERR_UNKNOWN";
+}
+
+lsm_status lsm_create(lsm_t** out, uint32_t b, uint64_t max_elements, int device) {
+  if (!out || b == 0 || b > (1u << 26)) return LSM_ERR_ARG;
+  *out = nullptr;
+  uint32_t L = 1;
+  while (L < uint32_t(kMaxLevels) && (uint64_t(b) * ((1ull << L) - 1)) < max_elements) ++L;
+  if (uint64_t(b) * ((1ull << L) - 1) < max_elements) return LSM_ERR_ARG;
+  uint64_t off[kMaxLevels + 1] = {};
+  for (uint32_t i = 0; i < L; ++i) off[i + 1] = off[i] + round_up(uint64_t(b) << i, kLevelAlign);
+  if (off[L] > (1ull << 31)) return LSM_ERR_ARG;
+
+  DeviceGuard g(device);
+  lsm_t* h = new (std::nothrow) lsm_t();
+  if (!h) return LSM_ERR_OOM;
+  h->device = device;
+  h->b = b;
+  h->L = L;
+  memcpy(h->level_off, off, sizeof(off));
+  h->capacity = off[L];
+  const uint64_t bpad = round_up(b, kLevelAlign) + kSlack;
+  const uint32_t sort_tiles = (b + kSortTile - 1) / kSortTile;
+  h->part_words = (fold_tiles(h->capacity) + 2) * (L + 1);
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = dalloc(&h->d_keys, h->capacity + kSlack);
+  if (e == cudaSuccess) e = dalloc(&h->d_vals, h->capacity + kSlack);
+  if (e == cudaSuccess) e = dalloc(&h->d_bk, bpad);
+  if (e == cudaSuccess) e = dalloc(&h->d_bv, bpad);
+  if (e == cudaSuccess) e = dalloc(&h->d_tk, bpad);
+  if (e == cudaSuccess) e = dalloc(&h->d_tv, bpad);
+  if (e == cudaSuccess) e = dalloc(&h->sws.ctl, kSortCtlWords);
+  if (e == cudaSuccess) e = dalloc(&h->sws.lookback, uint64_t(kSortPasses) * sort_tiles * 256);
+  if (e == cudaSuccess) e = dalloc(&h->d_part, h->part_words);
+  if (e == cudaSuccess) e = dalloc(&h->d_misc, kMiscWords);
+  if (e == cudaSuccess) e = dalloc(&h->d_u64, 8);
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&h->h_status), 64, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&h->h_u64), 64, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMemset(h->d_keys, 0, sizeof(uint32_t) * (h->capacity + kSlack));
+  if (e == cudaSuccess) e = cudaMemset(h->d_vals, 0, sizeof(uint32_t) * (h->capacity + kSlack));
+  if (e == cudaSuccess) e = cudaMemset(h->d_bk, 0, sizeof(uint32_t) * bpad);
+  if (e == cudaSuccess) e = cudaMemset(h->d_bv, 0, sizeof(uint32_t) * bpad);
+  if (e == cudaSuccess)
+    e = cudaMemset(h->sws.lookback, 0, sizeof(uint64_t) * kSortPasses * uint64_t(sort_tiles) * 256);
+  if (e == cudaSuccess) e = cudaMemset(h->d_misc, 0, sizeof(uint32_t) * kMiscWords);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return cuda_status(e);
+  }
+  h->sws.max_tiles = sort_tiles;
+  h->sws.epoch = 0;
+  h->sws.sticky = h->d_misc + kMiscSticky;
+  *out = h;
+  return LSM_OK;
+}
+
+void lsm_destroy(lsm_t* h) {
+  if (!h) return;
+  DeviceGuard g(h->device);
+  cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+}
+
+lsm_status lsm_insert_batch(lsm_t* h, const uint32_t* d_keys, const uint32_t* d_vals, uint64_t n,
+                            void* stream) {
+  return apply_call(h, kSortInsert, d_keys, d_vals, n, static_cast<cudaStream_t>(stream));
+}
+
+lsm_status lsm_delete_batch(lsm_t* h, const uint32_t* d_keys, uint64_t n, void* stream) {
+  return apply_call(h, kSortDelete, d_keys, nullptr, n, static_cast<cudaStream_t>(stream));
+}
+
+lsm_status lsm_update_batch(lsm_t* h, const uint32_t* d_keys, const uint32_t* d_vals,
+                            const uint8_t* d_is_delete, uint64_t n, void* stream) {
+  if (!h || (n && (!d_keys || !d_vals || !d_is_delete)) || n > h->b) return LSM_ERR_ARG;
+  if (n == 0) return LSM_OK;
+  DeviceGuard g(h->device);
+  return apply_batch(h, kSortUpdate, d_keys, d_vals, d_is_delete, n, static_cast<cudaStream_t>(stream), true);
+}
+
+lsm_status lsm_lookup(lsm_t* h, const uint32_t* d_q, uint64_t nq, uint32_t* d_val, uint8_t* d_found,
+                      void* stream) {
+  if (!h || (nq && (!d_q || !d_val || !d_found))) return LSM_ERR_ARG;
+  if (nq == 0) return LSM_OK;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const LevelSet ls = full_levels(h);
+  if (ls.count == 0) {
+    LSM_TRY(cudaMemsetAsync(d_val, 0, sizeof(uint32_t) * nq, st));
+    LSM_TRY(cudaMemsetAsync(d_found, 0, nq, st));
+    return LSM_OK;
+  }
+  const bool sorted = h->lookup_mode == 2 && nq <= 0xFFFFFFFFull;
+  ProfScope ps(h, LSM_PROF_LOOKUP, double(nq) * (9.0 + 32.0 * ls.count), st);
+  if (!sorted) return cuda_status(lookup_launch(ls, d_q, nq, d_val, d_found, st));
+  // Sorted mode: radix sort (key, position), then warp-cooperative search.
+  const uint64_t n = nq;
+  const uint64_t tiles = (n + kSortTile - 1) / kSortTile;
+  const uint64_t npad = round_up(n, kLevelAlign) + kSlack;
+  LSM_TRY(ensure_q(h, 4 * npad * sizeof(uint32_t)));
+  if (!h->qsws.lookback || h->qsws.max_tiles < tiles) {
+    if (h->qsws.lookback) cudaFree(h->qsws.lookback);
+    h->qsws.lookback = nullptr;
+    LSM_TRY(dalloc(&h->qsws.lookback, uint64_t(kSortPasses) * tiles * 256));
+    LSM_TRY(cudaMemset(h->qsws.lookback, 0, sizeof(uint64_t) * kSortPasses * tiles * 256));
+    h->qsws.max_tiles = uint32_t(tiles);
+    h->qsws.epoch = 0;
+  }
+  if (!h->d_qctl) LSM_TRY(dalloc(&h->d_qctl, kSortCtlWords));
+  h->qsws.ctl = h->d_qctl;
+  h->qsws.sticky = h->d_misc + kMiscSticky;
+  uint32_t* base = reinterpret_cast<uint32_t*>(h->d_q);
+  SortArgs a{};
+  a.mode = kSortQueries;
+  a.in_keys = d_q;
+  a.n_in = n;
+  a.n = uint32_t(n);
+  a.out_keys = base;
+  a.out_vals = base + npad;
+  a.tmp_keys = base + 2 * npad;
+  a.tmp_vals = base + 3 * npad;
+  LSM_TRY(sort_launch(a, h->qsws, st, nullptr, nullptr));
+  return cuda_status(lookup_sorted_launch(ls, a.out_keys, a.out_vals, n, d_val, d_found, st));
+}
+
+lsm_status lsm_count(lsm_t* h, const uint32_t* d_k1, const uint32_t* d_k2, uint64_t nq, uint32_t* d_count,
+                     void* stream) {
+  if (!h || (nq && (!d_k1 || !d_k2 || !d_count))) return LSM_ERR_ARG;
+  if (nq == 0) return LSM_OK;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const LevelSet ls = full_levels(h);
+  if (ls.count == 0) return cuda_status(cudaMemsetAsync(d_count, 0, sizeof(uint32_t) * nq, st));
+  ProfScope ps(h, LSM_PROF_COUNT, double(nq) * (12.0 + 64.0 * ls.count), st);
+  return cuda_status(count_launch(ls, d_k1, d_k2, nq, d_count, nullptr, st));
+}
+
+lsm_status lsm_range(lsm_t* h, const uint32_t* d_k1, const uint32_t* d_k2, uint64_t nq, uint64_t* d_offsets,
+                     uint32_t* d_keys, uint32_t* d_vals, uint64_t capacity, uint64_t* total_out, void* stream) {
+  if (!h || !d_offsets || !total_out || (nq && (!d_k1 || !d_k2))) return LSM_ERR_ARG;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const LevelSet ls = full_levels(h);
+  if (nq == 0 || ls.count == 0) {
+    LSM_TRY(cudaMemsetAsync(d_offsets, 0, sizeof(uint64_t) * (nq + 1), st));
+    *total_out = 0;
+    return LSM_OK;
+  }
+  // scratch: counts[nq] | bounds[nq * 2 * levels] | scan look-back[tiles]
+  const uint64_t cnt_words = round_up(nq, 2);
+  const uint64_t bnd_words = round_up(nq * 2 * ls.count, 2);
+  const uint64_t lb_words = scan_tiles(nq);
+  LSM_TRY(ensure_q(h, (cnt_words + bnd_words) * 4 + lb_words * 8));
+  uint32_t* counts = reinterpret_cast<uint32_t*>(h->d_q);
+  uint32_t* bounds = counts + cnt_words;
+  uint64_t* lb = reinterpret_cast<uint64_t*>(bounds + bnd_words);
+  {
+    ProfScope ps(h, LSM_PROF_COUNT, double(nq) * (12.0 + 64.0 * ls.count), st);
+    LSM_TRY(count_launch(ls, d_k1, d_k2, nq, counts, bounds, st));
+    LSM_TRY(scan_launch(counts, nq, d_offsets, lb, h->d_misc + kMiscCtrB, h->d_misc + kMiscSticky, st));
+  }
+  LSM_TRY(cudaMemcpyAsync(h->h_u64, d_offsets + nq, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+  LSM_TRY(cudaStreamSynchronize(st));
+  const uint64_t total = *h->h_u64;
+  *total_out = total;
+  if (total > capacity) return LSM_ERR_CAPACITY;
+  if (total && (!d_keys || !d_vals)) return LSM_ERR_ARG;
+  ProfScope ps(h, LSM_PROF_EMIT, 8.0 * double(total) + 8.0 * double(nq), st);
+  return cuda_status(range_emit_launch(ls, nq, bounds, d_offsets, d_keys, d_vals, st));
+}
+
+lsm_status lsm_cleanup(lsm_t* h, void* stream) {
+  if (!h) return LSM_ERR_ARG;
+  if (h->r == 0) return LSM_OK;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint64_t total = h->r * h->b;
+  if (h->clean_cap < total) {
+    if (h->d_ck) cudaFree(h->d_ck);
+    if (h->d_cv) cudaFree(h->d_cv);
+    if (h->d_clb) cudaFree(h->d_clb);
+    h->d_ck = h->d_cv = nullptr;
+    h->d_clb = nullptr;
+    h->clean_cap = 0;
+    const uint64_t cap = h->capacity;  // enough for any later cleanup too
+    LSM_TRY(dalloc(&h->d_ck, cap + kSlack));
+    LSM_TRY(dalloc(&h->d_cv, cap + kSlack));
+    LSM_TRY(dalloc(&h->d_clb, fold_tiles(cap) + 1));
+    h->clean_cap = cap;
+  }
+  const LevelSet ls = full_levels(h);
+  FoldArgs f{};
+  f.src.count = ls.count;
+  for (int i = 0; i < ls.count; ++i) {
+    f.src.keys[i] = ls.keys[i];
+    f.src.vals[i] = ls.vals[i];
+    f.src.n[i] = ls.n[i];
+  }
+  f.total = total;
+  f.out_keys = h->d_ck;
+  f.out_vals = h->d_cv;
+  f.part = h->d_part;
+  f.status = h->d_misc + kMiscSticky;
+  f.cleanup = true;
+  f.lookback = h->d_clb;
+  f.tile_ctr = h->d_misc + kMiscCtrA;
+  f.out_count = h->d_u64;
+  {
+    ProfScope ps(h, LSM_PROF_CLEANUP, 8.0 * double(total), st);
+    LSM_TRY(fold_launch(f, st));
+  }
+  LSM_TRY(cudaMemcpyAsync(h->h_u64, h->d_u64, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+  LSM_TRY(cudaStreamSynchronize(st));
+  const uint64_t n_live = *h->h_u64;
+  if (n_live > total) return LSM_ERR_CUDA;
+  const uint64_t r2 = (n_live + h->b - 1) / h->b;
+  DistributeArgs d{};
+  d.src_keys = h->d_ck;
+  d.src_vals = h->d_cv;
+  d.n_live = n_live;
+  d.keys = h->d_keys;
+  d.vals = h->d_vals;
+  d.total = r2 * h->b;
+  for (uint32_t i = 0; i < h->L; ++i) {
+    if (!((r2 >> i) & 1u)) continue;
+    d.level_off[d.nlevels] = h->level_off[i];
+    d.level_start[d.nlevels] = uint64_t(h->b) * (r2 & ((1ull << i) - 1));
+    d.level_size[d.nlevels] = uint64_t(h->b) << i;
+    ++d.nlevels;
+  }
+  {
+    ProfScope ps(h, LSM_PROF_CLEANUP, 8.0 * double(d.total), st);
+    LSM_TRY(distribute_launch(d, st));
+  }
+  h->r = r2;
+  return LSM_OK;
+}
+
+lsm_status lsm_stats(const lsm_t* h, uint64_t* r, uint64_t* resident, uint32_t* b, uint32_t* levels) {
+  if (!h) return LSM_ERR_ARG;
+  if (r) *r = h->r;
+  if (resident) *resident = h->r * h->b;
+  if (b) *b = h->b;
+  if (levels) *levels = h->L;
+  return LSM_OK;
+}
+
+lsm_status lsm_level_offset(const lsm_t* h, uint32_t i, uint64_t* offset, uint64_t* size) {
+  if (!h || !offset || !size) return LSM_ERR_ARG;
+  if (i >= h->L) {
+    *offset = h->capacity;
+    *size = 0;
+    return LSM_OK;
+  }
+  *offset = h->level_off[i];
+  *size = uint64_t(h->b) << i;
+  return LSM_OK;
+}
+
+uint64_t lsm_capacity(const lsm_t* h) { return h ? h->capacity : 0; }
+
+lsm_status lsm_reset(lsm_t* h) {
+  if (!h) return LSM_ERR_ARG;
+  h->r = 0;
+  return LSM_OK;
+}
+
+lsm_status lsm_profile(lsm_t* h, int enable) {
+  if (!h) return LSM_ERR_ARG;
+  DeviceGuard g(h->device);
+  LSM_TRY(cudaDeviceSynchronize());
+  for (auto& p : h->prof_pending) {
+    h->prof_pool.push_back(p.a);
+    h->prof_pool.push_back(p.b);
+  }
+  h->prof_pending.clear();
+  memset(h->prof_acc, 0, sizeof(h->prof_acc));
+  h->prof = enable != 0;
+  return LSM_OK;
+}
+
+lsm_status lsm_profile_read(lsm_t* h, lsm_profile_entry* out) {
+  if (!h || !out) return LSM_ERR_ARG;
+  DeviceGuard g(h->device);
+  LSM_TRY(cudaDeviceSynchronize());
+  for (auto& p : h->prof_pending) {
+    float ms = 0.f;
+    LSM_TRY(cudaEventElapsedTime(&ms, p.a, p.b));
+    lsm_profile_entry& e = h->prof_acc[p.group];
+    e.launches += 1;
+    e.ms += ms;
+    e.bytes += p.bytes;
+    h->prof_pool.push_back(p.a);
+    h->prof_pool.push_back(p.b);
+  }
+  h->prof_pending.clear();
+  memcpy(out, h->prof_acc, sizeof(h->prof_acc));
+  return LSM_OK;
+}
+
+lsm_status lsm_dump_levels(const lsm_t* h, uint32_t* h_keys, uint32_t* h_vals, void* stream) {
+  if (!h || !h_keys || !h_vals) return LSM_ERR_ARG;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (uint32_t i = 0; i < h->L; ++i) {
+    if (!((h->r >> i) & 1u)) continue;
+    const uint64_t off = h->level_off[i], n = uint64_t(h->b) << i;
+    LSM_TRY(cudaMemcpyAsync(h_keys + off, h->d_keys + off, n * 4, cudaMemcpyDeviceToHost, st));
+    LSM_TRY(cudaMemcpyAsync(h_vals + off, h->d_vals + off, n * 4, cudaMemcpyDeviceToHost, st));
+  }
+  return cuda_status(cudaStreamSynchronize(st));
+}
+
+lsm_status lsm_sort_pairs(lsm_t* h, const uint32_t* d_keys_in, const uint32_t* d_vals_in, uint32_t* d_keys_out,
+                          uint32_t* d_vals_out, uint64_t n, void* stream) {
+  if (!h || n > h->b || (n && (!d_keys_in || !d_vals_in || !d_keys_out || !d_vals_out))) return LSM_ERR_ARG;
+  if (n == 0) return LSM_OK;
+  DeviceGuard g(h->device);
+  SortArgs a{};
+  a.mode = kSortPairs;
+  a.in_keys = d_keys_in;
+  a.in_vals = d_vals_in;
+  a.n_in = n;
+  a.n = uint32_t(n);
+  a.out_keys = d_keys_out;
+  a.out_vals = d_vals_out;
+  a.tmp_keys = h->d_tk;
+  a.tmp_vals = h->d_tv;
+  return cuda_status(sort_launch(a, h->sws, static_cast<cudaStream_t>(stream), nullptr, nullptr));
+}
+
+lsm_status lsm_set_option(lsm_t* h, lsm_option opt, int64_t value) {
+  if (!h) return LSM_ERR_ARG;
+  if (opt == LSM_OPT_LOOKUP_MODE) {
+    if (value < 0 || value > 2) return LSM_ERR_ARG;
+    h->lookup_mode = int(value);
+    return LSM_OK;
+  }
+  return LSM_ERR_ARG;
+}
+
+lsm_status lsm_get_option(lsm_t* h, lsm_option opt, int64_t* value) {
+  if (!h || !value) return LSM_ERR_ARG;
+  if (opt == LSM_OPT_LOOKUP_MODE) {
+    *value = h->lookup_mode;
+    return LSM_OK;
+  }
+  if (opt == LSM_OPT_DEVICE_ERROR) {
+    DeviceGuard g(h->device);
+    uint32_t w = 0;
+    LSM_TRY(cudaDeviceSynchronize());
+    LSM_TRY(cudaMemcpy(&w, h->d_misc + kMiscSticky, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    LSM_TRY(cudaMemset(h->d_misc + kMiscSticky, 0, sizeof(uint32_t)));
+    *value = w;
+    return LSM_OK;
+  }
+  return LSM_ERR_ARG;
+}
+
+}  // extern "C"

@@ -1,0 +1,147 @@
+// Internal interface between the host orchestrator (lsm_api.cu) and the
+// kernel translation units.  Plain structs of device pointers and sizes.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gpulsm {
+
+constexpr int kMaxLevels = 32;                 // levels a handle may allocate
+constexpr int kMaxSources = kMaxLevels + 1;    // fold: the batch + every level
+constexpr uint32_t kMaxUserKey = 0x7FFFFFFEu;  // 2^31 - 2
+constexpr uint32_t kPlaceboKv = 0xFFFFFFFEu;   // key 2^31 - 1 as a tombstone
+constexpr uint32_t kSlack = 32;                // elements readable past every buffer end
+constexpr uint32_t kLevelAlign = 32;           // level starts: multiples of 32 elements
+
+// Sticky device error bits (a device word, copied to the host on demand).
+constexpr uint32_t kErrBadKey = 1u;
+constexpr uint32_t kErrTimeout = 2u;
+constexpr uint32_t kErrAlign = 4u;
+
+// Spin-wait bound for decoupled look-back and mbarrier waits, in
+// nanoseconds of globaltimer: a wait that exceeds it sets kErrTimeout and
+// gives up instead of hanging the GPU.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+// ------------------------------------------------------------------ sort ---
+enum SortInput : int {
+  kSortPairs = 0,     // (keys[i], vals[i]) as given
+  kSortInsert = 1,    // batch of inserts: encode, reverse, pad
+  kSortDelete = 2,    // batch of deletes: tombstones, value 0
+  kSortUpdate = 3,    // mixed batch, per-op delete flag
+  kSortQueries = 4    // (keys[i], i): sort query keys with their positions
+};
+
+constexpr int kSortPasses = 4;
+constexpr int kSortTile = 4096;  // elements per CTA tile of a pass
+
+struct SortArgs {
+  int mode;
+  const uint32_t* in_keys;
+  const uint32_t* in_vals;
+  const uint8_t* in_del;
+  uint64_t n_in;        // ops available in the input (batch modes)
+  uint32_t n;           // elements to sort (b for a batch)
+  uint32_t* out_keys;   // destination; also used as ping-pong space
+  uint32_t* out_vals;
+  uint32_t* tmp_keys;   // n elements of scratch
+  uint32_t* tmp_vals;
+};
+
+struct SortWorkspace {
+  uint32_t* ctl;        // [hist 4*256][tile counters 4][status 1][pad]
+  uint64_t* lookback;   // kSortPasses * max_tiles * 256 words
+  uint32_t max_tiles;
+  uint32_t epoch;       // bumped per sort; 0 never used
+  uint32_t* sticky;     // persistent device error word (wait timeouts)
+};
+constexpr int kSortCtlWords = kSortPasses * 256 + kSortPasses + 4;
+constexpr int kSortCtlStatus = kSortPasses * 256 + kSortPasses;
+
+// Enqueues the whole sort.  If h_status is given, the device status word is
+// copied to it right after the key check (the histogram kernel) and `ev` is
+// recorded there, so the host can learn about bad keys early.
+cudaError_t sort_launch(const SortArgs& a, SortWorkspace& ws, cudaStream_t st,
+                        uint32_t* h_status, cudaEvent_t ev);
+
+// Device key check alone over n keys (multi-batch calls check all first).
+cudaError_t check_keys_launch(const uint32_t* keys, uint64_t n, uint32_t* status,
+                              cudaStream_t st);
+
+// ------------------------------------------------------------------ fold ---
+constexpr int kFoldTile = 4096;  // output elements per merge CTA
+
+struct FoldSources {
+  const uint32_t* keys[kMaxSources];
+  const uint32_t* vals[kMaxSources];
+  uint32_t n[kMaxSources];
+  int count;  // rank order: newest first
+};
+
+struct FoldArgs {
+  FoldSources src;
+  uint64_t total;
+  uint32_t* out_keys;
+  uint32_t* out_vals;
+  uint32_t* part;        // (ntiles + 1) * count co-ranks
+  uint32_t* status;
+  // cleanup only: keep the first element of every key if regular, compacted
+  bool cleanup;
+  uint64_t* lookback;    // ntiles words, zeroed by the launcher
+  uint32_t* tile_ctr;    // zeroed by the launcher
+  uint64_t* out_count;   // number of kept elements
+};
+
+inline uint64_t fold_tiles(uint64_t total) { return (total + kFoldTile - 1) / kFoldTile; }
+
+// fold_launch = fold_partition_launch + fold_merge_launch.
+cudaError_t fold_launch(const FoldArgs& a, cudaStream_t st);
+cudaError_t fold_partition_launch(const FoldArgs& a, cudaStream_t st);
+cudaError_t fold_merge_launch(const FoldArgs& a, cudaStream_t st);
+
+struct DistributeArgs {
+  const uint32_t* src_keys;  // compacted live pairs
+  const uint32_t* src_vals;
+  uint64_t n_live;
+  uint32_t* keys;            // level array
+  uint32_t* vals;
+  int nlevels;
+  uint64_t level_off[kMaxLevels];    // destination offset of each filled level
+  uint64_t level_start[kMaxLevels];  // first compacted index it receives
+  uint64_t level_size[kMaxLevels];
+  uint64_t total;                    // r' * b
+};
+cudaError_t distribute_launch(const DistributeArgs& a, cudaStream_t st);
+
+// ----------------------------------------------------------------- query ---
+struct LevelSet {
+  const uint32_t* keys[kMaxLevels];
+  const uint32_t* vals[kMaxLevels];
+  uint32_t n[kMaxLevels];
+  int count;  // full levels, newest (smallest) first
+};
+
+cudaError_t lookup_launch(const LevelSet& ls, const uint32_t* q, uint64_t nq,
+                          uint32_t* val, uint8_t* found, cudaStream_t st);
+
+// Lookup of queries already sorted by key (kSortQueries output): results go
+// to positions idx[i] of the output arrays.
+cudaError_t lookup_sorted_launch(const LevelSet& ls, const uint32_t* sq, const uint32_t* idx,
+                                 uint64_t nq, uint32_t* val, uint8_t* found, cudaStream_t st);
+
+// Count per query; when `bounds` is not null also stores, per query and
+// level, the window [lo, hi) (2 * count words per query).
+cudaError_t count_launch(const LevelSet& ls, const uint32_t* k1, const uint32_t* k2,
+                         uint64_t nq, uint32_t* count, uint32_t* bounds, cudaStream_t st);
+
+// Exclusive scan of n u32 into n + 1 u64 (out[n] = total).
+cudaError_t scan_launch(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* lookback,
+                        uint32_t* tile_ctr, uint32_t* status, cudaStream_t st);
+inline uint64_t scan_tiles(uint64_t n) { return (n + 2047) / 2048; }
+
+cudaError_t range_emit_launch(const LevelSet& ls, uint64_t nq, const uint32_t* bounds,
+                              const uint64_t* offsets, uint32_t* keys, uint32_t* vals,
+                              cudaStream_t st);
+
+}  // namespace gpulsm

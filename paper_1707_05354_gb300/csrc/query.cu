@@ -1,0 +1,372 @@
+// Retrieval paths of the GPU LSM: LOOKUP (§III-D, §IV-B, Fig. 2(b)), COUNT
+// (§III-E, §IV-C, Fig. 2(c)) and RANGE (§III-E, §IV-D, Fig. 2(d)).
+//
+// LOOKUP  searches the full levels from the newest (smallest) to the oldest
+//         for the first element whose key is >= q; if that element has key q
+//         it decides: regular -> found with its value, tombstone -> absent
+//         (and the search stops).  Each CTA first caches, per level, a sorted
+//         sample of every stride-th key variable (the top of the level's
+//         search tree) in shared memory; a search narrows to one stride there
+//         and finishes in global memory.
+//         lookup_direct takes the queries in input order (one thread each);
+//         lookup_sorted takes queries sorted by key: the first and last lane
+//         of a warp bound the warp's window in each level and every lane then
+//         searches only that window, which its neighbours share in cache
+//         (the "bulk" alternative of §IV-B).
+// COUNT   per query and level the window [lower_bound(k1), upper_bound(k2))
+//         on the original key; the windows of all levels are then merged on
+//         the key, newer level first among equal keys, and a key counts when
+//         its first element in that order (its newest version) is regular.
+//         This replaces the paper's gather + segmented sort + validation of
+//         §IV-C by a per-query multi-way merge of windows that are already
+//         sorted; the result is the same count.
+// RANGE   the same windows (kept from the count pass), an exclusive scan of
+//         the counts into offsets, and a second merge that writes each live
+//         (key, value) at its offset, keys ascending within a query (§IV-D).
+#include "lsm_device.cuh"
+
+namespace gpulsm {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kSplitWords = 8192;  // shared-memory splitter budget per CTA (32 KB)
+
+__device__ __forceinline__ void fill_splitters(const LevelSet& ls, int per_level, uint32_t* s_split,
+                                               uint32_t* s_stride) {
+  for (int l = 0; l < ls.count; ++l) {
+    const uint32_t n = ls.n[l];
+    const uint32_t stride = (n + per_level - 1) / per_level;
+    for (int j = threadIdx.x; j < per_level; j += blockDim.x) {
+      const uint64_t pos = uint64_t(j) * stride;
+      s_split[l * per_level + j] = pos < n ? __ldg(ls.keys[l] + pos) : 0xFFFFFFFFu;
+    }
+    if (threadIdx.x == 0) s_stride[l] = stride;
+  }
+}
+
+// lower_bound of key variable `target` in level l, using the cached samples.
+__device__ __forceinline__ uint32_t level_lower_bound(const LevelSet& ls, int l, int per_level,
+                                                      const uint32_t* s_split, const uint32_t* s_stride,
+                                                      uint32_t target) {
+  const uint32_t* sp = s_split + l * per_level;
+  uint32_t a = 0, b = uint32_t(per_level);
+  while (a < b) {
+    const uint32_t m = (a + b) >> 1;
+    if (sp[m] < target) a = m + 1; else b = m;
+  }
+  const uint32_t stride = s_stride[l], n = ls.n[l];
+  const uint32_t lo = a == 0 ? 0u : (a - 1) * stride + 1;
+  const uint64_t hi64 = uint64_t(a) * stride;
+  const uint32_t hi = hi64 < n ? uint32_t(hi64) : n;
+  return lower_bound_kv(ls.keys[l], lo, hi, target);
+}
+
+// Lookup of one key over the levels (newest first).
+__device__ __forceinline__ void lookup_one(const LevelSet& ls, int per_level, const uint32_t* s_split,
+                                           const uint32_t* s_stride, uint32_t key, uint32_t& val,
+                                           uint8_t& found) {
+  val = 0;
+  found = 0;
+  if (key > kMaxUserKey) return;
+  const uint32_t target = key << 1;
+  for (int l = 0; l < ls.count; ++l) {
+    const uint32_t pos = level_lower_bound(ls, l, per_level, s_split, s_stride, target);
+    if (pos < ls.n[l]) {
+      const uint32_t kv = __ldg(ls.keys[l] + pos);
+      if (key_of(kv) == key) {
+        if (kv & 1u) {
+          found = 1;
+          val = __ldg(ls.vals[l] + pos);
+        }
+        return;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) lookup_direct(LevelSet ls, int per_level,
+                                                          const uint32_t* __restrict__ q, uint64_t nq,
+                                                          uint32_t* __restrict__ out_v,
+                                                          uint8_t* __restrict__ out_f) {
+  extern __shared__ uint32_t s_split[];
+  __shared__ uint32_t s_stride[kMaxLevels];
+  fill_splitters(ls, per_level, s_split, s_stride);
+  __syncthreads();
+  for (uint64_t i = blockIdx.x * uint64_t(kThreads) + threadIdx.x; i < nq;
+       i += uint64_t(gridDim.x) * kThreads) {
+    uint32_t v;
+    uint8_t f;
+    lookup_one(ls, per_level, s_split, s_stride, __ldg(q + i), v, f);
+    out_v[i] = v;
+    out_f[i] = f;
+  }
+}
+
+// Queries sorted by key; results scattered back to positions idx[i].
+__global__ void __launch_bounds__(kThreads) lookup_sorted(LevelSet ls, int per_level,
+                                                          const uint32_t* __restrict__ sq,
+                                                          const uint32_t* __restrict__ idx, uint64_t nq,
+                                                          uint32_t* __restrict__ out_v,
+                                                          uint8_t* __restrict__ out_f) {
+  extern __shared__ uint32_t s_split[];
+  __shared__ uint32_t s_stride[kMaxLevels];
+  fill_splitters(ls, per_level, s_split, s_stride);
+  __syncthreads();
+  const uint32_t lane = lane_id();
+  const uint64_t warps = uint64_t(gridDim.x) * (kThreads / 32);
+  for (uint64_t w = (blockIdx.x * uint64_t(kThreads) + threadIdx.x) >> 5; w * 32 < nq; w += warps) {
+    const uint64_t i = w * 32 + lane;
+    const bool act = i < nq;
+    const uint32_t key = act ? __ldg(sq + i) : 0xFFFFFFFFu;
+    // the warp's smallest and largest valid query (queries are sorted and
+    // out-of-domain keys sort last)
+    const uint32_t nact = __popc(__ballot_sync(0xffffffffu, act && key <= kMaxUserKey));
+    uint32_t val = 0;
+    uint8_t found = 0;
+    bool done = !(act && key <= kMaxUserKey);
+    if (nact) {
+      const uint32_t kfirst = __shfl_sync(0xffffffffu, key, 0);
+      const uint32_t klast = __shfl_sync(0xffffffffu, key, nact - 1);
+      for (int l = 0; l < ls.count; ++l) {
+        if (__all_sync(0xffffffffu, done)) break;
+        // Lanes 0 and 1 find where the warp's smallest and largest key would
+        // start; every lane's answer lies in [wlo, whi] (lower bounds are
+        // monotone in the key), so each lane searches [wlo, whi + 1).
+        uint32_t edge = 0;
+        if (lane < 2)
+          edge = level_lower_bound(ls, l, per_level, s_split, s_stride,
+                                   (lane == 0 ? kfirst : klast) << 1);
+        const uint32_t wlo = __shfl_sync(0xffffffffu, edge, 0);
+        uint32_t whi = __shfl_sync(0xffffffffu, edge, 1);
+        whi = whi < ls.n[l] ? whi + 1 : ls.n[l];
+        if (!done) {
+          const uint32_t pos = lower_bound_kv(ls.keys[l], wlo, whi, key << 1);
+          if (pos < ls.n[l]) {
+            const uint32_t kv = __ldg(ls.keys[l] + pos);
+            if (key_of(kv) == key) {
+              done = true;
+              if (kv & 1u) {
+                found = 1;
+                val = __ldg(ls.vals[l] + pos);
+              }
+            }
+          }
+        }
+      }
+    }
+    if (act) {
+      const uint32_t o = __ldg(idx + i);
+      if (o < nq) {  // a permutation of [0, nq) unless the sort gave up on a wait
+        out_v[o] = val;
+        out_f[o] = found;
+      }
+    }
+  }
+}
+
+// Per-query multi-way merge of the level windows on the key, newer level
+// first among equal keys; visits the newest element of every key once.
+template <bool kEmit>
+__device__ __forceinline__ uint32_t merge_windows(const LevelSet& ls, const uint32_t* lo, const uint32_t* hi,
+                                                  uint32_t* out_k, uint32_t* out_v, uint64_t room = 0) {
+  uint32_t cur[kMaxLevels], head[kMaxLevels];
+  for (int l = 0; l < ls.count; ++l) {
+    cur[l] = lo[l];
+    head[l] = cur[l] < hi[l] ? key_of(__ldg(ls.keys[l] + cur[l])) : 0xFFFFFFFFu;
+  }
+  uint32_t c = 0, last = 0xFFFFFFFFu;
+  while (true) {
+    int best = -1;
+    uint32_t bk = 0xFFFFFFFFu;
+    for (int l = 0; l < ls.count; ++l)
+      if (head[l] < bk) {
+        bk = head[l];
+        best = l;
+      }
+    if (best < 0) break;
+    const uint32_t p = cur[best];
+    if (bk != last) {
+      last = bk;
+      const uint32_t kv = __ldg(ls.keys[best] + p);
+      if (kv & 1u) {
+        if (kEmit && c < room) {
+          out_k[c] = bk;
+          out_v[c] = __ldg(ls.vals[best] + p);
+        }
+        ++c;
+      }
+    }
+    cur[best] = p + 1;
+    head[best] = p + 1 < hi[best] ? key_of(__ldg(ls.keys[best] + p + 1)) : 0xFFFFFFFFu;
+  }
+  return c;
+}
+
+__global__ void __launch_bounds__(kThreads) count_kernel(LevelSet ls, const uint32_t* __restrict__ k1,
+                                                         const uint32_t* __restrict__ k2, uint64_t nq,
+                                                         uint32_t* __restrict__ out_count,
+                                                         uint32_t* __restrict__ bounds) {
+  for (uint64_t i = blockIdx.x * uint64_t(kThreads) + threadIdx.x; i < nq;
+       i += uint64_t(gridDim.x) * kThreads) {
+    const uint32_t a = __ldg(k1 + i);
+    uint32_t z = __ldg(k2 + i);
+    if (z > kMaxUserKey) z = kMaxUserKey;
+    uint32_t lo[kMaxLevels], hi[kMaxLevels];
+    const bool empty = a > z;
+    for (int l = 0; l < ls.count; ++l) {
+      if (empty) {
+        lo[l] = hi[l] = 0;
+      } else {
+        lo[l] = lower_bound_kv(ls.keys[l], 0, ls.n[l], a << 1);
+        hi[l] = lower_bound_kv(ls.keys[l], lo[l], ls.n[l], (z + 1u) << 1);
+      }
+    }
+    out_count[i] = merge_windows<false>(ls, lo, hi, nullptr, nullptr);
+    if (bounds) {
+      uint32_t* b = bounds + i * 2 * ls.count;
+      for (int l = 0; l < ls.count; ++l) {
+        b[2 * l] = lo[l];
+        b[2 * l + 1] = hi[l];
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) range_emit(LevelSet ls, uint64_t nq,
+                                                       const uint32_t* __restrict__ bounds,
+                                                       const uint64_t* __restrict__ offsets,
+                                                       uint32_t* __restrict__ keys,
+                                                       uint32_t* __restrict__ vals) {
+  for (uint64_t i = blockIdx.x * uint64_t(kThreads) + threadIdx.x; i < nq;
+       i += uint64_t(gridDim.x) * kThreads) {
+    uint32_t lo[kMaxLevels], hi[kMaxLevels];
+    const uint32_t* b = bounds + i * 2 * ls.count;
+    for (int l = 0; l < ls.count; ++l) {
+      lo[l] = b[2 * l];
+      hi[l] = b[2 * l + 1];
+    }
+    const uint64_t o = offsets[i];
+    merge_windows<true>(ls, lo, hi, keys + o, vals + o, offsets[i + 1] - o);
+  }
+}
+
+constexpr int kScanIPT = 8;
+constexpr int kScanTile = kThreads * kScanIPT;  // 2048
+constexpr uint64_t kLbAgg = 1ull << 62, kLbIncl = 2ull << 62, kLbMask = (1ull << 62) - 1;
+
+__global__ void __launch_bounds__(kThreads) scan_kernel(const uint32_t* __restrict__ in, uint64_t n,
+                                                        uint64_t* __restrict__ out, uint64_t* lookback,
+                                                        uint32_t* tile_ctr, uint32_t* status,
+                                                        uint64_t ntiles) {
+  __shared__ uint64_t s_scan[kThreads / 32];
+  __shared__ uint64_t s_prefix;
+  __shared__ uint32_t s_tile;
+  const uint32_t tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+  __syncthreads();
+  const uint64_t tile = s_tile;
+  const uint64_t base = tile * kScanTile + uint64_t(tid) * kScanIPT;
+  uint32_t v[kScanIPT];
+  uint64_t sum = 0;
+#pragma unroll
+  for (int j = 0; j < kScanIPT; ++j) {
+    v[j] = base + j < n ? __ldg(in + base + j) : 0u;
+    sum += v[j];
+  }
+  uint64_t tile_sum;
+  const uint64_t before = block_excl_scan<kThreads, uint64_t>(sum, s_scan, tile_sum);
+  if (tid == 0) {
+    uint64_t prefix = 0;
+    if (tile == 0) {
+      st_relaxed_u64(lookback, kLbIncl | tile_sum);
+    } else {
+      st_relaxed_u64(lookback + tile, kLbAgg | tile_sum);
+      int64_t t = int64_t(tile) - 1;
+      uint64_t t0 = 0;
+      while (t >= 0) {
+        const uint64_t w = ld_relaxed_u64(lookback + t);
+        if (!(w & (kLbAgg | kLbIncl))) {
+          if (t0 == 0) t0 = globaltimer_ns();
+          else if (globaltimer_ns() - t0 > kWaitLimitNs) {
+            atomicOr(status, kErrTimeout);
+            break;
+          }
+          continue;
+        }
+        prefix += w & kLbMask;
+        if (w & kLbIncl) break;
+        --t;
+      }
+      st_relaxed_u64(lookback + tile, kLbIncl | (prefix + tile_sum));
+    }
+    s_prefix = prefix;
+    if (tile == ntiles - 1) out[n] = prefix + tile_sum;
+  }
+  __syncthreads();
+  uint64_t run = s_prefix + before;
+#pragma unroll
+  for (int j = 0; j < kScanIPT; ++j) {
+    if (base + j < n) out[base + j] = run;
+    run += v[j];
+  }
+}
+
+int splitters_per_level(int count) {
+  if (count <= 0) return 1;
+  int per = kSplitWords / count;
+  return per < 1 ? 1 : per;
+}
+
+unsigned persistent_grid(uint64_t work, int per_block, unsigned cap) {
+  uint64_t b = (work + per_block - 1) / per_block;
+  if (b > cap) b = cap;
+  return unsigned(b ? b : 1);
+}
+
+}  // namespace
+
+cudaError_t lookup_launch(const LevelSet& ls, const uint32_t* q, uint64_t nq, uint32_t* val, uint8_t* found,
+                          cudaStream_t st) {
+  if (nq == 0) return cudaSuccess;
+  const int per = splitters_per_level(ls.count);
+  const size_t smem = size_t(per) * (ls.count ? ls.count : 1) * sizeof(uint32_t);
+  lookup_direct<<<persistent_grid(nq, kThreads, 152 * 6), kThreads, smem, st>>>(ls, per, q, nq, val, found);
+  return cudaGetLastError();
+}
+
+cudaError_t lookup_sorted_launch(const LevelSet& ls, const uint32_t* sq, const uint32_t* idx, uint64_t nq,
+                                 uint32_t* val, uint8_t* found, cudaStream_t st) {
+  if (nq == 0) return cudaSuccess;
+  const int per = splitters_per_level(ls.count);
+  const size_t smem = size_t(per) * (ls.count ? ls.count : 1) * sizeof(uint32_t);
+  lookup_sorted<<<persistent_grid(nq, kThreads, 152 * 6), kThreads, smem, st>>>(ls, per, sq, idx, nq, val,
+                                                                               found);
+  return cudaGetLastError();
+}
+
+cudaError_t count_launch(const LevelSet& ls, const uint32_t* k1, const uint32_t* k2, uint64_t nq,
+                         uint32_t* count, uint32_t* bounds, cudaStream_t st) {
+  if (nq == 0) return cudaSuccess;
+  count_kernel<<<persistent_grid(nq, kThreads, 152 * 8), kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds);
+  return cudaGetLastError();
+}
+
+cudaError_t scan_launch(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* lookback, uint32_t* tile_ctr,
+                        uint32_t* status, cudaStream_t st) {
+  cudaError_t e;
+  if (n == 0) return cudaMemsetAsync(out, 0, sizeof(uint64_t), st);
+  const uint64_t ntiles = scan_tiles(n);
+  if ((e = cudaMemsetAsync(lookback, 0, sizeof(uint64_t) * ntiles, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(tile_ctr, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+  scan_kernel<<<unsigned(ntiles), kThreads, 0, st>>>(in, n, out, lookback, tile_ctr, status, ntiles);
+  return cudaGetLastError();
+}
+
+cudaError_t range_emit_launch(const LevelSet& ls, uint64_t nq, const uint32_t* bounds, const uint64_t* offsets,
+                              uint32_t* keys, uint32_t* vals, cudaStream_t st) {
+  if (nq == 0) return cudaSuccess;
+  range_emit<<<persistent_grid(nq, kThreads, 152 * 8), kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals);
+  return cudaGetLastError();
+}
+
+}  // namespace gpulsm

@@ -1,0 +1,304 @@
+"""ctypes binding of libgpulsm.so (the C ABI in include/gpulsm.h).
+
+Argument marshalling only: every step of every operation runs in the CUDA
+kernels of the library.  Importing this module loads the library and raises
+``ImportError`` when it has not been built (``paper_1707_05354_gb300.build``);
+there is no CPU fallback.
+
+Two layers:
+  * module functions with the C names (``lsm_create``, ``lsm_insert_batch``,
+    ...) taking raw device pointers (ints) and a stream handle, raising
+    :class:`LSMError` on any status but LSM_OK;
+  * :class:`LSM`, a convenience wrapper over torch CUDA tensors (uint32 data
+    travels in int32 tensors, bit for bit).
+"""
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgpulsm.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libgpulsm.so is not built: run `python -m paper_1707_05354_gb300.build` "
+                      "(or __graft_entry__.build()) on a machine with the CUDA toolkit")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+STATUS = {0: "LSM_OK", 1: "LSM_ERR_ARG", 2: "LSM_ERR_KEY_RANGE", 3: "LSM_ERR_FULL", 4: "LSM_ERR_OOM",
+          5: "LSM_ERR_BUDGET", 6: "LSM_ERR_CAPACITY", 7: "LSM_ERR_CUDA", 8: "LSM_ERR_TIMEOUT"}
+LSM_OK, LSM_ERR_ARG, LSM_ERR_KEY_RANGE, LSM_ERR_FULL = 0, 1, 2, 3
+LSM_ERR_OOM, LSM_ERR_BUDGET, LSM_ERR_CAPACITY, LSM_ERR_CUDA, LSM_ERR_TIMEOUT = 4, 5, 6, 7, 8
+LSM_OPT_LOOKUP_MODE, LSM_OPT_DEVICE_ERROR = 1, 2
+LOOKUP_AUTO, LOOKUP_DIRECT, LOOKUP_SORTED = 0, 1, 2
+
+_vp, _u64, _u32, _i32, _i64 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int64
+_SIGS = {
+    "lsm_status_str": ([_i32], ctypes.c_char_p),
+    "lsm_create": ([ctypes.POINTER(_vp), _u32, _u64, _i32], _i32),
+    "lsm_destroy": ([_vp], None),
+    "lsm_insert_batch": ([_vp, _vp, _vp, _u64, _vp], _i32),
+    "lsm_delete_batch": ([_vp, _vp, _u64, _vp], _i32),
+    "lsm_update_batch": ([_vp, _vp, _vp, _vp, _u64, _vp], _i32),
+    "lsm_lookup": ([_vp, _vp, _u64, _vp, _vp, _vp], _i32),
+    "lsm_count": ([_vp, _vp, _vp, _u64, _vp, _vp], _i32),
+    "lsm_range": ([_vp, _vp, _vp, _u64, _vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp], _i32),
+    "lsm_cleanup": ([_vp, _vp], _i32),
+    "lsm_stats": ([_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u32),
+                   ctypes.POINTER(_u32)], _i32),
+    "lsm_level_offset": ([_vp, _u32, ctypes.POINTER(_u64), ctypes.POINTER(_u64)], _i32),
+    "lsm_dump_levels": ([_vp, _vp, _vp, _vp], _i32),
+    "lsm_capacity": ([_vp], _u64),
+    "lsm_sort_pairs": ([_vp, _vp, _vp, _vp, _vp, _u64, _vp], _i32),
+    "lsm_set_option": ([_vp, _i32, _i64], _i32),
+    "lsm_get_option": ([_vp, _i32, ctypes.POINTER(_i64)], _i32),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+EXPORTED = tuple(_SIGS)
+
+
+class LSMError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__("%s%s" % (where + ": " if where else "", STATUS.get(status, status)))
+
+
+def _check(status, where):
+    if status != LSM_OK:
+        raise LSMError(status, where)
+    return status
+
+
+def lsm_status_str(s):
+    return _lib.lsm_status_str(s).decode()
+
+
+def lsm_create(b, max_elements, device=0):
+    h = _vp()
+    _check(_lib.lsm_create(ctypes.byref(h), b, max_elements, device), "lsm_create")
+    return h.value
+
+
+def lsm_destroy(h):
+    _lib.lsm_destroy(h)
+
+
+def lsm_insert_batch(h, d_keys, d_vals, n, stream=None):
+    return _check(_lib.lsm_insert_batch(h, d_keys, d_vals, n, stream), "lsm_insert_batch")
+
+
+def lsm_delete_batch(h, d_keys, n, stream=None):
+    return _check(_lib.lsm_delete_batch(h, d_keys, n, stream), "lsm_delete_batch")
+
+
+def lsm_update_batch(h, d_keys, d_vals, d_is_delete, n, stream=None):
+    return _check(_lib.lsm_update_batch(h, d_keys, d_vals, d_is_delete, n, stream), "lsm_update_batch")
+
+
+def lsm_lookup(h, d_q, nq, d_val, d_found, stream=None):
+    return _check(_lib.lsm_lookup(h, d_q, nq, d_val, d_found, stream), "lsm_lookup")
+
+
+def lsm_count(h, d_k1, d_k2, nq, d_count, stream=None):
+    return _check(_lib.lsm_count(h, d_k1, d_k2, nq, d_count, stream), "lsm_count")
+
+
+def lsm_range(h, d_k1, d_k2, nq, d_offsets, d_keys, d_vals, capacity, stream=None):
+    """Returns (status, total); LSM_ERR_CAPACITY is returned, not raised."""
+    total = _u64(0)
+    s = _lib.lsm_range(h, d_k1, d_k2, nq, d_offsets, d_keys, d_vals, capacity, ctypes.byref(total), stream)
+    if s not in (LSM_OK, LSM_ERR_CAPACITY):
+        raise LSMError(s, "lsm_range")
+    return s, total.value
+
+
+def lsm_cleanup(h, stream=None):
+    return _check(_lib.lsm_cleanup(h, stream), "lsm_cleanup")
+
+
+def lsm_stats(h):
+    r, res, b, lv = _u64(), _u64(), _u32(), _u32()
+    _check(_lib.lsm_stats(h, ctypes.byref(r), ctypes.byref(res), ctypes.byref(b), ctypes.byref(lv)), "lsm_stats")
+    return dict(r=r.value, resident=res.value, b=b.value, levels=lv.value)
+
+
+def lsm_level_offset(h, i):
+    off, size = _u64(), _u64()
+    _check(_lib.lsm_level_offset(h, i, ctypes.byref(off), ctypes.byref(size)), "lsm_level_offset")
+    return off.value, size.value
+
+
+def lsm_capacity(h):
+    return _lib.lsm_capacity(h)
+
+
+def lsm_dump_levels(h, h_keys, h_vals, stream=None):
+    return _check(_lib.lsm_dump_levels(h, h_keys, h_vals, stream), "lsm_dump_levels")
+
+
+def lsm_sort_pairs(h, d_kin, d_vin, d_kout, d_vout, n, stream=None):
+    return _check(_lib.lsm_sort_pairs(h, d_kin, d_vin, d_kout, d_vout, n, stream), "lsm_sort_pairs")
+
+
+def lsm_set_option(h, opt, value):
+    return _check(_lib.lsm_set_option(h, opt, value), "lsm_set_option")
+
+
+def lsm_get_option(h, opt):
+    v = _i64()
+    _check(_lib.lsm_get_option(h, opt, ctypes.byref(v)), "lsm_get_option")
+    return v.value
+
+
+# --------------------------------------------------------------------------
+# torch convenience layer
+# --------------------------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _stream(device):
+    return _torch().cuda.current_stream(device).cuda_stream
+
+
+def as_device_u32(a, device):
+    """numpy uint32 (or any int array) -> int32 CUDA tensor with the same bits."""
+    import numpy as np
+    torch = _torch()
+    if isinstance(a, torch.Tensor):
+        return a.to(device=device).contiguous()
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.uint32)).view(np.int32)
+    return torch.from_numpy(arr.copy()).to(device)
+
+
+def as_device_u8(a, device):
+    import numpy as np
+    torch = _torch()
+    if isinstance(a, torch.Tensor):
+        return a.to(device=device, dtype=torch.uint8).contiguous()
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.uint8)).copy()).to(device)
+
+
+def to_numpy_u32(t):
+    import numpy as np
+    return t.cpu().numpy().view(np.uint32)
+
+
+class LSM:
+    """A GPU LSM dictionary on one CUDA device (batch size b)."""
+
+    def __init__(self, b, max_elements, device=0):
+        self.device = device
+        self.b = b
+        self.h = lsm_create(b, max_elements, device)
+
+    def close(self):
+        if self.h:
+            lsm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # updates -------------------------------------------------------------
+    def insert(self, keys, vals):
+        k, v = as_device_u32(keys, self.device), as_device_u32(vals, self.device)
+        lsm_insert_batch(self.h, _ptr(k), _ptr(v), k.numel(), _stream(self.device))
+
+    def delete(self, keys):
+        k = as_device_u32(keys, self.device)
+        lsm_delete_batch(self.h, _ptr(k), k.numel(), _stream(self.device))
+
+    def update(self, keys, vals, is_delete):
+        k, v = as_device_u32(keys, self.device), as_device_u32(vals, self.device)
+        d = as_device_u8(is_delete, self.device)
+        lsm_update_batch(self.h, _ptr(k), _ptr(v), _ptr(d), k.numel(), _stream(self.device))
+
+    def call(self, kind, keys, vals=None, is_delete=None):
+        if kind == "insert":
+            self.insert(keys, vals)
+        elif kind == "delete":
+            self.delete(keys)
+        elif kind == "update":
+            self.update(keys, vals, is_delete)
+        else:
+            raise ValueError(kind)
+
+    def cleanup(self):
+        lsm_cleanup(self.h, _stream(self.device))
+
+    # queries -------------------------------------------------------------
+    def lookup(self, q):
+        torch = _torch()
+        qd = as_device_u32(q, self.device)
+        n = qd.numel()
+        val = torch.empty(n, dtype=torch.int32, device=self.device)
+        found = torch.empty(n, dtype=torch.uint8, device=self.device)
+        lsm_lookup(self.h, _ptr(qd), n, _ptr(val), _ptr(found), _stream(self.device))
+        return val, found
+
+    def count(self, k1, k2):
+        torch = _torch()
+        a, z = as_device_u32(k1, self.device), as_device_u32(k2, self.device)
+        out = torch.empty(a.numel(), dtype=torch.int32, device=self.device)
+        lsm_count(self.h, _ptr(a), _ptr(z), a.numel(), _ptr(out), _stream(self.device))
+        return out
+
+    def range(self, k1, k2, capacity=None):
+        """(offsets int64[nq+1], keys int32[total], vals int32[total]); grows
+        the output buffers and retries once on LSM_ERR_CAPACITY."""
+        torch = _torch()
+        a, z = as_device_u32(k1, self.device), as_device_u32(k2, self.device)
+        nq = a.numel()
+        off = torch.empty(nq + 1, dtype=torch.int64, device=self.device)
+        cap = max(1, capacity if capacity is not None else 8 * nq)
+        for _ in range(2):
+            ok = torch.empty(cap, dtype=torch.int32, device=self.device)
+            ov = torch.empty(cap, dtype=torch.int32, device=self.device)
+            s, total = lsm_range(self.h, _ptr(a), _ptr(z), nq, _ptr(off), _ptr(ok), _ptr(ov), cap,
+                                 _stream(self.device))
+            if s == LSM_OK:
+                return off, ok[:total], ov[:total]
+            cap = max(1, total)
+        raise LSMError(LSM_ERR_CAPACITY, "range")
+
+    # state ---------------------------------------------------------------
+    def stats(self):
+        return lsm_stats(self.h)
+
+    @property
+    def r(self):
+        return self.stats()["r"]
+
+    def levels(self):
+        """Host copy of every full level: {i: (key variables, values)} as uint32."""
+        import numpy as np
+        cap = lsm_capacity(self.h)
+        hk = np.zeros(cap, np.uint32)
+        hv = np.zeros(cap, np.uint32)
+        lsm_dump_levels(self.h, hk.ctypes.data, hv.ctypes.data, _stream(self.device))
+        r = self.r
+        out = {}
+        for i in range(self.stats()["levels"]):
+            if (r >> i) & 1:
+                off, size = lsm_level_offset(self.h, i)
+                out[i] = (hk[off:off + size].copy(), hv[off:off + size].copy())
+        return out
+
+    def set_lookup_mode(self, mode):
+        lsm_set_option(self.h, LSM_OPT_LOOKUP_MODE, mode)
+
+    def device_errors(self):
+        return lsm_get_option(self.h, LSM_OPT_DEVICE_ERROR)

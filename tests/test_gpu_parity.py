@@ -1,0 +1,303 @@
+"""Parity of the CUDA path with the CPU oracle (needs a GPU).
+
+Every comparison is exact (integer work): level contents against the
+structural oracle S, query answers against the ordered-map oracle O1 (or the
+offline oracle O2 at full size).  All calls go through the C ABI via the
+ctypes binding.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1707_05354_gb300 import workload
+from tests.walkthrough import parse
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def g(lsm_lib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return lsm_lib
+
+
+def u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def assert_levels(lsm, s):
+    lv = lsm.levels()
+    assert lsm.r == s.r
+    for i in range(40):
+        ekv, ev = s.level(i)
+        if len(ekv):
+            assert i in lv, "level %d missing" % i
+            np.testing.assert_array_equal(lv[i][0], ekv, err_msg="keys of level %d" % i)
+            np.testing.assert_array_equal(lv[i][1], ev, err_msg="values of level %d" % i)
+        else:
+            assert i not in lv
+
+
+def assert_queries(lsm, o1, q, k1, k2):
+    val, found = lsm.lookup(q)
+    ev, ef = o1.lookup(q)
+    np.testing.assert_array_equal(found.cpu().numpy(), ef)
+    np.testing.assert_array_equal(u32(val), ev)
+    np.testing.assert_array_equal(u32(lsm.count(k1, k2)), o1.count(k1, k2))
+    off, rk, rv = lsm.range(k1, k2)
+    eo, ek, evv = o1.range(k1, k2)
+    np.testing.assert_array_equal(off.cpu().numpy().astype(np.uint64), eo)
+    np.testing.assert_array_equal(u32(rk), ek)
+    np.testing.assert_array_equal(u32(rv), evv)
+
+
+# ------------------------------------------------------------------ golden --
+def test_walkthrough_on_gpu(g):
+    b, steps = parse("fig1_walkthrough.txt")
+    lsm = g.LSM(b, 64 * b)
+    for st in steps:
+        if st[0] == "op":
+            _, kind, keys, vals, dels = st
+            lsm.call(kind, keys, vals, dels)
+        elif st[0] == "cleanup":
+            lsm.cleanup()
+        elif st[0] == "r":
+            assert lsm.r == st[1]
+        elif st[0] == "level":
+            lv = lsm.levels()
+            if st[2] is None:
+                assert st[1] not in lv
+            else:
+                np.testing.assert_array_equal(lv[st[1]][0], st[2])
+                np.testing.assert_array_equal(lv[st[1]][1], st[3])
+        elif st[0] == "lookup":
+            val, found = lsm.lookup(st[1])
+            np.testing.assert_array_equal(found.cpu().numpy(), st[3])
+            np.testing.assert_array_equal(u32(val), st[2])
+        elif st[0] == "count":
+            _, k1, k2, n = st
+            assert int(u32(lsm.count([k1], [min(k2, 2**32 - 1)]))[0]) == n
+        elif st[0] == "range":
+            _, k1, k2, pairs = st
+            off, rk, rv = lsm.range([k1], [min(k2, 2**32 - 1)])
+            assert list(zip(u32(rk).tolist(), u32(rv).tolist())) == pairs
+    assert lsm.device_errors() == 0
+
+
+# -------------------------------------------------------------------- sort --
+@pytest.mark.parametrize("n", [1, 2, 31, 4095, 4096, 4097, 12345, 1 << 16, (1 << 20) - 3])
+def test_sort_pairs_matches_stable_sort(g, n):
+    lsm = g.LSM(max(n, 1), max(n, 1))
+    rng = np.random.default_rng(n)
+    if n % 2:
+        keys = rng.integers(0, 2**32, size=n, dtype=np.uint64).astype(np.uint32)
+    else:  # many duplicates: stability matters
+        keys = rng.integers(0, 50, size=n).astype(np.uint32) * np.uint32(0x01010101)
+    vals = np.arange(n, dtype=np.uint32)
+    kd, vd = g.as_device_u32(keys, 0), g.as_device_u32(vals, 0)
+    ko, vo = torch.empty_like(kd), torch.empty_like(vd)
+    g.lsm_sort_pairs(lsm.h, kd.data_ptr(), vd.data_ptr(), ko.data_ptr(), vo.data_ptr(), n,
+                     torch.cuda.current_stream().cuda_stream)
+    order = np.argsort(keys, kind="stable")
+    np.testing.assert_array_equal(u32(ko), keys[order])
+    np.testing.assert_array_equal(u32(vo), vals[order])
+
+
+# ------------------------------------------------------ configuration tiny --
+def test_tiny_configuration_bit_exact(g):
+    cfg = workload.tiny()
+    b = cfg["b"]
+    lsm = g.LSM(b, 64 * b)
+    o1 = oracle.MapOracle(b)
+    s = oracle.StructuralOracle(b)
+    for kind, k, v, d in cfg["calls"]:
+        lsm.call(kind, k, v, d)
+        o1.call(kind, k, v, d)
+        s.call(kind, k, v, d)
+        assert_levels(lsm, s)
+    k1, k2 = cfg["count"]
+    val, found = lsm.lookup(cfg["lookups"])
+    ev, ef = o1.lookup(cfg["lookups"])
+    np.testing.assert_array_equal(found.cpu().numpy(), ef)
+    np.testing.assert_array_equal(u32(val), ev)
+    np.testing.assert_array_equal(u32(lsm.count(k1, k2)), o1.count(k1, k2))
+    r1, r2 = cfg["range"]
+    off, rk, rv = lsm.range(r1, r2)
+    eo, ek, evv = o1.range(r1, r2)
+    np.testing.assert_array_equal(off.cpu().numpy().astype(np.uint64), eo)
+    np.testing.assert_array_equal(u32(rk), ek)
+    np.testing.assert_array_equal(u32(rv), evv)
+    lsm.set_lookup_mode(g.LOOKUP_SORTED)
+    val2, found2 = lsm.lookup(cfg["lookups"])
+    np.testing.assert_array_equal(found2.cpu().numpy(), ef)
+    np.testing.assert_array_equal(u32(val2), ev)
+    lsm.cleanup()
+    s.cleanup()
+    assert_levels(lsm, s)
+    assert_queries(lsm, o1, cfg["lookups"][:5000], k1[:3000], k2[:3000])
+    assert lsm.device_errors() == 0
+
+
+# ------------------------------------------------------- random, many b ---
+def random_calls(rng, b, ncalls, key_space):
+    calls = []
+    for _ in range(ncalls):
+        kind = rng.choice(["insert", "delete", "update", "insert"])
+        n = int(rng.integers(1, b + 1)) if kind == "update" else int(rng.integers(1, 3 * b + 1))
+        keys = rng.integers(0, key_space, size=n).astype(np.uint32)
+        vals = rng.integers(0, 2**32, size=n, dtype=np.uint64).astype(np.uint32)
+        dels = (rng.random(n) < 0.3).astype(np.uint8)
+        calls.append((kind, keys, vals, dels))
+    return calls
+
+
+@pytest.mark.parametrize("b,key_space,ncalls", [(1, 8, 40), (2, 16, 40), (3, 30, 30), (5, 50, 30),
+                                                 (17, 200, 25), (100, 3000, 20), (1000, 1 << 20, 12),
+                                                 (3000, 1 << 12, 12), (4096, (1 << 31) - 1, 10)])
+def test_random_logs_bit_exact(g, b, key_space, ncalls):
+    rng = np.random.default_rng(b * 7919 + key_space)
+    calls = random_calls(rng, b, ncalls, min(key_space, (1 << 31) - 1))
+    nb = sum(-(-len(c[1]) // b) if c[0] != "update" else 1 for c in calls)
+    lsm = g.LSM(b, (nb + 2) * b)
+    o1 = oracle.MapOracle(b)
+    s = oracle.StructuralOracle(b)
+    ks = min(key_space, (1 << 31) - 1)
+    q = np.concatenate([rng.integers(0, ks, size=2000), [0, ks - 1, (1 << 31) - 2, (1 << 31) - 1, 2**32 - 1]])
+    q = q.astype(np.uint32)
+    k1 = rng.integers(0, ks, size=500).astype(np.uint32)
+    k2 = (k1.astype(np.int64) + rng.integers(-3, max(4, ks // 50), size=500)).clip(0, 2**32 - 1).astype(np.uint32)
+    for i, c in enumerate(calls):
+        lsm.call(*c)
+        o1.call(*c)
+        s.call(*c)
+        if i % 4 == 3 or i == len(calls) - 1:
+            assert_levels(lsm, s)
+            assert_queries(lsm, o1, q, k1, k2)
+    lsm.cleanup()
+    s.cleanup()
+    assert_levels(lsm, s)
+    assert_queries(lsm, o1, q, k1, k2)
+    more = random_calls(rng, b, 3, ks)
+    for c in more:
+        lsm.call(*c)
+        o1.call(*c)
+        s.call(*c)
+    assert_levels(lsm, s)
+    assert_queries(lsm, o1, q, k1, k2)
+    assert lsm.device_errors() == 0
+
+
+def test_deep_fold_many_sources(g):
+    """Folds of up to 9 sources over many tiles, b not a multiple of 32."""
+    b = 1000
+    lsm = g.LSM(b, 600 * b)
+    o1 = oracle.MapOracle(b)
+    s = oracle.StructuralOracle(b)
+    rng = np.random.default_rng(5)
+    for t in range(511):
+        keys = rng.integers(0, 1 << 16, size=b).astype(np.uint32)  # heavy duplication
+        vals = np.full(b, t, np.uint32)
+        dels = (rng.random(b) < 0.05).astype(np.uint8)
+        lsm.update(keys, vals, dels)
+        o1.call("update", keys, vals, dels)
+        s.call("update", keys, vals, dels)
+        if t in (6, 62, 255, 510):
+            assert_levels(lsm, s)
+    q = rng.integers(0, 1 << 16, size=20000).astype(np.uint32)
+    k1 = rng.integers(0, 1 << 16, size=2000).astype(np.uint32)
+    assert_queries(lsm, o1, q, k1, k1 + 40)
+    lsm.set_lookup_mode(g.LOOKUP_SORTED)
+    assert_queries(lsm, o1, q, k1, k1 + 40)
+    assert lsm.device_errors() == 0
+
+
+# ------------------------------------------------------------------- edges --
+def test_edges(g):
+    b = 64
+    lsm = g.LSM(b, 3 * b)    # two levels: room for 3 batches
+    empty_q = np.array([0, 5, (1 << 31) - 2], np.uint32)
+    val, found = lsm.lookup(empty_q)
+    assert not found.cpu().numpy().any() and not u32(val).any()
+    assert not u32(lsm.count([0], [2**32 - 1])).any()
+    off, rk, rv = lsm.range([0, 10], [100, 5])
+    assert off.cpu().numpy().tolist() == [0, 0, 0] and rk.numel() == 0
+    lsm.cleanup()                                    # empty: no-op
+    assert lsm.r == 0
+    lsm.insert(np.zeros(0, np.uint32), np.zeros(0, np.uint32))  # n = 0: no-op
+    assert lsm.r == 0
+    # key out of range: error, nothing applied
+    with pytest.raises(g.LSMError) as e:
+        lsm.insert(np.array([1, (1 << 31) - 1], np.uint32), np.array([1, 2], np.uint32))
+    assert e.value.status == g.LSM_ERR_KEY_RANGE
+    assert lsm.r == 0
+    lsm.insert(np.arange(b, dtype=np.uint32), np.arange(b, dtype=np.uint32))
+    assert lsm.r == 1
+    before = lsm.levels()
+    for bad in ([2**32 - 1], [5, 2**31]):
+        with pytest.raises(g.LSMError):
+            lsm.delete(np.array(bad, np.uint32))
+    with pytest.raises(g.LSMError):   # multi-batch call: checked as a whole
+        keys = np.arange(3 * b, dtype=np.uint32)
+        keys[2 * b + 5] = 2**31 + 7
+        lsm.insert(keys, keys)
+    assert lsm.r == 1
+    after = lsm.levels()
+    assert before.keys() == after.keys()
+    np.testing.assert_array_equal(before[0][0], after[0][0])
+    # capacity: 3 batches fit, the 4th does not
+    lsm.insert(np.arange(b, dtype=np.uint32) + 1000, np.ones(b, np.uint32))
+    lsm.insert(np.arange(b, dtype=np.uint32) + 2000, np.ones(b, np.uint32))
+    assert lsm.r == 3
+    with pytest.raises(g.LSMError) as e:
+        lsm.insert(np.arange(b, dtype=np.uint32), np.ones(b, np.uint32))
+    assert e.value.status == g.LSM_ERR_FULL
+    assert lsm.r == 3
+    # update batch larger than b is an argument error
+    with pytest.raises(g.LSMError) as e:
+        lsm.update(np.arange(b + 1, dtype=np.uint32), np.zeros(b + 1, np.uint32), np.zeros(b + 1, np.uint8))
+    assert e.value.status == g.LSM_ERR_ARG
+    # range with too small a buffer: LSM_ERR_CAPACITY with offsets and total
+    a = g.as_device_u32([0], 0)
+    z = g.as_device_u32([100000], 0)
+    offs = torch.empty(2, dtype=torch.int64, device=0)
+    ok = torch.empty(4, dtype=torch.int32, device=0)
+    s, total = g.lsm_range(lsm.h, a.data_ptr(), z.data_ptr(), 1, offs.data_ptr(), ok.data_ptr(),
+                           ok.data_ptr(), 4, torch.cuda.current_stream().cuda_stream)
+    assert s == g.LSM_ERR_CAPACITY and total == 3 * b
+    assert offs.cpu().numpy().tolist() == [0, 3 * b]
+    off, rk, rv = lsm.range([0], [100000], capacity=4)   # retries with the reported total
+    assert rk.numel() == 3 * b
+    # delete everything, then cleanup -> empty
+    lsm2 = g.LSM(b, 8 * b)
+    lsm2.insert(np.arange(b, dtype=np.uint32), np.arange(b, dtype=np.uint32))
+    lsm2.delete(np.arange(b, dtype=np.uint32))
+    lsm2.cleanup()
+    assert lsm2.r == 0
+    assert not u32(lsm2.count([0], [2**31])).any()
+    lsm2.insert(np.array([7], np.uint32), np.array([70], np.uint32))  # padded single op
+    assert lsm2.r == 1
+    val, found = lsm2.lookup([7, 8])
+    assert found.cpu().numpy().tolist() == [1, 0] and u32(val).tolist() == [70, 0]
+    assert lsm.device_errors() == 0 and lsm2.device_errors() == 0
+
+
+def test_max_user_key_and_lookup_mode_agreement(g):
+    b = 256
+    lsm = g.LSM(b, 16 * b)
+    keys = np.array([(1 << 31) - 2, 0, 1, (1 << 30)] * (b // 4), np.uint32)
+    vals = np.arange(b, dtype=np.uint32)
+    lsm.insert(keys, vals)
+    o1 = oracle.MapOracle(b)
+    o1.call("insert", keys, vals)
+    q = np.array([(1 << 31) - 2, (1 << 31) - 1, 2**32 - 1, 0, 1, 2, 1 << 30], np.uint32)
+    for mode in (g.LOOKUP_DIRECT, g.LOOKUP_SORTED, g.LOOKUP_AUTO):
+        lsm.set_lookup_mode(mode)
+        val, found = lsm.lookup(q)
+        ev, ef = o1.lookup(q)
+        np.testing.assert_array_equal(found.cpu().numpy(), ef)
+        np.testing.assert_array_equal(u32(val), ev)
+    assert u32(lsm.count([0], [2**32 - 1])).tolist() == [4]
