@@ -204,11 +204,15 @@ lsm_status lsm_sort_pairs(lsm_t* h, const uint32_t* d_keys_in, const uint32_t* d
  *   LSM_OPT_LOOKUP_MODE  0 = automatic, 1 = one search per query in input
  *                        order, 2 = sort the queries first (§IV-B "bulk").
  *   LSM_OPT_DEVICE_ERROR read-only: sticky device error bits seen so far
- *                        (1 = bad key, 2 = wait timeout); reading clears them.
+ *                        (1 = bad key, 2 = wait timeout, 4 = misaligned
+ *                        copy avoided); synchronises; reading clears them.
+ *   LSM_OPT_KERNEL_LAUNCHES read-only: CUDA kernels launched by the library
+ *                        in this process so far (all handles); h may be NULL.
  */
 typedef enum {
   LSM_OPT_LOOKUP_MODE = 1,
-  LSM_OPT_DEVICE_ERROR = 2
+  LSM_OPT_DEVICE_ERROR = 2,
+  LSM_OPT_KERNEL_LAUNCHES = 3
 } lsm_option;
 
 lsm_status lsm_set_option(lsm_t* h, lsm_option opt, int64_t value);

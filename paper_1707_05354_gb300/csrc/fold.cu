@@ -342,6 +342,7 @@ cudaError_t fold_partition_launch(const FoldArgs& a, cudaStream_t st) {
   const uint64_t ntiles = fold_tiles(a.total);
   if (ntiles == 0) return cudaSuccess;
   const uint64_t pblocks = ((ntiles + 1) * 32 + 255) / 256;
+  count_launches(1);
   fold_partition<<<unsigned(pblocks), 256, 0, st>>>(a.src, a.total, uint32_t(ntiles), a.part);
   return cudaGetLastError();
 }
@@ -366,10 +367,12 @@ cudaError_t fold_merge_launch(const FoldArgs& a, cudaStream_t st) {
   if (a.cleanup) {
     if ((e = cudaMemsetAsync(a.lookback, 0, sizeof(uint64_t) * ntiles, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(a.tile_ctr, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+    count_launches(1);
     fold_merge<true><<<unsigned(ntiles), kThreads, kMergeSmem, st>>>(
         a.src, a.total, a.part, a.out_keys, a.out_vals, a.status, a.lookback, a.tile_ctr, a.out_count,
         uint32_t(ntiles));
   } else {
+    count_launches(1);
     fold_merge<false><<<unsigned(ntiles), kThreads, kMergeSmem, st>>>(
         a.src, a.total, a.part, a.out_keys, a.out_vals, a.status, nullptr, nullptr, nullptr,
         uint32_t(ntiles));
@@ -387,6 +390,7 @@ cudaError_t distribute_launch(const DistributeArgs& a, cudaStream_t st) {
   if (a.total == 0) return cudaSuccess;
   uint64_t blocks = (a.total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
+  count_launches(1);
   distribute<<<unsigned(blocks), 256, 0, st>>>(a);
   return cudaGetLastError();
 }

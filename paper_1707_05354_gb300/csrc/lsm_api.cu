@@ -4,6 +4,7 @@
 // is set, and an update batch lands in level ffz(r).  All device work is
 // enqueued on the caller's stream; the host waits only where the interface
 // says so (the key check of an update, the totals of range and cleanup).
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -13,6 +14,12 @@
 #include "lsm_kernels.h"
 
 using namespace gpulsm;
+
+namespace gpulsm {
+static std::atomic<uint64_t> g_launches{0};
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace gpulsm
 
 struct lsm_t {
   int device = 0;
@@ -616,6 +623,10 @@ lsm_status lsm_set_option(lsm_t* h, lsm_option opt, int64_t value) {
 }
 
 lsm_status lsm_get_option(lsm_t* h, lsm_option opt, int64_t* value) {
+  if (value && opt == LSM_OPT_KERNEL_LAUNCHES) {  // process-wide, no handle needed
+    *value = int64_t(launches_so_far());
+    return LSM_OK;
+  }
   if (!h || !value) return LSM_ERR_ARG;
   if (opt == LSM_OPT_LOOKUP_MODE) {
     *value = h->lookup_mode;

@@ -7,6 +7,11 @@
 
 namespace gpulsm {
 
+// Number of kernels this library has launched (all handles); read through
+// LSM_OPT_KERNEL_LAUNCHES.  Incremented by every launcher below.
+void count_launches(uint64_t n);
+uint64_t launches_so_far();
+
 constexpr int kMaxLevels = 32;                 // levels a handle may allocate
 constexpr int kMaxSources = kMaxLevels + 1;    // fold: the batch + every level
 constexpr uint32_t kMaxUserKey = 0x7FFFFFFEu;  // 2^31 - 2

@@ -330,6 +330,7 @@ cudaError_t lookup_launch(const LevelSet& ls, const uint32_t* q, uint64_t nq, ui
   if (nq == 0) return cudaSuccess;
   const int per = splitters_per_level(ls.count);
   const size_t smem = size_t(per) * (ls.count ? ls.count : 1) * sizeof(uint32_t);
+  count_launches(1);
   lookup_direct<<<persistent_grid(nq, kThreads, 152 * 6), kThreads, smem, st>>>(ls, per, q, nq, val, found);
   return cudaGetLastError();
 }
@@ -339,6 +340,7 @@ cudaError_t lookup_sorted_launch(const LevelSet& ls, const uint32_t* sq, const u
   if (nq == 0) return cudaSuccess;
   const int per = splitters_per_level(ls.count);
   const size_t smem = size_t(per) * (ls.count ? ls.count : 1) * sizeof(uint32_t);
+  count_launches(1);
   lookup_sorted<<<persistent_grid(nq, kThreads, 152 * 6), kThreads, smem, st>>>(ls, per, sq, idx, nq, val,
                                                                                found);
   return cudaGetLastError();
@@ -347,6 +349,7 @@ cudaError_t lookup_sorted_launch(const LevelSet& ls, const uint32_t* sq, const u
 cudaError_t count_launch(const LevelSet& ls, const uint32_t* k1, const uint32_t* k2, uint64_t nq,
                          uint32_t* count, uint32_t* bounds, cudaStream_t st) {
   if (nq == 0) return cudaSuccess;
+  count_launches(1);
   count_kernel<<<persistent_grid(nq, kThreads, 152 * 8), kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds);
   return cudaGetLastError();
 }
@@ -358,6 +361,7 @@ cudaError_t scan_launch(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t*
   const uint64_t ntiles = scan_tiles(n);
   if ((e = cudaMemsetAsync(lookback, 0, sizeof(uint64_t) * ntiles, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(tile_ctr, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+  count_launches(1);
   scan_kernel<<<unsigned(ntiles), kThreads, 0, st>>>(in, n, out, lookback, tile_ctr, status, ntiles);
   return cudaGetLastError();
 }
@@ -365,6 +369,7 @@ cudaError_t scan_launch(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t*
 cudaError_t range_emit_launch(const LevelSet& ls, uint64_t nq, const uint32_t* bounds, const uint64_t* offsets,
                               uint32_t* keys, uint32_t* vals, cudaStream_t st) {
   if (nq == 0) return cudaSuccess;
+  count_launches(1);
   range_emit<<<persistent_grid(nq, kThreads, 152 * 8), kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals);
   return cudaGetLastError();
 }

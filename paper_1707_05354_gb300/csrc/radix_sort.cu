@@ -249,6 +249,7 @@ cudaError_t sort_launch(const SortArgs& a, SortWorkspace& ws, cudaStream_t st, u
   Loader ld{a.mode, a.in_keys, a.in_vals, a.in_del, a.n_in, a.n};
   uint32_t hblocks = (a.n + 255) / 256;
   if (hblocks > 4 * 152) hblocks = 4 * 152;
+  count_launches(1);
   sort_histogram<<<hblocks, 256, 0, st>>>(ld, ws.ctl);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (h_status) {
@@ -260,10 +261,12 @@ cudaError_t sort_launch(const SortArgs& a, SortWorkspace& ws, cudaStream_t st, u
   uint32_t* bk[2] = {a.tmp_keys, a.out_keys};
   uint32_t* bv[2] = {a.tmp_vals, a.out_vals};
   const size_t lb_stride = size_t(ws.max_tiles) * kRadix;
+  count_launches(1);
   sort_pass<true><<<ntiles, kThreads, 0, st>>>(ld, nullptr, nullptr, bk[0], bv[0], ws.ctl, ws.lookback,
                                                 0, ws.epoch, ws.sticky);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int p = 1; p < kSortPasses; ++p) {
+    count_launches(1);
     sort_pass<false><<<ntiles, kThreads, 0, st>>>(ld, bk[(p - 1) & 1], bv[(p - 1) & 1], bk[p & 1],
                                                    bv[p & 1], ws.ctl, ws.lookback + p * lb_stride, p,
                                                    ws.epoch, ws.sticky);
@@ -276,6 +279,7 @@ cudaError_t check_keys_launch(const uint32_t* keys, uint64_t n, uint32_t* status
   if (n == 0) return cudaSuccess;
   uint64_t blocks = (n + 255) / 256;
   if (blocks > 8 * 152) blocks = 8 * 152;
+  count_launches(1);
   check_keys<<<unsigned(blocks), 256, 0, st>>>(keys, n, status);
   return cudaGetLastError();
 }

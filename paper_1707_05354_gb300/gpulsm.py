@@ -29,8 +29,14 @@ STATUS = {0: "LSM_OK", 1: "LSM_ERR_ARG", 2: "LSM_ERR_KEY_RANGE", 3: "LSM_ERR_FUL
           5: "LSM_ERR_BUDGET", 6: "LSM_ERR_CAPACITY", 7: "LSM_ERR_CUDA", 8: "LSM_ERR_TIMEOUT"}
 LSM_OK, LSM_ERR_ARG, LSM_ERR_KEY_RANGE, LSM_ERR_FULL = 0, 1, 2, 3
 LSM_ERR_OOM, LSM_ERR_BUDGET, LSM_ERR_CAPACITY, LSM_ERR_CUDA, LSM_ERR_TIMEOUT = 4, 5, 6, 7, 8
-LSM_OPT_LOOKUP_MODE, LSM_OPT_DEVICE_ERROR = 1, 2
+LSM_OPT_LOOKUP_MODE, LSM_OPT_DEVICE_ERROR, LSM_OPT_KERNEL_LAUNCHES = 1, 2, 3
 LOOKUP_AUTO, LOOKUP_DIRECT, LOOKUP_SORTED = 0, 1, 2
+PROF_GROUPS = ("sort", "partition", "merge", "lookup", "count", "emit", "cleanup")
+
+
+class ProfileEntry(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
 
 _vp, _u64, _u32, _i32, _i64 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int64
 _SIGS = {
@@ -52,6 +58,9 @@ _SIGS = {
     "lsm_sort_pairs": ([_vp, _vp, _vp, _vp, _vp, _u64, _vp], _i32),
     "lsm_set_option": ([_vp, _i32, _i64], _i32),
     "lsm_get_option": ([_vp, _i32, ctypes.POINTER(_i64)], _i32),
+    "lsm_reset": ([_vp], _i32),
+    "lsm_profile": ([_vp, _i32], _i32),
+    "lsm_profile_read": ([_vp, ctypes.POINTER(ProfileEntry)], _i32),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -151,6 +160,29 @@ def lsm_set_option(h, opt, value):
 def lsm_get_option(h, opt):
     v = _i64()
     _check(_lib.lsm_get_option(h, opt, ctypes.byref(v)), "lsm_get_option")
+    return v.value
+
+
+def lsm_reset(h):
+    return _check(_lib.lsm_reset(h), "lsm_reset")
+
+
+def lsm_profile(h, enable):
+    return _check(_lib.lsm_profile(h, 1 if enable else 0), "lsm_profile")
+
+
+def lsm_profile_read(h):
+    """{group name: dict(launches, ms, bytes)} accumulated since lsm_profile(h, 1)."""
+    arr = (ProfileEntry * len(PROF_GROUPS))()
+    _check(_lib.lsm_profile_read(h, arr), "lsm_profile_read")
+    return {n: dict(launches=int(e.launches), ms=float(e.ms), bytes=float(e.bytes))
+            for n, e in zip(PROF_GROUPS, arr)}
+
+
+def kernel_launches():
+    """Kernels launched by the library in this process (all handles)."""
+    v = _i64()
+    _check(_lib.lsm_get_option(None, LSM_OPT_KERNEL_LAUNCHES, ctypes.byref(v)), "lsm_get_option")
     return v.value
 
 
