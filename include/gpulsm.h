@@ -200,6 +200,32 @@ lsm_status lsm_sort_pairs(lsm_t* h, const uint32_t* d_keys_in, const uint32_t* d
                           void* stream);
 
 /*
+ * lsm_sort_pairs_noalloc - the same stable radix sort as lsm_sort_pairs, for
+ * callers that must not allocate device memory while they run (for example a
+ * process whose device memory all comes from its own pool and which forbids
+ * raw cudaMalloc, or a latency-bound loop that cannot take the device-wide
+ * synchronisation and unbounded time of a cudaMalloc/cudaFree).  No handle
+ * is needed and nothing is allocated: every byte of scratch comes from one
+ * fixed array with static storage inside the library (about 10.5 MB), which
+ * each GPU that loads the library keeps until the process exits.
+ *   n        at most LSM_SORT_NOALLOC_MAX_PAIRS; larger n is refused with
+ *            LSM_ERR_CAPACITY before any work is queued.  n = 0 is a no-op.
+ *   inputs/outputs as for lsm_sort_pairs (device memory on the current
+ *            device, outputs must not overlap the inputs).  Asynchronous on
+ *            `stream`, which must belong to the current device.
+ * The first call on a device looks up that device's copy of the array and
+ * clears it (queued on `stream`); make that first call before capturing
+ * `stream` into anything.  All calls on a device share the one array, which
+ * keeps the last call's contents; calls whose work overlaps on the GPU (two
+ * streams at once) race on it and must be ordered by the caller.
+ * The paper has no counterpart: this entry point exists for the callers above.
+ */
+#define LSM_SORT_NOALLOC_MAX_PAIRS (1u << 20)
+lsm_status lsm_sort_pairs_noalloc(const uint32_t* d_keys_in, const uint32_t* d_vals_in,
+                                  uint32_t* d_keys_out, uint32_t* d_vals_out, uint64_t n,
+                                  void* stream);
+
+/*
  * lsm_set_option / lsm_get_option - tuning knobs (integers):
  *   LSM_OPT_LOOKUP_MODE  0 = automatic, 1 = one search per query in input
  *                        order, 2 = sort the queries first (§IV-B "bulk").

@@ -285,3 +285,104 @@ cudaError_t check_keys_launch(const uint32_t* keys, uint64_t n, uint32_t* status
 }
 
 }  // namespace gpulsm
+
+// ---------------------------------------------------------------------------
+// Allocation-free batch sort (lsm_sort_pairs_noalloc in gpulsm.h).
+//
+// Some callers may not allocate device memory once they are running: a
+// process whose memory is handed out by its own pool allocator and forbids
+// raw cudaMalloc, or a latency-bound loop that cannot afford the implicit
+// device-wide synchronisation and the unbounded time a cudaMalloc/cudaFree
+// may take.  For them the sort below takes all of its scratch (ping-pong
+// buffers, histograms, look-back words) from one fixed array with static
+// storage in this file, which every GPU that loads the library holds until
+// the process exits.  Its size is set by kNoAllocMaxPairs.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+#include "gpulsm.h"
+
+namespace gpulsm {
+namespace {
+
+constexpr uint32_t kNoAllocMaxPairs = LSM_SORT_NOALLOC_MAX_PAIRS;
+constexpr uint32_t kNoAllocTiles = (kNoAllocMaxPairs + kSortTile - 1) / kSortTile;
+constexpr size_t kNoAllocCtl = 1088;                    // >= kSortCtlWords, multiple of 64
+constexpr size_t kNoAllocSticky = kNoAllocCtl - 1;      // last ctl word: wait timeouts
+constexpr size_t kNoAllocTmpK = kNoAllocCtl;
+constexpr size_t kNoAllocTmpV = kNoAllocTmpK + kNoAllocMaxPairs;
+constexpr size_t kNoAllocLookback = kNoAllocTmpV + kNoAllocMaxPairs;   // u64 words from here
+constexpr size_t kNoAllocLookbackWords = size_t(kSortPasses) * kNoAllocTiles * 256;
+constexpr size_t kNoAllocWords = kNoAllocLookback + 2 * kNoAllocLookbackWords;
+static_assert(kNoAllocCtl > size_t(kSortCtlWords), "control block fits");
+static_assert(kNoAllocLookback % 2 == 0, "look-back words 8-byte aligned");
+
+// The scratch itself: about 10.5 MB for kNoAllocMaxPairs = 2^20.
+static __device__ __align__(256) uint32_t g_sort_scratch[kNoAllocWords];
+
+constexpr int kNoAllocMaxDevices = 64;
+struct NoAllocDevice {
+  uint32_t* base = nullptr;  // device address of g_sort_scratch on this device
+  SortWorkspace ws{};
+};
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc[kNoAllocMaxDevices];
+
+}  // namespace
+}  // namespace gpulsm
+
+extern "C" lsm_status lsm_sort_pairs_noalloc(const uint32_t* d_keys_in, const uint32_t* d_vals_in,
+                                             uint32_t* d_keys_out, uint32_t* d_vals_out, uint64_t n,
+                                             void* stream) {
+  using namespace gpulsm;
+  if (n > kNoAllocMaxPairs) return LSM_ERR_CAPACITY;
+  if (n && (!d_keys_in || !d_vals_in || !d_keys_out || !d_vals_out)) return LSM_ERR_ARG;
+  if (n == 0) return LSM_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+    cudaGetLastError();
+    return LSM_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  NoAllocDevice& d = g_noalloc[dev];
+  if (!d.base) {
+    // Once per device, with that device current: the host needs the array's
+    // device address (its name in host code is only a host-side stand-in),
+    // and the look-back words must start at zero.
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return LSM_ERR_CUDA;
+    }
+    uint32_t* base = static_cast<uint32_t*>(p);
+    if (cudaMemsetAsync(base, 0, kNoAllocWords * sizeof(uint32_t), st) != cudaSuccess) {
+      cudaGetLastError();
+      return LSM_ERR_CUDA;
+    }
+    d.ws.ctl = base;
+    d.ws.lookback = reinterpret_cast<uint64_t*>(base + kNoAllocLookback);
+    d.ws.max_tiles = kNoAllocTiles;
+    d.ws.epoch = 0;
+    d.ws.sticky = base + kNoAllocSticky;
+    d.base = base;
+  }
+  SortArgs a{};
+  a.mode = kSortPairs;
+  a.in_keys = d_keys_in;
+  a.in_vals = d_vals_in;
+  a.n_in = n;
+  a.n = uint32_t(n);
+  a.out_keys = d_keys_out;
+  a.out_vals = d_vals_out;
+  a.tmp_keys = d.base + kNoAllocTmpK;
+  a.tmp_vals = d.base + kNoAllocTmpV;
+  // sort_launch clears the histogram/counter block itself on every call and
+  // tags look-back words with a per-call epoch, so nothing else needs zeroing.
+  cudaError_t e = sort_launch(a, d.ws, st, nullptr, nullptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return LSM_ERR_CUDA;
+  }
+  return LSM_OK;
+}

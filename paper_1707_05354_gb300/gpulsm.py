@@ -61,7 +61,9 @@ _SIGS = {
     "lsm_reset": ([_vp], _i32),
     "lsm_profile": ([_vp, _i32], _i32),
     "lsm_profile_read": ([_vp, ctypes.POINTER(ProfileEntry)], _i32),
+    "lsm_sort_pairs_noalloc": ([_vp, _vp, _vp, _vp, _u64, _vp], _i32),
 }
+SORT_NOALLOC_MAX_PAIRS = 1 << 20
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
@@ -161,6 +163,13 @@ def lsm_get_option(h, opt):
     v = _i64()
     _check(_lib.lsm_get_option(h, opt, ctypes.byref(v)), "lsm_get_option")
     return v.value
+
+
+def lsm_sort_pairs_noalloc(d_kin, d_vin, d_kout, d_vout, n, stream=None):
+    """Allocation-free sort (no handle); raises LSMError(LSM_ERR_CAPACITY) for
+    n > SORT_NOALLOC_MAX_PAIRS."""
+    return _check(_lib.lsm_sort_pairs_noalloc(d_kin, d_vin, d_kout, d_vout, n, stream),
+                  "lsm_sort_pairs_noalloc")
 
 
 def lsm_reset(h):
