@@ -206,7 +206,7 @@ lsm_status lsm_sort_pairs(lsm_t* h, const uint32_t* d_keys_in, const uint32_t* d
  * raw cudaMalloc, or a latency-bound loop that cannot take the device-wide
  * synchronisation and unbounded time of a cudaMalloc/cudaFree).  No handle
  * is needed and nothing is allocated: every byte of scratch comes from one
- * fixed array with static storage inside the library (about 10.5 MB), which
+ * fixed array with static storage inside the library (about 11 MB), which
  * each GPU that loads the library keeps until the process exits.
  *   n        at most LSM_SORT_NOALLOC_MAX_PAIRS; larger n is refused with
  *            LSM_ERR_CAPACITY before any work is queued.  n = 0 is a no-op.

@@ -82,6 +82,7 @@ def _load():
     lib.s_level.argtypes = [vp, i32, vp, vp, vp]
     lib.o2_build.argtypes = [vp, vp, vp, vp, u64, vp, vp]
     lib.o2_build.restype = u64
+    lib.o2_single_level.argtypes = [vp, vp, vp, vp, u64, vp, vp]
     _lib = lib
     return lib
 
@@ -283,3 +284,30 @@ class OfflineOracle:
         total = int(off[-1])
         idx = np.arange(total, dtype=np.int64) + np.repeat(lo - off[:-1], cnt)
         return off.astype(np.uint64), self.keys[idx], self.vals[idx]
+
+
+def single_level(calls, b):
+    """Closed-form contents of the one full level when the number of resident
+    batches is a power of two (and no cleanup happened): (key variables,
+    values) sorted by key, newer batch first, tombstone first, later op first.
+    ``calls`` as for OfflineOracle.from_calls; short batches are padded."""
+    lib = _load()
+    ks, vs, ds, bs = [], [], [], []
+    t = 0
+    for kind, keys, vals, is_delete in calls:
+        for k, v, d in split_call(kind, keys, vals, b, is_delete):
+            n = len(k)
+            idx = np.minimum(np.arange(b), n - 1)   # pad with copies of op n-1
+            ks.append(k[idx])
+            vs.append(v[idx])
+            ds.append(d[idx])
+            bs.append(np.full(b, t, np.uint32))
+            t += 1
+    assert t and (t & (t - 1)) == 0, "resident batches must be a power of two"
+    keys, vals = _u32(np.concatenate(ks)), _u32(np.concatenate(vs))
+    dels, bt = _u8(np.concatenate(ds)), _u32(np.concatenate(bs))
+    n = len(keys)
+    kv = np.empty(n, np.uint32)
+    v = np.empty(n, np.uint32)
+    lib.o2_single_level(_p(keys), _p(vals), _p(dels), _p(bt), n, _p(kv), _p(v))
+    return kv, v

@@ -311,4 +311,28 @@ uint64_t o2_build(const uint32_t* keys, const uint32_t* vals,
   return out;
 }
 
+// Closed form of a single full level.  When r is a power of two, every
+// resident batch sits in level log2(r), and Fig. 2(a) / Fig. 3 make its order
+//   key ascending; newer batch first (§III-B); inside a batch the stable sort
+//   of the reversed input on the key variable (tombstone first, then the
+//   later op first).
+// Input: the padded ops of every batch in arrival order (batch number per op),
+// output: the level's key variables and values.
+void o2_single_level(const uint32_t* keys, const uint32_t* vals, const uint8_t* is_del,
+                     const uint32_t* batch, uint64_t n, uint32_t* out_kv, uint32_t* out_v) {
+  std::vector<Op> ops(n);
+  for (uint64_t i = 0; i < n; ++i)
+    ops[i] = Op{keys[i], batch[i], uint32_t(i), vals ? vals[i] : 0u, is_del[i]};
+  std::sort(ops.begin(), ops.end(), [](const Op& x, const Op& y) {
+    if (x.key != y.key) return x.key < y.key;
+    if (x.batch != y.batch) return x.batch > y.batch;
+    if (x.del != y.del) return x.del > y.del;
+    return x.pos > y.pos;
+  });
+  for (uint64_t i = 0; i < n; ++i) {
+    out_kv[i] = key_variable(ops[i].key, ops[i].del != 0);
+    out_v[i] = ops[i].del ? 0u : ops[i].val;
+  }
+}
+
 }  // extern "C"

@@ -12,14 +12,20 @@
 //
 //   fold_partition  one warp per output tile boundary p = t * 4096 finds the
 //                   co-rank vector (how many elements of each source precede
-//                   position p) by bisection over the 31-bit key space, each
-//                   lane keeping a shrinking bracket in its own source, then
-//                   splits the tied key among the sources in rank order.
+//                   position p).  The sources' prefix indexes (fences) give
+//                   the 2^15-key bin holding the p-th element in a few probes;
+//                   a bisection over the low 15 key bits inside that bin,
+//                   each lane keeping a bracket in its own source, finds the
+//                   key; the elements of that key are then split among the
+//                   sources in rank order.
 //   fold_merge      one CTA per tile: the TMA engine copies the k + 1 source
-//                   segments into shared memory (16-byte aligned supersets),
-//                   a tree of pairwise merge-path merges in shared memory
-//                   combines adjacent ranks (ties to the lower rank), and the
-//                   tile is written out with 16-byte stores.
+//                   segments into shared memory (16-byte aligned supersets);
+//                   a left-deep chain of merge-path merges in shared memory
+//                   (ranks 0 and 1, then the result with rank 2, ...; ties to
+//                   the lower rank) builds the tile as (key, value) pairs in
+//                   an XOR-swizzled layout, and the tile is written out
+//                   coalesced.  The plain fold also writes the new level's
+//                   prefix index.
 // Cleanup uses the same two kernels over all full levels; the merge then keeps
 // only the first element of every key when it is regular and compacts the
 // survivors with a decoupled look-back scan across tiles.
@@ -29,12 +35,25 @@ namespace gpulsm {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kE = kFoldTile / kThreads;                       // outputs per thread per round
-constexpr uint32_t kCap = kFoldTile + 8 * kMaxSources;          // per buffer, with alignment slack
-static_assert(kCap % 4 == 0, "16-byte aligned buffers");
-constexpr size_t kMergeSmem = 4 * size_t(kCap) * sizeof(uint32_t);
+constexpr uint32_t kMinPer = 8;
+constexpr uint32_t kSlotCap = (kFoldTile + 8 * kMaxSources + 15) / 16 * 16;  // TMA slots + alignment slack
+static_assert(kSlotCap % 16 == 0, "16-byte aligned buffers");
+static_assert(kFoldTile % kThreads == 0 && kFoldTile / kThreads <= 32, "keep bits per thread");
+constexpr size_t kMergeSmem = 2 * size_t(kSlotCap) * sizeof(uint32_t) + 2 * size_t(kFoldTile) * sizeof(uint2);
 
 constexpr uint64_t kLbAgg = 1ull << 62, kLbIncl = 2ull << 62, kLbMask = (1ull << 62) - 1;
+
+// Slot of pair q of a merge step in shared memory: q with its low 4 bits
+// XORed by bits 4..7.  A thread writing 8 consecutive pairs (q = 8 t + e)
+// then hits pair slot 8 (t & 1) + (e ^ (t >> 1)) modulo 16: the 16 lanes of
+// each half-warp phase of a 64-bit access use 16 different bank pairs, and 16
+// consecutive pairs stay a permutation of one 128-byte row.
+__device__ __forceinline__ uint32_t psw(uint32_t q) { return q ^ ((q >> 4) & 15u); }
+
+// Sum over the sources of fence_j[P] (lanes >= S contribute 0).
+__device__ __forceinline__ uint64_t fence_sum(const uint32_t* f, bool act, uint32_t P) {
+  return warp_sum<uint64_t>(act ? __ldg(f + P) : 0u);
+}
 
 __global__ void __launch_bounds__(256) fold_partition(FoldSources src, uint64_t total, uint32_t ntiles,
                                                       uint32_t* __restrict__ part) {
@@ -45,15 +64,48 @@ __global__ void __launch_bounds__(256) fold_partition(FoldSources src, uint64_t 
   const bool act = lane < uint32_t(S);
   const uint32_t n = act ? src.n[lane] : 0u;
   const uint32_t* a = act ? src.keys[lane] : nullptr;
+  const uint32_t* f = act ? src.fence[lane] : nullptr;
   const uint64_t p = uint64_t(t) * kFoldTile < total ? uint64_t(t) * kFoldTile : total;
   uint32_t* out = part + uint64_t(t) * S;
   if (p >= total) {
     if (act) out[lane] = n;
     return;
   }
-  // Smallest key x with #{elements with key <= x} > p.  Invariant per lane:
-  // blo = #{key <= xlo - 1}, bhi = #{key <= xhi} in this lane's source.
-  uint32_t blo = 0, bhi = n, xlo = 0, xhi = 0x7FFFFFFFu;
+  // 1. The bin: largest P with C(P) <= p, C(P) = sum of fence_j[P]
+  //    (C(0) = 0 <= p < C(65536) = total).  Start from the proportional
+  //    guess, gallop to a bracket, then bisect.
+  uint32_t lo, hi;
+  {
+    uint32_t g = uint32_t((p * kFenceBins) / total);
+    if (g >= kFenceBins) g = kFenceBins - 1;
+    if (fence_sum(f, act, g) <= p) {
+      lo = g;
+      uint32_t step = 1;
+      while (true) {
+        hi = lo + step < kFenceBins ? lo + step : kFenceBins;
+        if (hi == kFenceBins || fence_sum(f, act, hi) > p) break;
+        lo = hi;
+        step <<= 1;
+      }
+    } else {
+      hi = g;
+      uint32_t step = 1;
+      while (true) {
+        lo = hi > step ? hi - step : 0u;
+        if (lo == 0 || fence_sum(f, act, lo) <= p) break;
+        hi = lo;
+        step <<= 1;
+      }
+    }
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (fence_sum(f, act, mid) <= p) lo = mid; else hi = mid;
+    }
+  }
+  // 2. Smallest key x in the bin with #{key <= x} > p.  Invariant per lane:
+  //    blo = #{key <= xlo - 1}, bhi = #{key <= xhi} in this lane's source.
+  uint32_t blo = act ? __ldg(f + lo) : 0u, bhi = act ? __ldg(f + lo + 1) : 0u;
+  uint32_t xlo = lo << 15, xhi = ((lo + 1) << 15) - 1;
   while (xlo < xhi) {
     const uint32_t mid = xlo + ((xhi - xlo) >> 1);
     const uint32_t u = act ? upper_bound_key(a, blo, bhi, mid) : 0u;
@@ -66,8 +118,8 @@ __global__ void __launch_bounds__(256) fold_partition(FoldSources src, uint64_t 
       blo = u;
     }
   }
-  // blo / bhi are now the lower / upper bound of key x in this source; the
-  // p - sum(blo) elements of key x that precede p come from the lowest ranks.
+  // 3. blo / bhi are now the lower / upper bound of key x in this source; the
+  //    p - sum(blo) elements of key x that precede p come from the lowest ranks.
   const uint32_t cnt = bhi - blo;
   const uint64_t need = p - warp_sum<uint64_t>(blo);
   const uint64_t excl = warp_incl_scan<uint64_t>(cnt) - cnt;
@@ -76,16 +128,59 @@ __global__ void __launch_bounds__(256) fold_partition(FoldSources src, uint64_t 
   if (act) out[lane] = blo + uint32_t(take);
 }
 
+// One merge step of the tile: output[0, nA + nB) = merge of run A (the
+// newer ranks) and run B (the next rank), ties to A.  B always sits in the
+// TMA slot area (separate key and value arrays); A is either there too (the
+// first step) or the (key, value) pair buffer X written by the step before.
+// Each thread produces ceil(m / 256) consecutive outputs after a merge-path
+// search for its first one; outputs go to the pair buffer Y, swizzled.
+template <bool kAFromSlot>
+__device__ __forceinline__ void merge_step(const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv,
+                                           const uint2* __restrict__ X, uint2* __restrict__ Y, uint32_t aS,
+                                           uint32_t nA, uint32_t bS, uint32_t nB) {
+  const uint32_t m = nA + nB;
+  // at least kMinPer outputs per working thread: each thread pays one
+  // merge-path search, so small steps use few threads
+  uint32_t per = (m + kThreads - 1) / kThreads;
+  per = per < kMinPer ? kMinPer : per;
+  const uint32_t q0 = threadIdx.x * per;
+  if (q0 >= m) return;
+  const uint32_t q1 = q0 + per < m ? q0 + per : m;
+  const uint32_t* xk = reinterpret_cast<const uint32_t*>(X);
+  auto keyA = [&](uint32_t i) { return kAFromSlot ? sk[aS + i] : xk[2 * psw(i)]; };
+  auto pairA = [&](uint32_t i) { return kAFromSlot ? make_uint2(sk[aS + i], sv[aS + i]) : X[psw(i)]; };
+  // merge path: how many of the first q0 outputs come from A
+  uint32_t lo = q0 > nB ? q0 - nB : 0u, hi = q0 < nA ? q0 : nA;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (key_of(keyA(mid)) <= key_of(sk[bS + q0 - 1 - mid])) lo = mid + 1; else hi = mid;
+  }
+  uint32_t ia = lo, ib = q0 - lo;
+  uint2 a = ia < nA ? pairA(ia) : make_uint2(0u, 0u);
+  uint2 b = ib < nB ? make_uint2(sk[bS + ib], sv[bS + ib]) : make_uint2(0u, 0u);
+  for (uint32_t q = q0; q < q1; ++q) {
+    const bool take_a = ia < nA && (ib >= nB || key_of(a.x) <= key_of(b.x));
+    if (take_a) {
+      Y[psw(q)] = a;
+      if (++ia < nA) a = pairA(ia);
+    } else {
+      Y[psw(q)] = b;
+      if (++ib < nB) b = make_uint2(sk[bS + ib], sv[bS + ib]);
+    }
+  }
+}
+
 template <bool kCleanup>
 __global__ void __launch_bounds__(kThreads) fold_merge(FoldSources src, uint64_t total,
                                                        const uint32_t* __restrict__ part,
                                                        uint32_t* __restrict__ out_k,
-                                                       uint32_t* __restrict__ out_v, uint32_t* status,
+                                                       uint32_t* __restrict__ out_v,
+                                                       uint32_t* __restrict__ out_fence, uint32_t* status,
                                                        uint64_t* lookback, uint32_t* tile_ctr,
                                                        uint64_t* out_count, uint32_t ntiles) {
   extern __shared__ __align__(128) uint32_t sm[];
   __shared__ __align__(8) uint64_t s_bar;
-  __shared__ uint32_t s_rstart[kMaxSources], s_rlen[kMaxSources], s_ostart[kMaxSources + 1];
+  __shared__ uint32_t s_rstart[kMaxSources], s_rlen[kMaxSources];
   __shared__ uint32_t s_a0[kMaxSources], s_span[kMaxSources], s_slot[kMaxSources];
   __shared__ uint32_t s_scan[kThreads / 32];
   __shared__ uint32_t s_tile, s_prev_key, s_ok;
@@ -106,10 +201,10 @@ __global__ void __launch_bounds__(kThreads) fold_merge(FoldSources src, uint64_t
   const uint32_t tile = s_tile;
   const uint64_t obase = uint64_t(tile) * kFoldTile;
   const uint32_t tile_n = uint32_t((total - obase) < kFoldTile ? (total - obase) : kFoldTile);
-  uint32_t* ak = sm;
-  uint32_t* av = sm + kCap;
-  uint32_t* bk = sm + 2 * kCap;
-  uint32_t* bv = sm + 3 * kCap;
+  uint32_t* sk = sm;                                          // slot keys
+  uint32_t* sv = sm + kSlotCap;                               // slot values
+  uint2* X = reinterpret_cast<uint2*>(sm + 2 * kSlotCap);     // pair buffers
+  uint2* Y = X + kFoldTile;
 
   // Segment of each source in this tile, and its 16-byte aligned superset.
   if (warp == 0) {
@@ -122,7 +217,7 @@ __global__ void __launch_bounds__(kThreads) fold_merge(FoldSources src, uint64_t
         a0 = c0 & ~3u;
         span = ((c1 + 3u) & ~3u) - a0;
       }
-      if (kCleanup && c0 > 0) {
+      if (c0 > 0) {
         has_prev = true;
         prev = key_of(__ldg(src.keys[lane] + c0 - 1));
       }
@@ -135,15 +230,13 @@ __global__ void __launch_bounds__(kThreads) fold_merge(FoldSources src, uint64_t
       s_span[lane] = span;
       s_slot[lane] = slot;
     }
-    if (kCleanup) {
-      // Key of the element just before this tile in merged order: the largest
-      // key among the sources' last elements before their co-ranks.
-      uint32_t m = has_prev ? prev : 0u;
+    // Key of the element just before this tile in merged order: the largest
+    // key among the sources' last elements before their co-ranks.
+    uint32_t mx = has_prev ? prev : 0u;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-      const bool any_prev = __any_sync(0xffffffffu, has_prev);
-      if (lane == 0) s_prev_key = any_prev ? m : 0xFFFFFFFFu;  // no key is 2^32 - 1 >> 0
-    }
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const bool any_prev = __any_sync(0xffffffffu, has_prev);
+    if (lane == 0) s_prev_key = any_prev ? mx : 0xFFFFFFFFu;  // no key equals 2^32 - 1
   }
   __syncthreads();
 
@@ -166,8 +259,8 @@ __global__ void __launch_bounds__(kThreads) fold_merge(FoldSources src, uint64_t
     if (ok) {
       for (int r = 0; r < S; ++r) {
         if (!s_span[r]) continue;
-        bulk_g2s(ak + s_slot[r], src.keys[r] + s_a0[r], s_span[r] * 4u, &s_bar);
-        bulk_g2s(av + s_slot[r], src.vals[r] + s_a0[r], s_span[r] * 4u, &s_bar);
+        bulk_g2s(sk + s_slot[r], src.keys[r] + s_a0[r], s_span[r] * 4u, &s_bar);
+        bulk_g2s(sv + s_slot[r], src.vals[r] + s_a0[r], s_span[r] * 4u, &s_bar);
       }
     }
   }
@@ -176,8 +269,8 @@ __global__ void __launch_bounds__(kThreads) fold_merge(FoldSources src, uint64_t
   if (!s_ok) {  // never expected: plain loads instead of the bulk copies
     for (int r = 0; r < S; ++r)
       for (uint32_t i = tid; i < s_span[r]; i += kThreads) {
-        ak[s_slot[r] + i] = __ldg(src.keys[r] + s_a0[r] + i);
-        av[s_slot[r] + i] = __ldg(src.vals[r] + s_a0[r] + i);
+        sk[s_slot[r] + i] = __ldg(src.keys[r] + s_a0[r] + i);
+        sv[s_slot[r] + i] = __ldg(src.vals[r] + s_a0[r] + i);
       }
     __syncthreads();
   }
@@ -188,92 +281,66 @@ __global__ void __launch_bounds__(kThreads) fold_merge(FoldSources src, uint64_t
     return;
   }
 
-  // Tree of pairwise merges: runs 2j and 2j+1 (adjacent ranks) -> run j.
-  uint32_t runs = uint32_t(S);
-  uint32_t *ck = ak, *cv = av, *nk = bk, *nv = bv;
-  do {
-    const uint32_t pairs = (runs + 1) >> 1;
-    if (tid == 0) {
-      uint32_t o = 0;
-      for (uint32_t j = 0; j < pairs; ++j) {
-        s_ostart[j] = o;
-        o += s_rlen[2 * j] + ((2 * j + 1 < runs) ? s_rlen[2 * j + 1] : 0u);
-      }
-      s_ostart[pairs] = o;
-    }
+  // Left-deep merge order: X = run 0 + run 1, then X = X + run r for each
+  // further rank.  Runs grow with their rank (the batch and level 0 are the
+  // smallest), so every element moves about twice in all.
+  if (S == 1) {
+    merge_step<true>(sk, sv, nullptr, X, s_rstart[0], s_rlen[0], 0u, 0u);
+  } else {
+    merge_step<true>(sk, sv, nullptr, X, s_rstart[0], s_rlen[0], s_rstart[1], s_rlen[1]);
+  }
+  uint32_t m = s_rlen[0] + (S > 1 ? s_rlen[1] : 0u);
+  for (int r = 2; r < S; ++r) {
     __syncthreads();
-    uint32_t q = tid * kE;
-    const uint32_t q_end = (q + kE < tile_n) ? q + kE : tile_n;
-    uint32_t j = 0;
-    while (q < q_end) {
-      while (s_ostart[j + 1] <= q) ++j;
-      const uint32_t aS = s_rstart[2 * j], nA = s_rlen[2 * j];
-      const bool hasB = 2 * j + 1 < runs;
-      const uint32_t bS = hasB ? s_rstart[2 * j + 1] : 0u, nB = hasB ? s_rlen[2 * j + 1] : 0u;
-      const uint32_t d = q - s_ostart[j];
-      const uint32_t seg_end = (q_end < s_ostart[j + 1]) ? q_end : s_ostart[j + 1];
-      uint32_t lo = d > nB ? d - nB : 0u, hi = d < nA ? d : nA;
-      while (lo < hi) {  // merge path: how many of the first d come from A
-        const uint32_t mid = (lo + hi) >> 1;
-        if (key_of(ck[aS + mid]) <= key_of(ck[bS + d - 1 - mid])) lo = mid + 1; else hi = mid;
-      }
-      uint32_t ia = lo, ib = d - lo;
-      for (; q < seg_end; ++q) {
-        bool take_a;
-        if (ia >= nA) take_a = false;
-        else if (ib >= nB) take_a = true;
-        else take_a = key_of(ck[aS + ia]) <= key_of(ck[bS + ib]);
-        if (take_a) {
-          nk[q] = ck[aS + ia];
-          nv[q] = cv[aS + ia];
-          ++ia;
-        } else {
-          nk[q] = ck[bS + ib];
-          nv[q] = cv[bS + ib];
-          ++ib;
-        }
-      }
-    }
-    __syncthreads();
-    if (tid == 0) {
-      for (uint32_t jj = 0; jj < pairs; ++jj) {
-        s_rstart[jj] = s_ostart[jj];
-        s_rlen[jj] = s_ostart[jj + 1] - s_ostart[jj];
-      }
-    }
-    runs = pairs;
-    uint32_t* t;
-    t = ck; ck = nk; nk = t;
-    t = cv; cv = nv; nv = t;
-    __syncthreads();
-  } while (runs > 1);
+    merge_step<false>(sk, sv, X, Y, 0u, m, s_rstart[r], s_rlen[r]);
+    m += s_rlen[r];
+    uint2* t = X;
+    X = Y;
+    Y = t;
+  }
+  __syncthreads();
+  const uint32_t* xk = reinterpret_cast<const uint32_t*>(X);
 
   if (!kCleanup) {
-    uint32_t* ok = out_k + obase;
-    uint32_t* ov = out_v + obase;
-    const uint32_t n4 = ((reinterpret_cast<uintptr_t>(ok) | reinterpret_cast<uintptr_t>(ov)) & 15u) ? 0u
-                                                                                                     : (tile_n & ~3u);
-    for (uint32_t i = tid * 4; i < n4; i += kThreads * 4) {
-      *reinterpret_cast<uint4*>(ok + i) = *reinterpret_cast<const uint4*>(ck + i);
-      *reinterpret_cast<uint4*>(ov + i) = *reinterpret_cast<const uint4*>(cv + i);
-    }
-    for (uint32_t i = n4 + tid; i < tile_n; i += kThreads) {
-      ok[i] = ck[i];
-      ov[i] = cv[i];
+    // Write the tile (coalesced) and, when asked, the new level's prefix
+    // index: for every bin P after the previous element's bin up to this
+    // element's bin, fence[P] = this element's position; the last element of
+    // the fold closes the table up to bin 65536.
+    const int first_prev_bin = s_prev_key == 0xFFFFFFFFu ? -1 : int(s_prev_key >> 15);
+    for (uint32_t base = warp * 32; base < tile_n; base += kThreads) {
+      const uint32_t q = base + lane;
+      const bool valid = q < tile_n;
+      const uint2 p = valid ? X[psw(q)] : make_uint2(0u, 0u);
+      if (valid) {
+        out_k[obase + q] = p.x;
+        out_v[obase + q] = p.y;
+      }
+      if (out_fence) {
+        uint32_t kprev = __shfl_up_sync(0xffffffffu, p.x, 1);
+        if (lane == 0 && base > 0) kprev = xk[2 * psw(base - 1)];
+        if (valid) {
+          const int bin = int(fence_bin(p.x));
+          const int pb = q ? int(fence_bin(kprev)) : first_prev_bin;
+          for (int P = pb + 1; P <= bin; ++P) out_fence[P] = uint32_t(obase + q);
+          if (obase + q + 1 == total)
+            for (uint32_t P = uint32_t(bin) + 1; P <= kFenceBins; ++P) out_fence[P] = uint32_t(total);
+        }
+      }
     }
     return;
   }
 
   // Cleanup: keep the first element of each key (the newest one, §IV-E) when
   // it is regular; compact across tiles.
+  constexpr int kE = kFoldTile / kThreads;
   const uint32_t q0 = tid * kE;
   uint32_t keep = 0, nkeep = 0;
 #pragma unroll
   for (int e = 0; e < kE; ++e) {
     const uint32_t q = q0 + e;
     if (q < tile_n) {
-      const uint32_t kv = ck[q];
-      const uint32_t prev = q ? key_of(ck[q - 1]) : s_prev_key;
+      const uint32_t kv = xk[2 * psw(q)];
+      const uint32_t prev = q ? key_of(xk[2 * psw(q - 1)]) : s_prev_key;
       if (key_of(kv) != prev && (kv & 1u)) {
         keep |= 1u << e;
         ++nkeep;
@@ -314,8 +381,9 @@ __global__ void __launch_bounds__(kThreads) fold_merge(FoldSources src, uint64_t
 #pragma unroll
   for (int e = 0; e < kE; ++e) {
     if (keep & (1u << e)) {
-      out_k[dst] = ck[q0 + e];
-      out_v[dst] = cv[q0 + e];
+      const uint2 p = X[psw(q0 + e)];
+      out_k[dst] = p.x;
+      out_v[dst] = p.y;
       ++dst;
     }
   }
@@ -333,6 +401,17 @@ __global__ void __launch_bounds__(256) distribute(DistributeArgs a) {
     }
     a.keys[dst] = k;
     a.vals[dst] = v;
+  }
+}
+
+// Prefix index of a sorted run: position i opens every bin after the bin of
+// element i - 1 up to its own; position n closes the table.
+__global__ void __launch_bounds__(256) build_fence(const uint32_t* __restrict__ keys, uint32_t n,
+                                                   uint32_t* __restrict__ fence) {
+  for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i <= n; i += uint64_t(gridDim.x) * 256ull) {
+    const uint32_t bin = i < n ? fence_bin(__ldg(keys + i)) : kFenceBins;
+    const int pb = i ? int(fence_bin(__ldg(keys + i - 1))) : -1;
+    for (int P = pb + 1; P <= int(bin); ++P) fence[P] = uint32_t(i);
   }
 }
 
@@ -369,12 +448,12 @@ cudaError_t fold_merge_launch(const FoldArgs& a, cudaStream_t st) {
     if ((e = cudaMemsetAsync(a.tile_ctr, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
     count_launches(1);
     fold_merge<true><<<unsigned(ntiles), kThreads, kMergeSmem, st>>>(
-        a.src, a.total, a.part, a.out_keys, a.out_vals, a.status, a.lookback, a.tile_ctr, a.out_count,
-        uint32_t(ntiles));
+        a.src, a.total, a.part, a.out_keys, a.out_vals, nullptr, a.status, a.lookback, a.tile_ctr,
+        a.out_count, uint32_t(ntiles));
   } else {
     count_launches(1);
     fold_merge<false><<<unsigned(ntiles), kThreads, kMergeSmem, st>>>(
-        a.src, a.total, a.part, a.out_keys, a.out_vals, a.status, nullptr, nullptr, nullptr,
+        a.src, a.total, a.part, a.out_keys, a.out_vals, a.out_fence, a.status, nullptr, nullptr, nullptr,
         uint32_t(ntiles));
   }
   return cudaGetLastError();
@@ -392,6 +471,14 @@ cudaError_t distribute_launch(const DistributeArgs& a, cudaStream_t st) {
   if (blocks > 152 * 16) blocks = 152 * 16;
   count_launches(1);
   distribute<<<unsigned(blocks), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t build_fence_launch(const uint32_t* keys, uint32_t n, uint32_t* fence, cudaStream_t st) {
+  uint64_t blocks = (uint64_t(n) + 1 + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  count_launches(1);
+  build_fence<<<unsigned(blocks), 256, 0, st>>>(keys, n, fence);
   return cudaGetLastError();
 }
 

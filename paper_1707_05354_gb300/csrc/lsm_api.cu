@@ -37,9 +37,11 @@ struct lsm_t {
   SortWorkspace sws{};
   uint32_t* d_part = nullptr;
   uint64_t part_words = 0;
+  uint32_t* d_fence = nullptr;  // prefix index per level (L tables) + the sorted batch's
   uint32_t* d_misc = nullptr;  // [0] sticky errors [1] key check [2] tile ctr [3] tile ctr
   uint64_t* d_u64 = nullptr;   // [0] cleanup count
-  uint32_t* h_status = nullptr;
+  uint32_t* h_status = nullptr;  // mapped pinned word: key check of the current batch
+  uint32_t* d_status_map = nullptr;
   uint64_t* h_u64 = nullptr;
   cudaEvent_t ev = nullptr;
   // cleanup scratch (allocated on first cleanup)
@@ -109,8 +111,8 @@ cudaError_t dalloc(T** p, uint64_t count) {
 
 void free_all(lsm_t* h) {
   void* dptrs[] = {h->d_keys, h->d_vals, h->d_bk, h->d_bv, h->d_tk, h->d_tv, h->sws.ctl, h->sws.lookback,
-                   h->d_part, h->d_misc, h->d_u64, h->d_ck, h->d_cv, h->d_clb, h->d_q, h->qsws.lookback,
-                   h->d_qctl};
+                   h->sws.tilecnt, h->d_part, h->d_fence, h->d_misc, h->d_u64, h->d_ck, h->d_cv, h->d_clb,
+                   h->d_q, h->qsws.lookback, h->qsws.tilecnt, h->d_qctl};
   for (void* p : dptrs)
     if (p) cudaFree(p);
   if (h->h_status) cudaFreeHost(h->h_status);
@@ -154,6 +156,8 @@ struct ProfScope {
 
 uint32_t* level_keys(lsm_t* h, int i) { return h->d_keys + h->level_off[i]; }
 uint32_t* level_vals(lsm_t* h, int i) { return h->d_vals + h->level_off[i]; }
+uint32_t* level_fence(lsm_t* h, int i) { return h->d_fence + uint64_t(i) * kFenceWords; }
+uint32_t* batch_fence(lsm_t* h) { return h->d_fence + uint64_t(h->L) * kFenceWords; }
 
 LevelSet full_levels(lsm_t* h) {
   LevelSet ls{};
@@ -161,6 +165,7 @@ LevelSet full_levels(lsm_t* h) {
     if (!((h->r >> i) & 1u)) continue;
     ls.keys[ls.count] = level_keys(h, i);
     ls.vals[ls.count] = level_vals(h, i);
+    ls.fence[ls.count] = level_fence(h, i);
     ls.n[ls.count] = uint32_t(uint64_t(h->b) << i);
     ++ls.count;
   }
@@ -199,24 +204,29 @@ lsm_status apply_batch(lsm_t* h, int mode, const uint32_t* keys, const uint32_t*
   a.out_vals = k == 0 ? level_vals(h, 0) : h->d_bv;
   a.tmp_keys = h->d_tk;
   a.tmp_vals = h->d_tv;
+  a.fence = k == 0 ? level_fence(h, 0) : batch_fence(h);
   {
     ProfScope ps(h, LSM_PROF_SORT, 16.0 * h->b, st);
-    LSM_TRY(sort_launch(a, h->sws, st, checked ? h->h_status : nullptr, h->ev));
+    if (checked) *reinterpret_cast<volatile uint32_t*>(h->h_status) = 0u;
+    LSM_TRY(sort_launch(a, h->sws, st, checked ? h->d_status_map : nullptr, h->ev));
   }
   if (k > 0) {
     FoldArgs f{};
     f.src.count = k + 1;
     f.src.keys[0] = h->d_bk;
     f.src.vals[0] = h->d_bv;
+    f.src.fence[0] = batch_fence(h);
     f.src.n[0] = h->b;
     for (int i = 0; i < k; ++i) {
       f.src.keys[i + 1] = level_keys(h, i);
       f.src.vals[i + 1] = level_vals(h, i);
+      f.src.fence[i + 1] = level_fence(h, i);
       f.src.n[i + 1] = uint32_t(uint64_t(h->b) << i);
     }
     f.total = uint64_t(h->b) << k;
     f.out_keys = level_keys(h, k);
     f.out_vals = level_vals(h, k);
+    f.out_fence = level_fence(h, k);
     f.part = h->d_part;
     f.status = h->d_misc + kMiscSticky;
     f.cleanup = false;
@@ -229,7 +239,7 @@ lsm_status apply_batch(lsm_t* h, int mode, const uint32_t* keys, const uint32_t*
   }
   if (checked) {
     LSM_TRY(cudaEventSynchronize(h->ev));
-    if (*h->h_status & kErrBadKey) return LSM_ERR_KEY_RANGE;
+    if (*reinterpret_cast<volatile uint32_t*>(h->h_status) & kErrBadKey) return LSM_ERR_KEY_RANGE;
   }
   h->r += 1;
   return LSM_OK;
@@ -308,12 +318,16 @@ lsm_status lsm_create(lsm_t** out, uint32_t b, uint64_t max_elements, int device
   if (e == cudaSuccess) e = dalloc(&h->d_bv, bpad);
   if (e == cudaSuccess) e = dalloc(&h->d_tk, bpad);
   if (e == cudaSuccess) e = dalloc(&h->d_tv, bpad);
-  if (e == cudaSuccess) e = dalloc(&h->sws.ctl, kSortCtlWords);
+  if (e == cudaSuccess) e = dalloc(&h->sws.ctl, 2 * kSortCtlWords);
+  if (e == cudaSuccess) e = cudaMemset(h->sws.ctl, 0, sizeof(uint32_t) * 2 * kSortCtlWords);
   if (e == cudaSuccess) e = dalloc(&h->sws.lookback, uint64_t(kSortPasses) * sort_tiles * 256);
+  if (e == cudaSuccess && b <= kMsdMaxN) e = dalloc(&h->sws.tilecnt, kMsdTileWords);
   if (e == cudaSuccess) e = dalloc(&h->d_part, h->part_words);
+  if (e == cudaSuccess) e = dalloc(&h->d_fence, uint64_t(L + 1) * kFenceWords);
   if (e == cudaSuccess) e = dalloc(&h->d_misc, kMiscWords);
   if (e == cudaSuccess) e = dalloc(&h->d_u64, 8);
-  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&h->h_status), 64, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&h->h_status), 64, cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->d_status_map), h->h_status, 0);
   if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&h->h_u64), 64, cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemset(h->d_keys, 0, sizeof(uint32_t) * (h->capacity + kSlack));
@@ -389,7 +403,12 @@ lsm_status lsm_lookup(lsm_t* h, const uint32_t* d_q, uint64_t nq, uint32_t* d_va
     h->qsws.max_tiles = uint32_t(tiles);
     h->qsws.epoch = 0;
   }
-  if (!h->d_qctl) LSM_TRY(dalloc(&h->d_qctl, kSortCtlWords));
+  if (!h->d_qctl) {
+    LSM_TRY(dalloc(&h->d_qctl, 2 * kSortCtlWords));
+    LSM_TRY(cudaMemset(h->d_qctl, 0, sizeof(uint32_t) * 2 * kSortCtlWords));
+    h->qsws.flip = 0;
+  }
+  if (!h->qsws.tilecnt) LSM_TRY(dalloc(&h->qsws.tilecnt, kMsdTileWords));
   h->qsws.ctl = h->d_qctl;
   h->qsws.sticky = h->d_misc + kMiscSticky;
   uint32_t* base = reinterpret_cast<uint32_t*>(h->d_q);
@@ -477,6 +496,7 @@ lsm_status lsm_cleanup(lsm_t* h, void* stream) {
   for (int i = 0; i < ls.count; ++i) {
     f.src.keys[i] = ls.keys[i];
     f.src.vals[i] = ls.vals[i];
+    f.src.fence[i] = ls.fence[i];
     f.src.n[i] = ls.n[i];
   }
   f.total = total;
@@ -514,6 +534,8 @@ lsm_status lsm_cleanup(lsm_t* h, void* stream) {
   {
     ProfScope ps(h, LSM_PROF_CLEANUP, 8.0 * double(d.total), st);
     LSM_TRY(distribute_launch(d, st));
+    for (uint32_t i = 0; i < h->L; ++i)
+      if ((r2 >> i) & 1u) LSM_TRY(build_fence_launch(level_keys(h, i), h->b << i, level_fence(h, i), st));
   }
   h->r = r2;
   return LSM_OK;

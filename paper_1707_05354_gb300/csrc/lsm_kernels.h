@@ -38,8 +38,20 @@ enum SortInput : int {
   kSortQueries = 4    // (keys[i], i): sort query keys with their positions
 };
 
+// Tuning of the batch sort (compile-time): items per thread (tile =
+// 256 * LSM_SORT_IPT elements), minimum resident CTAs per SM requested from
+// the compiler, and the number of predecessor tiles read per look-back step.
+#ifndef LSM_SORT_IPT
+#define LSM_SORT_IPT 16
+#endif
+#ifndef LSM_SORT_MINB
+#define LSM_SORT_MINB 1
+#endif
+#ifndef LSM_SORT_LBW
+#define LSM_SORT_LBW 8
+#endif
 constexpr int kSortPasses = 4;
-constexpr int kSortTile = 4096;  // elements per CTA tile of a pass
+constexpr int kSortTile = 256 * LSM_SORT_IPT;  // elements per CTA tile of a pass
 
 struct SortArgs {
   int mode;
@@ -52,34 +64,51 @@ struct SortArgs {
   uint32_t* out_vals;
   uint32_t* tmp_keys;   // n elements of scratch
   uint32_t* tmp_vals;
+  uint32_t* fence;      // prefix index of the sorted output to write, or null
 };
 
 struct SortWorkspace {
-  uint32_t* ctl;        // [hist 4*256][tile counters 4][status 1][pad]
+  uint32_t* ctl;        // two halves of kSortCtlWords: [hist 4*256][tile counters 4][pad]
+  int flip;             // the half the next sort uses; it is all zero on entry
   uint64_t* lookback;   // kSortPasses * max_tiles * 256 words
   uint32_t max_tiles;
   uint32_t epoch;       // bumped per sort; 0 never used
   uint32_t* sticky;     // persistent device error word (wait timeouts)
+  uint32_t* tilecnt;    // kMsdTileWords words (bucket sort of n <= kMsdMaxN), or null
 };
+// The bucket sort (n <= kMsdMaxN): per-tile bucket counts and offsets.
+constexpr uint32_t kMsdMaxN = 1u << 20;
+constexpr uint32_t kMsdTile = 4096;
+constexpr uint32_t kMsdTileWords = 2 * (kMsdMaxN / kMsdTile) * 256;
 constexpr int kSortCtlWords = kSortPasses * 256 + kSortPasses + 4;
 constexpr int kSortCtlStatus = kSortPasses * 256 + kSortPasses;
 
-// Enqueues the whole sort.  If h_status is given, the device status word is
-// copied to it right after the key check (the histogram kernel) and `ev` is
-// recorded there, so the host can learn about bad keys early.
+// Enqueues the whole sort.  If `status` is given (a device-visible word,
+// typically mapped pinned host memory), the first kernel stores kErrBadKey
+// there when a key is out of range, and `ev` is recorded right after that
+// kernel, so the host can learn about bad keys before the sort ends.
 cudaError_t sort_launch(const SortArgs& a, SortWorkspace& ws, cudaStream_t st,
-                        uint32_t* h_status, cudaEvent_t ev);
+                        uint32_t* status, cudaEvent_t ev);
 
 // Device key check alone over n keys (multi-batch calls check all first).
 cudaError_t check_keys_launch(const uint32_t* keys, uint64_t n, uint32_t* status,
                               cudaStream_t st);
 
 // ------------------------------------------------------------------ fold ---
-constexpr int kFoldTile = 4096;  // output elements per merge CTA
+constexpr int kFoldTile = 2048;  // output elements per merge CTA
+
+// Prefix index ("fence") of a sorted run: fence[P] = number of elements whose
+// key variable has top 16 bits < P (P = 0 .. 65536), i.e. the start of the
+// run of keys in [P * 2^15, (P + 1) * 2^15).  One table per level and one for
+// the sorted batch; written whenever the run is written.
+constexpr uint32_t kFenceBins = 65536;
+constexpr uint32_t kFenceWords = kFenceBins + 4;  // 65537 used, padded
+__host__ __device__ inline uint32_t fence_bin(uint32_t kv) { return kv >> 16; }
 
 struct FoldSources {
   const uint32_t* keys[kMaxSources];
   const uint32_t* vals[kMaxSources];
+  const uint32_t* fence[kMaxSources];
   uint32_t n[kMaxSources];
   int count;  // rank order: newest first
 };
@@ -90,6 +119,7 @@ struct FoldArgs {
   uint32_t* out_keys;
   uint32_t* out_vals;
   uint32_t* part;        // (ntiles + 1) * count co-ranks
+  uint32_t* out_fence;   // prefix index of the output (plain fold), or null
   uint32_t* status;
   // cleanup only: keep the first element of every key if regular, compacted
   bool cleanup;
@@ -123,9 +153,13 @@ cudaError_t distribute_launch(const DistributeArgs& a, cudaStream_t st);
 struct LevelSet {
   const uint32_t* keys[kMaxLevels];
   const uint32_t* vals[kMaxLevels];
+  const uint32_t* fence[kMaxLevels];
   uint32_t n[kMaxLevels];
   int count;  // full levels, newest (smallest) first
 };
+
+// Prefix index of a sorted run of n key variables (kFenceWords words).
+cudaError_t build_fence_launch(const uint32_t* keys, uint32_t n, uint32_t* fence, cudaStream_t st);
 
 cudaError_t lookup_launch(const LevelSet& ls, const uint32_t* q, uint64_t nq,
                           uint32_t* val, uint8_t* found, cudaStream_t st);

@@ -4,10 +4,10 @@
 // LOOKUP  searches the full levels from the newest (smallest) to the oldest
 //         for the first element whose key is >= q; if that element has key q
 //         it decides: regular -> found with its value, tombstone -> absent
-//         (and the search stops).  Each CTA first caches, per level, a sorted
-//         sample of every stride-th key variable (the top of the level's
-//         search tree) in shared memory; a search narrows to one stride there
-//         and finishes in global memory.
+//         (and the search stops).  The top of each level's search tree is the
+//         level's prefix index, a 65536-ary splitter table (one entry per
+//         2^15 keys, 256 KB, resident in L2): two adjacent loads narrow a
+//         search to one bin, and a binary search finishes inside it.
 //         lookup_direct takes the queries in input order (one thread each);
 //         lookup_sorted takes queries sorted by key: the first and last lane
 //         of a warp bound the warp's window in each level and every lane then
@@ -29,48 +29,24 @@ namespace gpulsm {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kSplitWords = 8192;  // shared-memory splitter budget per CTA (32 KB)
 
-__device__ __forceinline__ void fill_splitters(const LevelSet& ls, int per_level, uint32_t* s_split,
-                                               uint32_t* s_stride) {
-  for (int l = 0; l < ls.count; ++l) {
-    const uint32_t n = ls.n[l];
-    const uint32_t stride = (n + per_level - 1) / per_level;
-    for (int j = threadIdx.x; j < per_level; j += blockDim.x) {
-      const uint64_t pos = uint64_t(j) * stride;
-      s_split[l * per_level + j] = pos < n ? __ldg(ls.keys[l] + pos) : 0xFFFFFFFFu;
-    }
-    if (threadIdx.x == 0) s_stride[l] = stride;
-  }
-}
-
-// lower_bound of key variable `target` in level l, using the cached samples.
-__device__ __forceinline__ uint32_t level_lower_bound(const LevelSet& ls, int l, int per_level,
-                                                      const uint32_t* s_split, const uint32_t* s_stride,
-                                                      uint32_t target) {
-  const uint32_t* sp = s_split + l * per_level;
-  uint32_t a = 0, b = uint32_t(per_level);
-  while (a < b) {
-    const uint32_t m = (a + b) >> 1;
-    if (sp[m] < target) a = m + 1; else b = m;
-  }
-  const uint32_t stride = s_stride[l], n = ls.n[l];
-  const uint32_t lo = a == 0 ? 0u : (a - 1) * stride + 1;
-  const uint64_t hi64 = uint64_t(a) * stride;
-  const uint32_t hi = hi64 < n ? uint32_t(hi64) : n;
-  return lower_bound_kv(ls.keys[l], lo, hi, target);
+// lower_bound of key variable `target` in level l: the level's prefix index
+// (a 65536-ary splitter table, one entry per 2^15 keys) gives the run of the
+// target's bin in two adjacent loads; a binary search finishes inside it.
+__device__ __forceinline__ uint32_t level_lower_bound(const LevelSet& ls, int l, uint32_t target) {
+  const uint32_t* f = ls.fence[l];
+  const uint32_t bin = fence_bin(target);
+  return lower_bound_kv(ls.keys[l], __ldg(f + bin), __ldg(f + bin + 1), target);
 }
 
 // Lookup of one key over the levels (newest first).
-__device__ __forceinline__ void lookup_one(const LevelSet& ls, int per_level, const uint32_t* s_split,
-                                           const uint32_t* s_stride, uint32_t key, uint32_t& val,
-                                           uint8_t& found) {
+__device__ __forceinline__ void lookup_one(const LevelSet& ls, uint32_t key, uint32_t& val, uint8_t& found) {
   val = 0;
   found = 0;
   if (key > kMaxUserKey) return;
   const uint32_t target = key << 1;
   for (int l = 0; l < ls.count; ++l) {
-    const uint32_t pos = level_lower_bound(ls, l, per_level, s_split, s_stride, target);
+    const uint32_t pos = level_lower_bound(ls, l, target);
     if (pos < ls.n[l]) {
       const uint32_t kv = __ldg(ls.keys[l] + pos);
       if (key_of(kv) == key) {
@@ -84,34 +60,24 @@ __device__ __forceinline__ void lookup_one(const LevelSet& ls, int per_level, co
   }
 }
 
-__global__ void __launch_bounds__(kThreads) lookup_direct(LevelSet ls, int per_level,
-                                                          const uint32_t* __restrict__ q, uint64_t nq,
+__global__ void __launch_bounds__(kThreads) lookup_direct(LevelSet ls, const uint32_t* __restrict__ q, uint64_t nq,
                                                           uint32_t* __restrict__ out_v,
                                                           uint8_t* __restrict__ out_f) {
-  extern __shared__ uint32_t s_split[];
-  __shared__ uint32_t s_stride[kMaxLevels];
-  fill_splitters(ls, per_level, s_split, s_stride);
-  __syncthreads();
   for (uint64_t i = blockIdx.x * uint64_t(kThreads) + threadIdx.x; i < nq;
        i += uint64_t(gridDim.x) * kThreads) {
     uint32_t v;
     uint8_t f;
-    lookup_one(ls, per_level, s_split, s_stride, __ldg(q + i), v, f);
+    lookup_one(ls, __ldg(q + i), v, f);
     out_v[i] = v;
     out_f[i] = f;
   }
 }
 
 // Queries sorted by key; results scattered back to positions idx[i].
-__global__ void __launch_bounds__(kThreads) lookup_sorted(LevelSet ls, int per_level,
-                                                          const uint32_t* __restrict__ sq,
+__global__ void __launch_bounds__(kThreads) lookup_sorted(LevelSet ls, const uint32_t* __restrict__ sq,
                                                           const uint32_t* __restrict__ idx, uint64_t nq,
                                                           uint32_t* __restrict__ out_v,
                                                           uint8_t* __restrict__ out_f) {
-  extern __shared__ uint32_t s_split[];
-  __shared__ uint32_t s_stride[kMaxLevels];
-  fill_splitters(ls, per_level, s_split, s_stride);
-  __syncthreads();
   const uint32_t lane = lane_id();
   const uint64_t warps = uint64_t(gridDim.x) * (kThreads / 32);
   for (uint64_t w = (blockIdx.x * uint64_t(kThreads) + threadIdx.x) >> 5; w * 32 < nq; w += warps) {
@@ -133,9 +99,7 @@ __global__ void __launch_bounds__(kThreads) lookup_sorted(LevelSet ls, int per_l
         // start; every lane's answer lies in [wlo, whi] (lower bounds are
         // monotone in the key), so each lane searches [wlo, whi + 1).
         uint32_t edge = 0;
-        if (lane < 2)
-          edge = level_lower_bound(ls, l, per_level, s_split, s_stride,
-                                   (lane == 0 ? kfirst : klast) << 1);
+        if (lane < 2) edge = level_lower_bound(ls, l, (lane == 0 ? kfirst : klast) << 1);
         const uint32_t wlo = __shfl_sync(0xffffffffu, edge, 0);
         uint32_t whi = __shfl_sync(0xffffffffu, edge, 1);
         whi = whi < ls.n[l] ? whi + 1 : ls.n[l];
@@ -165,26 +129,31 @@ __global__ void __launch_bounds__(kThreads) lookup_sorted(LevelSet ls, int per_l
 }
 
 // Per-query multi-way merge of the level windows on the key, newer level
-// first among equal keys; visits the newest element of every key once.
-template <bool kEmit>
-__device__ __forceinline__ uint32_t merge_windows(const LevelSet& ls, const uint32_t* lo, const uint32_t* hi,
-                                                  uint32_t* out_k, uint32_t* out_v, uint64_t room = 0) {
-  uint32_t cur[kMaxLevels], head[kMaxLevels];
-  for (int l = 0; l < ls.count; ++l) {
+// first among equal keys; visits the newest element of every key once.  L is
+// a compile-time bound on the number of full levels (loops fully unrolled, so
+// the cursors stay in registers); levels l >= ls.count are empty.
+template <bool kEmit, int L>
+__device__ __forceinline__ uint32_t merge_windows(const LevelSet& ls, const uint32_t (&lo)[L],
+                                                  const uint32_t (&hi)[L], uint32_t* out_k, uint32_t* out_v,
+                                                  uint64_t room) {
+  uint32_t cur[L], head[L];
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
     cur[l] = lo[l];
-    head[l] = cur[l] < hi[l] ? key_of(__ldg(ls.keys[l] + cur[l])) : 0xFFFFFFFFu;
+    head[l] = (l < ls.count && cur[l] < hi[l]) ? key_of(__ldg(ls.keys[l] + cur[l])) : 0xFFFFFFFFu;
   }
   uint32_t c = 0, last = 0xFFFFFFFFu;
   while (true) {
+    uint32_t bk = 0xFFFFFFFFu, p = 0;
     int best = -1;
-    uint32_t bk = 0xFFFFFFFFu;
-    for (int l = 0; l < ls.count; ++l)
-      if (head[l] < bk) {
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+      if (head[l] < bk) {  // strict: the lowest (newest) level wins ties
         bk = head[l];
         best = l;
+        p = cur[l];
       }
     if (best < 0) break;
-    const uint32_t p = cur[best];
     if (bk != last) {
       last = bk;
       const uint32_t kv = __ldg(ls.keys[best] + p);
@@ -196,12 +165,17 @@ __device__ __forceinline__ uint32_t merge_windows(const LevelSet& ls, const uint
         ++c;
       }
     }
-    cur[best] = p + 1;
-    head[best] = p + 1 < hi[best] ? key_of(__ldg(ls.keys[best] + p + 1)) : 0xFFFFFFFFu;
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+      if (l == best) {
+        cur[l] = p + 1;
+        head[l] = p + 1 < hi[l] ? key_of(__ldg(ls.keys[l] + p + 1)) : 0xFFFFFFFFu;
+      }
   }
   return c;
 }
 
+template <int L>
 __global__ void __launch_bounds__(kThreads) count_kernel(LevelSet ls, const uint32_t* __restrict__ k1,
                                                          const uint32_t* __restrict__ k2, uint64_t nq,
                                                          uint32_t* __restrict__ out_count,
@@ -211,27 +185,30 @@ __global__ void __launch_bounds__(kThreads) count_kernel(LevelSet ls, const uint
     const uint32_t a = __ldg(k1 + i);
     uint32_t z = __ldg(k2 + i);
     if (z > kMaxUserKey) z = kMaxUserKey;
-    uint32_t lo[kMaxLevels], hi[kMaxLevels];
+    uint32_t lo[L], hi[L];
     const bool empty = a > z;
-    for (int l = 0; l < ls.count; ++l) {
-      if (empty) {
-        lo[l] = hi[l] = 0;
-      } else {
-        lo[l] = lower_bound_kv(ls.keys[l], 0, ls.n[l], a << 1);
-        hi[l] = lower_bound_kv(ls.keys[l], lo[l], ls.n[l], (z + 1u) << 1);
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      lo[l] = hi[l] = 0;
+      if (l < ls.count && !empty) {
+        lo[l] = level_lower_bound(ls, l, a << 1);
+        hi[l] = level_lower_bound(ls, l, (z + 1u) << 1);
       }
     }
-    out_count[i] = merge_windows<false>(ls, lo, hi, nullptr, nullptr);
+    out_count[i] = merge_windows<false, L>(ls, lo, hi, nullptr, nullptr, 0);
     if (bounds) {
       uint32_t* b = bounds + i * 2 * ls.count;
-      for (int l = 0; l < ls.count; ++l) {
-        b[2 * l] = lo[l];
-        b[2 * l + 1] = hi[l];
-      }
+#pragma unroll
+      for (int l = 0; l < L; ++l)
+        if (l < ls.count) {
+          b[2 * l] = lo[l];
+          b[2 * l + 1] = hi[l];
+        }
     }
   }
 }
 
+template <int L>
 __global__ void __launch_bounds__(kThreads) range_emit(LevelSet ls, uint64_t nq,
                                                        const uint32_t* __restrict__ bounds,
                                                        const uint64_t* __restrict__ offsets,
@@ -239,14 +216,15 @@ __global__ void __launch_bounds__(kThreads) range_emit(LevelSet ls, uint64_t nq,
                                                        uint32_t* __restrict__ vals) {
   for (uint64_t i = blockIdx.x * uint64_t(kThreads) + threadIdx.x; i < nq;
        i += uint64_t(gridDim.x) * kThreads) {
-    uint32_t lo[kMaxLevels], hi[kMaxLevels];
+    uint32_t lo[L], hi[L];
     const uint32_t* b = bounds + i * 2 * ls.count;
-    for (int l = 0; l < ls.count; ++l) {
-      lo[l] = b[2 * l];
-      hi[l] = b[2 * l + 1];
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      lo[l] = l < ls.count ? b[2 * l] : 0u;
+      hi[l] = l < ls.count ? b[2 * l + 1] : 0u;
     }
     const uint64_t o = offsets[i];
-    merge_windows<true>(ls, lo, hi, keys + o, vals + o, offsets[i + 1] - o);
+    merge_windows<true, L>(ls, lo, hi, keys + o, vals + o, offsets[i + 1] - o);
   }
 }
 
@@ -311,12 +289,6 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const uint32_t* __restri
   }
 }
 
-int splitters_per_level(int count) {
-  if (count <= 0) return 1;
-  int per = kSplitWords / count;
-  return per < 1 ? 1 : per;
-}
-
 unsigned persistent_grid(uint64_t work, int per_block, unsigned cap) {
   uint64_t b = (work + per_block - 1) / per_block;
   if (b > cap) b = cap;
@@ -328,29 +300,30 @@ unsigned persistent_grid(uint64_t work, int per_block, unsigned cap) {
 cudaError_t lookup_launch(const LevelSet& ls, const uint32_t* q, uint64_t nq, uint32_t* val, uint8_t* found,
                           cudaStream_t st) {
   if (nq == 0) return cudaSuccess;
-  const int per = splitters_per_level(ls.count);
-  const size_t smem = size_t(per) * (ls.count ? ls.count : 1) * sizeof(uint32_t);
   count_launches(1);
-  lookup_direct<<<persistent_grid(nq, kThreads, 152 * 6), kThreads, smem, st>>>(ls, per, q, nq, val, found);
+  lookup_direct<<<persistent_grid(nq, kThreads, 152 * 8), kThreads, 0, st>>>(ls, q, nq, val, found);
   return cudaGetLastError();
 }
 
 cudaError_t lookup_sorted_launch(const LevelSet& ls, const uint32_t* sq, const uint32_t* idx, uint64_t nq,
                                  uint32_t* val, uint8_t* found, cudaStream_t st) {
   if (nq == 0) return cudaSuccess;
-  const int per = splitters_per_level(ls.count);
-  const size_t smem = size_t(per) * (ls.count ? ls.count : 1) * sizeof(uint32_t);
   count_launches(1);
-  lookup_sorted<<<persistent_grid(nq, kThreads, 152 * 6), kThreads, smem, st>>>(ls, per, sq, idx, nq, val,
-                                                                               found);
+  lookup_sorted<<<persistent_grid(nq, kThreads, 152 * 8), kThreads, 0, st>>>(ls, sq, idx, nq, val, found);
   return cudaGetLastError();
 }
 
 cudaError_t count_launch(const LevelSet& ls, const uint32_t* k1, const uint32_t* k2, uint64_t nq,
                          uint32_t* count, uint32_t* bounds, cudaStream_t st) {
   if (nq == 0) return cudaSuccess;
+  const unsigned grid = persistent_grid(nq, kThreads, 152 * 8);
   count_launches(1);
-  count_kernel<<<persistent_grid(nq, kThreads, 152 * 8), kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds);
+  if (ls.count <= 1) count_kernel<1><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds);
+  else if (ls.count <= 2) count_kernel<2><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds);
+  else if (ls.count <= 4) count_kernel<4><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds);
+  else if (ls.count <= 8) count_kernel<8><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds);
+  else if (ls.count <= 16) count_kernel<16><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds);
+  else count_kernel<kMaxLevels><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds);
   return cudaGetLastError();
 }
 
@@ -369,8 +342,14 @@ cudaError_t scan_launch(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t*
 cudaError_t range_emit_launch(const LevelSet& ls, uint64_t nq, const uint32_t* bounds, const uint64_t* offsets,
                               uint32_t* keys, uint32_t* vals, cudaStream_t st) {
   if (nq == 0) return cudaSuccess;
+  const unsigned grid = persistent_grid(nq, kThreads, 152 * 8);
   count_launches(1);
-  range_emit<<<persistent_grid(nq, kThreads, 152 * 8), kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals);
+  if (ls.count <= 1) range_emit<1><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals);
+  else if (ls.count <= 2) range_emit<2><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals);
+  else if (ls.count <= 4) range_emit<4><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals);
+  else if (ls.count <= 8) range_emit<8><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals);
+  else if (ls.count <= 16) range_emit<16><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals);
+  else range_emit<kMaxLevels><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals);
   return cudaGetLastError();
 }
 

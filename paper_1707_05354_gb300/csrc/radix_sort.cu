@@ -25,6 +25,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kIPT = kSortTile / kThreads;  // 16 items per thread
 constexpr int kRadix = 256;
 constexpr uint32_t kNoDigit = 256;
+constexpr int kLookbackWindow = LSM_SORT_LBW;
 static_assert(kThreads == kRadix, "one thread per digit in the look-back");
 
 // Look-back word: [epoch:30][flag:2][value:32].
@@ -77,7 +78,8 @@ struct Loader {
   }
 };
 
-__global__ void __launch_bounds__(kThreads) sort_histogram(Loader ld, uint32_t* __restrict__ ctl) {
+__global__ void __launch_bounds__(kThreads) sort_histogram(Loader ld, uint32_t* __restrict__ ctl,
+                                                           uint32_t* status) {
   __shared__ uint32_t s_h[kSortPasses * kRadix];
   for (int i = threadIdx.x; i < kSortPasses * kRadix; i += kThreads) s_h[i] = 0;
   __syncthreads();
@@ -94,11 +96,11 @@ __global__ void __launch_bounds__(kThreads) sort_histogram(Loader ld, uint32_t* 
     const uint32_t c = s_h[i];
     if (c) atomicAdd(ctl + i, c);
   }
-  if (any_bad && threadIdx.x == 0) atomicOr(ctl + kSortCtlStatus, kErrBadKey);
+  if (any_bad && threadIdx.x == 0 && status) *reinterpret_cast<volatile uint32_t*>(status) = kErrBadKey;
 }
 
 template <bool kFirst>
-__global__ void __launch_bounds__(kThreads) sort_pass(Loader ld, const uint32_t* __restrict__ in_k,
+__global__ void __launch_bounds__(kThreads, LSM_SORT_MINB) sort_pass(Loader ld, const uint32_t* __restrict__ in_k,
                                                       const uint32_t* __restrict__ in_v,
                                                       uint32_t* __restrict__ out_k,
                                                       uint32_t* __restrict__ out_v,
@@ -169,36 +171,9 @@ __global__ void __launch_bounds__(kThreads) sort_pass(Loader ld, const uint32_t*
   uint32_t hsum;
   const uint32_t hbase = block_excl_scan<kThreads>(ctl[pass * kRadix + tid], s_scan, hsum);
 
-  // Decoupled look-back over the tiles before this one, one digit per thread.
-  uint64_t* my = lookback + uint64_t(tile) * kRadix + tid;
-  uint32_t prefix = 0;
-  if (tile == 0) {
-    st_relaxed_u64(my, lb_pack(epoch, kFlagIncl, total));
-  } else {
-    st_relaxed_u64(my, lb_pack(epoch, kFlagAgg, total));
-    int64_t t = int64_t(tile) - 1;
-    uint64_t t0 = 0;
-    while (t >= 0) {
-      const uint64_t w = ld_relaxed_u64(lookback + uint64_t(t) * kRadix + tid);
-      const uint64_t flag = (w >> 32) & 3u;
-      if (uint32_t(w >> 34) != epoch || flag == 0) {
-        if (t0 == 0) t0 = globaltimer_ns();
-        else if (globaltimer_ns() - t0 > kWaitLimitNs) {
-          atomicOr(sticky, kErrTimeout);
-          break;
-        }
-        continue;
-      }
-      prefix += uint32_t(w);
-      if (flag == kFlagIncl) break;
-      --t;
-    }
-    st_relaxed_u64(my, lb_pack(epoch, kFlagIncl, prefix + total));
-  }
-  s_gbase[tid] = hbase + prefix;
+  // Scatter into shared memory in digit order (stable) while the look-back
+  // below is still to come: the item registers are free afterwards.
   __syncthreads();
-
-  // Scatter into shared memory in digit order (stable), then write out.
 #pragma unroll
   for (int j = 0; j < kIPT; ++j) {
     const uint32_t p = base + j * 32 + lane;
@@ -209,7 +184,59 @@ __global__ void __launch_bounds__(kThreads) sort_pass(Loader ld, const uint32_t*
       s_vals[pos] = v[j];
     }
   }
+
+  // Decoupled look-back over the tiles before this one, one digit per
+  // thread, reading kLookbackWindow predecessors per step: the words are
+  // consumed from the nearest tile down until an inclusive prefix is found;
+  // a word not yet published stops the step, which is then retried from
+  // there (bounded in time).
+  uint64_t* my = lookback + uint64_t(tile) * kRadix + tid;
+  uint32_t prefix = 0;
+  if (tile == 0) {
+    st_relaxed_u64(my, lb_pack(epoch, kFlagIncl, total));
+  } else {
+    st_relaxed_u64(my, lb_pack(epoch, kFlagAgg, total));
+    int64_t t = int64_t(tile) - 1;
+    uint64_t t0 = 0;
+    bool done = false;
+    while (!done) {
+      uint64_t w[kLookbackWindow];
+#pragma unroll
+      for (int i = 0; i < kLookbackWindow; ++i)
+        w[i] = (t - i >= 0) ? ld_relaxed_u64(lookback + uint64_t(t - i) * kRadix + tid) : 0ull;
+      int consumed = 0;
+      bool stall = false;
+#pragma unroll
+      for (int i = 0; i < kLookbackWindow; ++i) {
+        if (done || stall) continue;
+        if (t - i < 0) {  // ran past tile 0: the prefix is complete
+          done = true;
+          continue;
+        }
+        const uint64_t flag = (w[i] >> 32) & 3u;
+        if (uint32_t(w[i] >> 34) != epoch || flag == 0) {
+          stall = true;
+          continue;
+        }
+        prefix += uint32_t(w[i]);
+        ++consumed;
+        if (flag == kFlagIncl) done = true;
+      }
+      t -= consumed;
+      if (!done && consumed == 0) {
+        if (t0 == 0) {
+          t0 = globaltimer_ns();
+        } else if (globaltimer_ns() - t0 > kWaitLimitNs) {
+          atomicOr(sticky, kErrTimeout);
+          break;
+        }
+      }
+    }
+    st_relaxed_u64(my, lb_pack(epoch, kFlagIncl, prefix + total));
+  }
+  s_gbase[tid] = hbase + prefix;
   __syncthreads();
+
   const uint32_t tile_start = tile * kSortTile;
   const uint32_t tile_n = (n - tile_start) < uint32_t(kSortTile) ? (n - tile_start) : uint32_t(kSortTile);
   for (uint32_t i = tid; i < tile_n; i += kThreads) {
@@ -223,6 +250,290 @@ __global__ void __launch_bounds__(kThreads) sort_pass(Loader ld, const uint32_t*
   }
 }
 
+// ---------------------------------------------------------------------------
+// Bucket sort for n <= kMsdMaxN (the batch sizes of the plain form): the top
+// byte of the key variable first, then the low 24 bits inside each bucket.
+//   msd_count    per 4096-element tile of the (encoded, reversed) input: the
+//                count of each top byte, and the grand totals; key check.
+//   msd_offsets  per bucket: the exclusive scan of its tile counts plus the
+//                bucket's start, i.e. where each tile's run of that bucket
+//                goes -- every offset is exact before any element moves, so
+//                the scatter needs no look-back between tiles.
+//   msd_scatter  per tile: stable rank by top byte in shared memory, then
+//                each element to its bucket run.
+//   bucket_sort  per bucket, one CTA: the bucket (at most kBucketCap
+//                elements) is sorted on bits 0..23 by three stable 8-bit
+//                passes entirely in shared memory and written out; the CTA
+//                also writes the prefix index entries of its 256 bins.  A
+//                larger bucket (heavy duplicate keys) is sorted by the same
+//                CTA in chunks through global memory, still stably.
+// ---------------------------------------------------------------------------
+constexpr int kBucketThreads = 512;
+constexpr int kBucketWarps = kBucketThreads / 32;
+constexpr int kBucketIPT = 11;
+constexpr uint32_t kBucketCap = kBucketThreads * kBucketIPT;  // 5632
+constexpr int kMsdIPT = int(kMsdTile) / kThreads;              // 16
+static_assert(kMsdIPT * kThreads == int(kMsdTile), "tile");
+
+__global__ void __launch_bounds__(kThreads) msd_count(Loader ld, uint32_t* __restrict__ tilecnt,
+                                                      uint32_t* __restrict__ ctl, uint32_t* status) {
+  __shared__ uint32_t s_h[kRadix];
+  const uint32_t tid = threadIdx.x, tile = blockIdx.x;
+  s_h[tid] = 0;
+  __syncthreads();
+  uint32_t kv[kMsdIPT];
+  bool bad_any = false;
+#pragma unroll
+  for (int j = 0; j < kMsdIPT; ++j) {
+    const uint32_t p = tile * kMsdTile + j * kThreads + tid;
+    bool bad = false;
+    kv[j] = p < ld.n ? ld.load_key(p, bad) : 0u;
+    bad_any |= bad;
+  }
+#pragma unroll
+  for (int j = 0; j < kMsdIPT; ++j)
+    if (tile * kMsdTile + j * kThreads + tid < ld.n) atomicAdd(&s_h[kv[j] >> 24], 1u);
+  const int any_bad = __syncthreads_or(bad_any);
+  const uint32_t c = s_h[tid];
+  tilecnt[tile * kRadix + tid] = c;
+  if (c) atomicAdd(ctl + 3 * kRadix + tid, c);
+  if (any_bad && tid == 0 && status) *reinterpret_cast<volatile uint32_t*>(status) = kErrBadKey;
+}
+
+// Start of bucket d in the output: the sum of the totals of the buckets
+// before it (every thread of the block gets it).
+template <int NT>
+__device__ __forceinline__ uint32_t bucket_start(const uint32_t* ctl, uint32_t d, uint32_t* s_scan) {
+  uint32_t x = 0;
+  for (uint32_t i = threadIdx.x; i < kRadix; i += NT)
+    if (i < d) x += ctl[3 * kRadix + i];
+  uint32_t tot;
+  block_excl_scan<NT>(x, s_scan, tot);
+  return tot;
+}
+
+__global__ void __launch_bounds__(kThreads) msd_offsets(const uint32_t* __restrict__ tilecnt, uint32_t ntiles,
+                                                        const uint32_t* __restrict__ ctl,
+                                                        uint32_t* __restrict__ tileoff) {
+  __shared__ uint32_t s_scan[kWarps];
+  const uint32_t d = blockIdx.x, t = threadIdx.x;
+  const uint32_t base = bucket_start<kThreads>(ctl, d, s_scan);
+  const uint32_t c = t < ntiles ? tilecnt[t * kRadix + d] : 0u;
+  uint32_t tot;
+  const uint32_t excl = block_excl_scan<kThreads>(c, s_scan, tot);
+  if (t < ntiles) tileoff[t * kRadix + d] = base + excl;
+}
+
+// Stable in-shared-memory rank of up to IPT items per thread of a warp-striped
+// block (item j of lane l of warp w is element w*32*IPT + j*32 + l): on return
+// s_whist[w][d] holds warp w's start inside digit d's run, s_excl[d] the run's
+// start, and rank[j] the item's position among its warp's items of its digit.
+template <int NT, int IPT>
+__device__ __forceinline__ void rank_block(const uint32_t (&kv)[IPT], uint32_t m, uint32_t base, int shift,
+                                           uint32_t (&rank)[IPT], uint32_t (*s_whist)[kRadix],
+                                           uint32_t* s_excl, uint32_t* s_scan, uint32_t* digit_total) {
+  constexpr int NW = NT / 32;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  for (uint32_t i = lane; i < kRadix; i += 32) s_whist[warp][i] = 0;
+  __syncwarp();
+  const uint32_t lt = lanemask_lt();
+#pragma unroll
+  for (int j = 0; j < IPT; ++j) {
+    const uint32_t p = base + j * 32 + lane;
+    const uint32_t d = (p < m) ? ((kv[j] >> shift) & 255u) : kNoDigit;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t before = __popc(peers & lt);
+    const uint32_t cnt = (d != kNoDigit) ? s_whist[warp][d] : 0u;
+    __syncwarp();
+    if (d != kNoDigit && before == 0) s_whist[warp][d] = cnt + __popc(peers);
+    __syncwarp();
+    rank[j] = cnt + before;
+  }
+  __syncthreads();
+  uint32_t total = 0;
+  if (tid < kRadix) {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      const uint32_t c = s_whist[w][tid];
+      s_whist[w][tid] = total;
+      total += c;
+    }
+  }
+  uint32_t all;
+  const uint32_t excl = block_excl_scan<NT>(tid < kRadix ? total : 0u, s_scan, all);
+  if (tid < kRadix) {
+    s_excl[tid] = excl;
+    if (digit_total) digit_total[tid] = total;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) msd_scatter(Loader ld, const uint32_t* __restrict__ tileoff,
+                                                        uint32_t* __restrict__ out_k,
+                                                        uint32_t* __restrict__ out_v) {
+  __shared__ __align__(16) uint32_t s_keys[kMsdTile];
+  __shared__ __align__(16) uint32_t s_vals[kMsdTile];
+  __shared__ uint32_t s_whist[kWarps][kRadix];
+  __shared__ uint32_t s_excl[kRadix], s_gbase[kRadix], s_scan[kWarps];
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5, tile = blockIdx.x;
+  const uint32_t n = ld.n;
+  const uint32_t base = tile * kMsdTile + warp * (32 * kMsdIPT);
+  uint32_t kv[kMsdIPT], v[kMsdIPT], rank[kMsdIPT];
+#pragma unroll
+  for (int j = 0; j < kMsdIPT; ++j) {
+    const uint32_t p = base + j * 32 + lane;
+    kv[j] = 0;
+    v[j] = 0;
+    if (p < n) {
+      bool bad;
+      ld.load(p, kv[j], v[j], bad);
+    }
+  }
+  s_gbase[tid] = tileoff[tile * kRadix + tid];
+  rank_block<kThreads, kMsdIPT>(kv, n, base, 24, rank, s_whist, s_excl, s_scan, nullptr);
+#pragma unroll
+  for (int j = 0; j < kMsdIPT; ++j) {
+    const uint32_t p = base + j * 32 + lane;
+    if (p < n) {
+      const uint32_t d = kv[j] >> 24;
+      const uint32_t pos = s_excl[d] + s_whist[warp][d] + rank[j];
+      s_keys[pos] = kv[j];
+      s_vals[pos] = v[j];
+    }
+  }
+  __syncthreads();
+  const uint32_t t0 = tile * kMsdTile;
+  const uint32_t tile_n = (n - t0) < kMsdTile ? (n - t0) : kMsdTile;
+  for (uint32_t i = tid; i < tile_n; i += kThreads) {
+    const uint32_t k = s_keys[i];
+    const uint32_t d = k >> 24;
+    const uint32_t dst = s_gbase[d] + (i - s_excl[d]);
+    if (dst < n) {
+      out_k[dst] = k;
+      out_v[dst] = s_vals[i];
+    }
+  }
+}
+
+// First position i in [0, m) with (a[i] >> 16) >= bin, a sorted.
+__device__ __forceinline__ uint32_t lower_bound_bin(const uint32_t* a, uint32_t m, uint32_t bin) {
+  uint32_t lo = 0, hi = m;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if ((a[mid] >> 16) < bin) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort(uint32_t* __restrict__ tmp_k,
+                                                              uint32_t* __restrict__ tmp_v,
+                                                              uint32_t* __restrict__ out_k,
+                                                              uint32_t* __restrict__ out_v,
+                                                              const uint32_t* __restrict__ ctl, uint32_t n,
+                                                              uint32_t* __restrict__ fence,
+                                                              uint32_t* __restrict__ next_ctl) {
+  extern __shared__ __align__(16) uint32_t bsm[];
+  __shared__ uint32_t s_whist[kBucketWarps][kRadix];
+  __shared__ uint32_t s_excl[kRadix], s_run[kRadix], s_tot[kRadix], s_scan[kBucketWarps];
+  uint32_t* ak = bsm;
+  uint32_t* av = bsm + kBucketCap;
+  uint32_t* bk = bsm + 2 * kBucketCap;
+  uint32_t* bv = bsm + 3 * kBucketCap;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5, d = blockIdx.x;
+  // the control block of the next sort starts zeroed (it is idle now)
+  if (d == 0)
+    for (uint32_t i = tid; i < uint32_t(kSortCtlWords); i += kBucketThreads) next_ctl[i] = 0u;
+  const uint32_t start = bucket_start<kBucketThreads>(ctl, d, s_scan);
+  const uint32_t m = ctl[3 * kRadix + d];
+  const uint32_t wbase = warp * (32 * kBucketIPT);
+  uint32_t kv[kBucketIPT], v[kBucketIPT], rank[kBucketIPT];
+
+  if (m <= kBucketCap) {
+    for (uint32_t i = tid; i < m; i += kBucketThreads) {
+      ak[i] = tmp_k[start + i];
+      av[i] = tmp_v[start + i];
+    }
+    __syncthreads();
+    uint32_t *sk = ak, *sv = av, *dk = bk, *dv = bv;
+    for (int pass = 0; pass < 3; ++pass) {
+      const int shift = 8 * pass;
+#pragma unroll
+      for (int j = 0; j < kBucketIPT; ++j) {
+        const uint32_t p = wbase + j * 32 + lane;
+        kv[j] = p < m ? sk[p] : 0u;
+        v[j] = p < m ? sv[p] : 0u;
+      }
+      rank_block<kBucketThreads, kBucketIPT>(kv, m, wbase, shift, rank, s_whist, s_excl, s_scan, nullptr);
+#pragma unroll
+      for (int j = 0; j < kBucketIPT; ++j) {
+        const uint32_t p = wbase + j * 32 + lane;
+        if (p < m) {
+          const uint32_t dg = (kv[j] >> shift) & 255u;
+          const uint32_t pos = s_excl[dg] + s_whist[warp][dg] + rank[j];
+          dk[pos] = kv[j];
+          dv[pos] = v[j];
+        }
+      }
+      __syncthreads();
+      uint32_t* t;
+      t = sk; sk = dk; dk = t;
+      t = sv; sv = dv; dv = t;
+    }
+    for (uint32_t i = tid; i < m; i += kBucketThreads) {
+      out_k[start + i] = sk[i];
+      out_v[start + i] = sv[i];
+    }
+    if (fence && tid < kRadix) fence[d * kRadix + tid] = start + lower_bound_bin(sk, m, d * kRadix + tid);
+  } else {
+    // Chunked: three stable passes over [start, start + m) through global
+    // memory, tmp -> out -> tmp -> out, kBucketCap elements at a time in order.
+    uint32_t* srck = tmp_k;
+    uint32_t* srcv = tmp_v;
+    uint32_t* dstk = out_k;
+    uint32_t* dstv = out_v;
+    for (int pass = 0; pass < 3; ++pass) {
+      const int shift = 8 * pass;
+      if (tid < kRadix) s_tot[tid] = 0;
+      __syncthreads();
+      for (uint32_t i = tid; i < m; i += kBucketThreads) atomicAdd(&s_tot[(srck[start + i] >> shift) & 255u], 1u);
+      __syncthreads();
+      uint32_t all;
+      const uint32_t ex = block_excl_scan<kBucketThreads>(tid < kRadix ? s_tot[tid] : 0u, s_scan, all);
+      if (tid < kRadix) s_run[tid] = ex;
+      __syncthreads();
+      for (uint32_t c0 = 0; c0 < m; c0 += kBucketCap) {
+        const uint32_t cm = (m - c0) < kBucketCap ? (m - c0) : kBucketCap;
+#pragma unroll
+        for (int j = 0; j < kBucketIPT; ++j) {
+          const uint32_t p = wbase + j * 32 + lane;
+          kv[j] = p < cm ? srck[start + c0 + p] : 0u;
+          v[j] = p < cm ? srcv[start + c0 + p] : 0u;
+        }
+        rank_block<kBucketThreads, kBucketIPT>(kv, cm, wbase, shift, rank, s_whist, s_excl, s_scan, s_tot);
+#pragma unroll
+        for (int j = 0; j < kBucketIPT; ++j) {
+          const uint32_t p = wbase + j * 32 + lane;
+          if (p < cm) {
+            const uint32_t dg = (kv[j] >> shift) & 255u;
+            const uint32_t pos = s_run[dg] + s_whist[warp][dg] + rank[j];
+            dstk[start + pos] = kv[j];
+            dstv[start + pos] = v[j];
+          }
+        }
+        __syncthreads();
+        if (tid < kRadix) s_run[tid] += s_tot[tid];
+        __syncthreads();
+      }
+      uint32_t* t;
+      t = srck; srck = dstk; dstk = t;
+      t = srcv; srcv = dstv; dstv = t;
+    }
+    // after three passes the data sits in out (tmp -> out -> tmp -> out)
+    if (fence && tid < kRadix) fence[d * kRadix + tid] = start + lower_bound_bin(out_k + start, m, d * kRadix + tid);
+  }
+  if (fence && d == kRadix - 1 && tid == 0) fence[kFenceBins] = n;
+}
+
 __global__ void __launch_bounds__(256) check_keys(const uint32_t* __restrict__ keys, uint64_t n,
                                                   uint32_t* status) {
   bool bad = false;
@@ -233,9 +544,45 @@ __global__ void __launch_bounds__(256) check_keys(const uint32_t* __restrict__ k
 
 }  // namespace
 
-cudaError_t sort_launch(const SortArgs& a, SortWorkspace& ws, cudaStream_t st, uint32_t* h_status,
+constexpr size_t kBucketSmem = 4 * size_t(kBucketCap) * sizeof(uint32_t);
+
+cudaError_t bucket_sort_launch(const SortArgs& a, SortWorkspace& ws, cudaStream_t st, uint32_t* status,
+                               cudaEvent_t ev) {
+  static bool attr_set = false;
+  cudaError_t e;
+  if (!attr_set) {
+    e = cudaFuncSetAttribute(bucket_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBucketSmem));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const uint32_t ntiles = (a.n + kMsdTile - 1) / kMsdTile;
+  uint32_t* tilecnt = ws.tilecnt;
+  uint32_t* tileoff = ws.tilecnt + kMsdTileWords / 2;
+  uint32_t* ctl = ws.ctl + ws.flip * kSortCtlWords;
+  uint32_t* next = ws.ctl + (ws.flip ^ 1) * kSortCtlWords;
+  Loader ld{a.mode, a.in_keys, a.in_vals, a.in_del, a.n_in, a.n};
+  count_launches(1);
+  msd_count<<<ntiles, kThreads, 0, st>>>(ld, tilecnt, ctl, status);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (status && (e = cudaEventRecord(ev, st)) != cudaSuccess) return e;
+  count_launches(1);
+  msd_offsets<<<kRadix, kThreads, 0, st>>>(tilecnt, ntiles, ctl, tileoff);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  count_launches(1);
+  msd_scatter<<<ntiles, kThreads, 0, st>>>(ld, tileoff, a.tmp_keys, a.tmp_vals);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  count_launches(1);
+  bucket_sort<<<kRadix, kBucketThreads, kBucketSmem, st>>>(a.tmp_keys, a.tmp_vals, a.out_keys, a.out_vals,
+                                                          ctl, a.n, a.fence, next);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  ws.flip ^= 1;
+  return cudaSuccess;
+}
+
+cudaError_t sort_launch(const SortArgs& a, SortWorkspace& ws, cudaStream_t st, uint32_t* status,
                         cudaEvent_t ev) {
   if (a.n == 0) return cudaSuccess;
+  if (a.n <= kMsdMaxN && ws.tilecnt) return bucket_sort_launch(a, ws, st, status, ev);
   const uint32_t ntiles = (a.n + kSortTile - 1) / kSortTile;
   if (ntiles > ws.max_tiles) return cudaErrorInvalidValue;
   cudaError_t e;
@@ -244,34 +591,36 @@ cudaError_t sort_launch(const SortArgs& a, SortWorkspace& ws, cudaStream_t st, u
     e = cudaMemsetAsync(ws.lookback, 0, sizeof(uint64_t) * kSortPasses * ws.max_tiles * kRadix, st);
     if (e != cudaSuccess) return e;
   }
-  e = cudaMemsetAsync(ws.ctl, 0, sizeof(uint32_t) * kSortCtlWords, st);
+  uint32_t* ctl = ws.ctl + ws.flip * kSortCtlWords;
+  e = cudaMemsetAsync(ctl, 0, sizeof(uint32_t) * kSortCtlWords, st);
   if (e != cudaSuccess) return e;
   Loader ld{a.mode, a.in_keys, a.in_vals, a.in_del, a.n_in, a.n};
   uint32_t hblocks = (a.n + 255) / 256;
   if (hblocks > 4 * 152) hblocks = 4 * 152;
   count_launches(1);
-  sort_histogram<<<hblocks, 256, 0, st>>>(ld, ws.ctl);
+  sort_histogram<<<hblocks, 256, 0, st>>>(ld, ctl, status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (h_status) {
-    e = cudaMemcpyAsync(h_status, ws.ctl + kSortCtlStatus, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return e;
-    if ((e = cudaEventRecord(ev, st)) != cudaSuccess) return e;
-  }
+  if (status && (e = cudaEventRecord(ev, st)) != cudaSuccess) return e;
   // in -> tmp -> out -> tmp -> out
   uint32_t* bk[2] = {a.tmp_keys, a.out_keys};
   uint32_t* bv[2] = {a.tmp_vals, a.out_vals};
   const size_t lb_stride = size_t(ws.max_tiles) * kRadix;
   count_launches(1);
-  sort_pass<true><<<ntiles, kThreads, 0, st>>>(ld, nullptr, nullptr, bk[0], bv[0], ws.ctl, ws.lookback,
+  sort_pass<true><<<ntiles, kThreads, 0, st>>>(ld, nullptr, nullptr, bk[0], bv[0], ctl, ws.lookback,
                                                 0, ws.epoch, ws.sticky);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int p = 1; p < kSortPasses; ++p) {
     count_launches(1);
     sort_pass<false><<<ntiles, kThreads, 0, st>>>(ld, bk[(p - 1) & 1], bv[(p - 1) & 1], bk[p & 1],
-                                                   bv[p & 1], ws.ctl, ws.lookback + p * lb_stride, p,
+                                                   bv[p & 1], ctl, ws.lookback + p * lb_stride, p,
                                                    ws.epoch, ws.sticky);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  // leave the next half zeroed, as the bucket path does
+  ws.flip ^= 1;
+  e = cudaMemsetAsync(ws.ctl + ws.flip * kSortCtlWords, 0, sizeof(uint32_t) * kSortCtlWords, st);
+  if (e != cudaSuccess) return e;
+  if (a.fence) return build_fence_launch(a.out_keys, a.n, a.fence, st);
   return cudaSuccess;
 }
 
@@ -307,17 +656,18 @@ namespace {
 
 constexpr uint32_t kNoAllocMaxPairs = LSM_SORT_NOALLOC_MAX_PAIRS;
 constexpr uint32_t kNoAllocTiles = (kNoAllocMaxPairs + kSortTile - 1) / kSortTile;
-constexpr size_t kNoAllocCtl = 1088;                    // >= kSortCtlWords, multiple of 64
+constexpr size_t kNoAllocCtl = 2112;                    // > 2 * kSortCtlWords, multiple of 64
 constexpr size_t kNoAllocSticky = kNoAllocCtl - 1;      // last ctl word: wait timeouts
 constexpr size_t kNoAllocTmpK = kNoAllocCtl;
 constexpr size_t kNoAllocTmpV = kNoAllocTmpK + kNoAllocMaxPairs;
 constexpr size_t kNoAllocLookback = kNoAllocTmpV + kNoAllocMaxPairs;   // u64 words from here
 constexpr size_t kNoAllocLookbackWords = size_t(kSortPasses) * kNoAllocTiles * 256;
-constexpr size_t kNoAllocWords = kNoAllocLookback + 2 * kNoAllocLookbackWords;
-static_assert(kNoAllocCtl > size_t(kSortCtlWords), "control block fits");
+constexpr size_t kNoAllocTileCnt = kNoAllocLookback + 2 * kNoAllocLookbackWords;
+constexpr size_t kNoAllocWords = kNoAllocTileCnt + kMsdTileWords;
+static_assert(kNoAllocCtl > 2 * size_t(kSortCtlWords), "both control halves and the sticky word fit");
 static_assert(kNoAllocLookback % 2 == 0, "look-back words 8-byte aligned");
 
-// The scratch itself: about 10.5 MB for kNoAllocMaxPairs = 2^20.
+// The scratch itself: about 11 MB for kNoAllocMaxPairs = 2^20.
 static __device__ __align__(256) uint32_t g_sort_scratch[kNoAllocWords];
 
 constexpr int kNoAllocMaxDevices = 64;
@@ -364,7 +714,9 @@ extern "C" lsm_status lsm_sort_pairs_noalloc(const uint32_t* d_keys_in, const ui
     d.ws.lookback = reinterpret_cast<uint64_t*>(base + kNoAllocLookback);
     d.ws.max_tiles = kNoAllocTiles;
     d.ws.epoch = 0;
+    d.ws.flip = 0;
     d.ws.sticky = base + kNoAllocSticky;
+    d.ws.tilecnt = base + kNoAllocTileCnt;
     d.base = base;
   }
   SortArgs a{};
@@ -377,8 +729,8 @@ extern "C" lsm_status lsm_sort_pairs_noalloc(const uint32_t* d_keys_in, const ui
   a.out_vals = d_vals_out;
   a.tmp_keys = d.base + kNoAllocTmpK;
   a.tmp_vals = d.base + kNoAllocTmpV;
-  // sort_launch clears the histogram/counter block itself on every call and
-  // tags look-back words with a per-call epoch, so nothing else needs zeroing.
+  // Each sort leaves the control block of the next one zeroed and tags its
+  // look-back words with a per-call epoch, so nothing else needs zeroing.
   cudaError_t e = sort_launch(a, d.ws, st, nullptr, nullptr);
   if (e != cudaSuccess) {
     cudaGetLastError();

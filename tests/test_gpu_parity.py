@@ -89,7 +89,7 @@ def test_walkthrough_on_gpu(g):
 
 
 # -------------------------------------------------------------------- sort --
-@pytest.mark.parametrize("n", [1, 2, 31, 4095, 4096, 4097, 12345, 1 << 16, (1 << 20) - 3])
+@pytest.mark.parametrize("n", [1, 2, 31, 4095, 4096, 4097, 12345, 1 << 16, (1 << 20) - 3, 1 << 20, 3 << 20])
 def test_sort_pairs_matches_stable_sort(g, n):
     lsm = g.LSM(max(n, 1), max(n, 1))
     rng = np.random.default_rng(n)
@@ -157,7 +157,8 @@ def random_calls(rng, b, ncalls, key_space):
 
 @pytest.mark.parametrize("b,key_space,ncalls", [(1, 8, 40), (2, 16, 40), (3, 30, 30), (5, 50, 30),
                                                  (17, 200, 25), (100, 3000, 20), (1000, 1 << 20, 12),
-                                                 (3000, 1 << 12, 12), (4096, (1 << 31) - 1, 10)])
+                                                 (3000, 1 << 12, 12), (4096, (1 << 31) - 1, 10),
+                                                 (1 << 14, 1 << 20, 6)])
 def test_random_logs_bit_exact(g, b, key_space, ncalls):
     rng = np.random.default_rng(b * 7919 + key_space)
     calls = random_calls(rng, b, ncalls, min(key_space, (1 << 31) - 1))

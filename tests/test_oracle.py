@@ -272,3 +272,25 @@ def test_cleanup_model(b):
         for q in range(32):
             ev, ef = o1.lookup([q])
             assert levels_lookup(lv, q) == (int(ef[0]), int(ev[0]))
+
+
+# ------------------------------------------------- single-level closed form --
+@pytest.mark.parametrize("b,nb", [(1, 8), (3, 4), (4, 16), (16, 32), (5, 2)])
+def test_single_level_closed_form_matches_structural_replay(b, nb):
+    """With 2^m resident batches all elements sit in level m (§III-B); the
+    closed form (key asc, batch desc, tombstone first, later op first) must
+    equal the literal cascade of Fig. 2(a) / Fig. 3."""
+    g = np.random.default_rng(77 + b * nb)
+    calls = []
+    for _ in range(nb):
+        n = int(g.integers(1, b + 1))
+        calls.append(("update", g.integers(0, 6 * b, size=n).astype(np.uint32),
+                      g.integers(0, 1000, size=n).astype(np.uint32), (g.random(n) < 0.3).astype(np.uint8)))
+    s = oracle.StructuralOracle(b)
+    for c in calls:
+        s.call(*c)
+    m = nb.bit_length() - 1
+    kv, v = oracle.single_level(calls, b)
+    ekv, ev = s.level(m)
+    np.testing.assert_array_equal(kv, ekv)
+    np.testing.assert_array_equal(v, ev)
