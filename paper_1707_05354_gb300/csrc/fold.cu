@@ -10,38 +10,45 @@
 // k - 1 (newest to oldest).  Here that merge is done in one pass straight into
 // level k: every element is read once and written once.
 //
-//   fold_partition  one warp per output tile boundary p = t * 4096 finds the
-//                   co-rank vector (how many elements of each source precede
-//                   position p).  The sources' prefix indexes (fences) give
-//                   the 2^15-key bin holding the p-th element in a few probes;
-//                   a bisection over the low 15 key bits inside that bin,
-//                   each lane keeping a bracket in its own source, finds the
-//                   key; the elements of that key are then split among the
-//                   sources in rank order.
-//   fold_merge      one CTA per tile: the TMA engine copies the k + 1 source
-//                   segments into shared memory (16-byte aligned supersets);
-//                   a left-deep chain of merge-path merges in shared memory
-//                   (ranks 0 and 1, then the result with rank 2, ...; ties to
-//                   the lower rank) builds the tile as (key, value) pairs in
-//                   an XOR-swizzled layout, and the tile is written out
-//                   coalesced.  The plain fold also writes the new level's
-//                   prefix index.
+//   partition   one warp per output tile boundary p finds the co-rank vector
+//               (how many elements of each source precede position p).  The
+//               sources' prefix indexes (fences) give the 2^15-key bin
+//               holding the p-th element in a few probes; a bisection over
+//               the low 15 key bits inside that bin, each lane keeping a
+//               bracket in its own source, finds the key; the elements of
+//               that key are then split among the sources in rank order.
+//   merge       one tile per CTA: the TMA engine copies the k + 1 source
+//               segments into shared memory (16-byte aligned supersets); a
+//               left-deep chain of merge-path merges in shared memory (ranks
+//               0 and 1, then the result with rank 2, ...; ties to the lower
+//               rank) builds the tile as (key, value) pairs in an
+//               XOR-swizzled layout, the last step keeping its outputs in
+//               registers, which are written out with 16-byte stores.  The
+//               plain fold also writes the new level's prefix index.
 // Cleanup uses the same two kernels over all full levels; the merge then keeps
 // only the first element of every key when it is regular and compacts the
 // survivors with a decoupled look-back scan across tiles.
+//
+// The batched form (many dictionaries, one batch each per round) runs the
+// same partition and tile merge for every (instance, tile): a partition
+// kernel over all boundaries of all instances and a persistent merge kernel
+// whose CTAs take (instance, tile) work items from an atomic counter.
 #include "lsm_device.cuh"
 
 namespace gpulsm {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr uint32_t kMinPer = 8;
-constexpr uint32_t kSlotCap = (kFoldTile + 8 * kMaxSources + 15) / 16 * 16;  // TMA slots + alignment slack
-static_assert(kSlotCap % 16 == 0, "16-byte aligned buffers");
-static_assert(kFoldTile % kThreads == 0 && kFoldTile / kThreads <= 32, "keep bits per thread");
-constexpr size_t kMergeSmem = 2 * size_t(kSlotCap) * sizeof(uint32_t) + 2 * size_t(kFoldTile) * sizeof(uint2);
-
 constexpr uint64_t kLbAgg = 1ull << 62, kLbIncl = 2ull << 62, kLbMask = (1ull << 62) - 1;
+
+// Tile geometry for E outputs per thread per merge step.
+template <int E>
+struct TileGeom {
+  static constexpr uint32_t kTile = kThreads * E;
+  static constexpr uint32_t kSlotCap = (kTile + 8 * kMaxSources + 15) / 16 * 16;  // TMA slots + slack
+  static constexpr size_t kSmem = 2 * size_t(kSlotCap) * sizeof(uint32_t) + 2 * size_t(kTile) * sizeof(uint2);
+};
+static_assert(TileGeom<8>::kTile == kFoldTile, "the plain fold uses 8 outputs per thread");
 
 // Slot of pair q of a merge step in shared memory: q with its low 4 bits
 // XORed by bits 4..7.  A thread writing 8 consecutive pairs (q = 8 t + e)
@@ -50,40 +57,31 @@ constexpr uint64_t kLbAgg = 1ull << 62, kLbIncl = 2ull << 62, kLbMask = (1ull <<
 // consecutive pairs stay a permutation of one 128-byte row.
 __device__ __forceinline__ uint32_t psw(uint32_t q) { return q ^ ((q >> 4) & 15u); }
 
-// Sum over the sources of fence_j[P] (lanes >= S contribute 0).
-__device__ __forceinline__ uint64_t fence_sum(const uint32_t* f, bool act, uint32_t P) {
-  return warp_sum<uint64_t>(act ? __ldg(f + P) : 0u);
+// Sum over the sources of fence_j at 16-bit bin P (lanes >= S contribute 0);
+// cs = 16 - fshift of the lane's source.
+__device__ __forceinline__ uint64_t fence_sum(const uint32_t* f, bool act, uint32_t P, int cs, int fs,
+                                              uint32_t n) {
+  return warp_sum<uint64_t>(act ? fence_at(f, fs, n, P << cs) : 0u);
 }
 
-__global__ void __launch_bounds__(256) fold_partition(FoldSources src, uint64_t total, uint32_t ntiles,
-                                                      uint32_t* __restrict__ part) {
-  const uint32_t t = (blockIdx.x * 256u + threadIdx.x) >> 5;
-  if (t > ntiles) return;  // whole warp leaves together
-  const uint32_t lane = lane_id();
-  const int S = src.count;
-  const bool act = lane < uint32_t(S);
-  const uint32_t n = act ? src.n[lane] : 0u;
-  const uint32_t* a = act ? src.keys[lane] : nullptr;
-  const uint32_t* f = act ? src.fence[lane] : nullptr;
-  const uint64_t p = uint64_t(t) * kFoldTile < total ? uint64_t(t) * kFoldTile : total;
-  uint32_t* out = part + uint64_t(t) * S;
-  if (p >= total) {
-    if (act) out[lane] = n;
-    return;
-  }
+// This lane's co-rank at output position p < total (warp-collective; lane j
+// holds source j when act).
+__device__ __forceinline__ uint32_t corank_lane(bool act, const uint32_t* a, const uint32_t* f, int fs,
+                                                uint32_t n, uint64_t p, uint64_t total) {
+  const int cs = 16 - fs;
   // 1. The bin: largest P with C(P) <= p, C(P) = sum of fence_j[P]
   //    (C(0) = 0 <= p < C(65536) = total).  Start from the proportional
   //    guess, gallop to a bracket, then bisect.
   uint32_t lo, hi;
   {
-    uint32_t g = uint32_t((p * kFenceBins) / total);
-    if (g >= kFenceBins) g = kFenceBins - 1;
-    if (fence_sum(f, act, g) <= p) {
+    uint32_t g = uint32_t((p * kFenceBins16) / total);
+    if (g >= kFenceBins16) g = kFenceBins16 - 1;
+    if (fence_sum(f, act, g, cs, fs, n) <= p) {
       lo = g;
       uint32_t step = 1;
       while (true) {
-        hi = lo + step < kFenceBins ? lo + step : kFenceBins;
-        if (hi == kFenceBins || fence_sum(f, act, hi) > p) break;
+        hi = lo + step < kFenceBins16 ? lo + step : kFenceBins16;
+        if (hi == kFenceBins16 || fence_sum(f, act, hi, cs, fs, n) > p) break;
         lo = hi;
         step <<= 1;
       }
@@ -92,19 +90,19 @@ __global__ void __launch_bounds__(256) fold_partition(FoldSources src, uint64_t 
       uint32_t step = 1;
       while (true) {
         lo = hi > step ? hi - step : 0u;
-        if (lo == 0 || fence_sum(f, act, lo) <= p) break;
+        if (lo == 0 || fence_sum(f, act, lo, cs, fs, n) <= p) break;
         hi = lo;
         step <<= 1;
       }
     }
     while (hi - lo > 1) {
       const uint32_t mid = (lo + hi) >> 1;
-      if (fence_sum(f, act, mid) <= p) lo = mid; else hi = mid;
+      if (fence_sum(f, act, mid, cs, fs, n) <= p) lo = mid; else hi = mid;
     }
   }
   // 2. Smallest key x in the bin with #{key <= x} > p.  Invariant per lane:
   //    blo = #{key <= xlo - 1}, bhi = #{key <= xhi} in this lane's source.
-  uint32_t blo = act ? __ldg(f + lo) : 0u, bhi = act ? __ldg(f + lo + 1) : 0u;
+  uint32_t blo = act ? fence_at(f, fs, n, lo << cs) : 0u, bhi = act ? fence_at(f, fs, n, (lo + 1) << cs) : 0u;
   uint32_t xlo = lo << 15, xhi = ((lo + 1) << 15) - 1;
   while (xlo < xhi) {
     const uint32_t mid = xlo + ((xhi - xlo) >> 1);
@@ -125,27 +123,101 @@ __global__ void __launch_bounds__(256) fold_partition(FoldSources src, uint64_t 
   const uint64_t excl = warp_incl_scan<uint64_t>(cnt) - cnt;
   uint64_t take = 0;
   if (need > excl) take = (need - excl) < cnt ? (need - excl) : cnt;
-  if (act) out[lane] = blo + uint32_t(take);
+  return blo + uint32_t(take);
+}
+
+__global__ void __launch_bounds__(256) fold_partition(FoldSources src, uint64_t total, uint32_t ntiles,
+                                                      uint32_t tile, uint32_t* __restrict__ part) {
+  const uint32_t t = (blockIdx.x * 256u + threadIdx.x) >> 5;
+  if (t > ntiles) return;  // whole warp leaves together
+  const uint32_t lane = lane_id();
+  const int S = src.count;
+  const bool act = lane < uint32_t(S);
+  const uint32_t n = act ? src.n[lane] : 0u;
+  const uint64_t p = uint64_t(t) * tile < total ? uint64_t(t) * tile : total;
+  uint32_t* out = part + uint64_t(t) * S;
+  if (p >= total) {
+    if (act) out[lane] = n;
+    return;
+  }
+  const uint32_t c = corank_lane(act, act ? src.keys[lane] : nullptr, act ? src.fence[lane] : nullptr,
+                                 act ? src.fshift[lane] : 16, n, p, total);
+  if (act) out[lane] = c;
+}
+
+// Sources of instance i's fold in round k: its sorted batch, then levels
+// 0 .. k-1 (lane j describes source j).
+__device__ __forceinline__ void multi_source(const MultiArena& ar, const MultiInst& in, int j,
+                                             const uint32_t*& keys, const uint32_t*& vals, const uint32_t*& fence,
+                                             uint32_t& n, int& fshift) {
+  if (j == 0) {
+    keys = ar.bkeys + in.boff;
+    vals = ar.bvals + in.boff;
+    fence = ar.fence + in.batch_fence;
+    n = in.b;
+    fshift = in.fshift_batch;
+  } else {
+    keys = ar.keys + in.lvl_off[j - 1];
+    vals = ar.vals + in.lvl_off[j - 1];
+    fence = ar.fence + in.lvl_fence[j - 1];
+    n = in.b << (j - 1);
+    fshift = in.lvl_fshift[j - 1];
+  }
+}
+
+// Largest i with prefix[i] + i * extra <= w (prefix has n + 1 entries).
+__device__ __forceinline__ uint32_t find_instance(const uint64_t* prefix, uint32_t n, uint64_t w, uint64_t extra) {
+  uint32_t lo = 0, hi = n;  // answer in [lo, hi)
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (prefix[mid] + mid * extra <= w) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) multi_partition(MultiFoldArgs a) {
+  const uint64_t w = (uint64_t(blockIdx.x) * 256u + threadIdx.x) >> 5;
+  const uint32_t n_inst = a.ar.n;
+  if (w >= a.total_tiles + n_inst) return;  // whole warp leaves together
+  const uint32_t i = find_instance(a.tile_prefix, n_inst, w, 1);
+  const MultiInst& in = a.ar.inst[i];
+  const uint32_t t = uint32_t(w - (a.tile_prefix[i] + i));
+  const uint32_t lane = lane_id();
+  const int S = a.k + 1;
+  const bool act = lane < uint32_t(S);
+  const uint32_t *keys = nullptr, *vals = nullptr, *fence = nullptr;
+  uint32_t n = 0;
+  int fs = 16;
+  if (act) multi_source(a.ar, in, int(lane), keys, vals, fence, n, fs);
+  const uint64_t total = uint64_t(in.b) << a.k;
+  const uint64_t p = uint64_t(t) * a.tile < total ? uint64_t(t) * a.tile : total;
+  uint32_t* out = a.part + (a.tile_prefix[i] + i + t) * S;
+  if (p >= total) {
+    if (act) out[lane] = n;
+    return;
+  }
+  const uint32_t c = corank_lane(act, keys, fence, fs, n, p, total);
+  if (act) out[lane] = c;
 }
 
 // One merge step of the tile: output[0, nA + nB) = merge of run A (the
 // newer ranks) and run B (the next rank), ties to A.  B always sits in the
 // TMA slot area (separate key and value arrays); A is either there too (the
 // first step) or the (key, value) pair buffer X written by the step before.
-// Each thread produces ceil(m / 256) consecutive outputs after a merge-path
-// search for its first one; outputs go to the pair buffer Y, swizzled.
-template <bool kAFromSlot>
+// Thread t produces outputs [E t, E t + E) after a merge-path search for its
+// first one (threads past the end idle); the outputs go to the swizzled pair
+// buffer Y, or stay in registers (kToRegs) when this is the last step.
+// An exhausted run's head key becomes kSentinel, above every key, so the
+// choice of each output is a single comparison.
+constexpr uint32_t kSentinel = 0x80000000u;
+
+template <int E, bool kAFromSlot, bool kToRegs>
 __device__ __forceinline__ void merge_step(const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv,
                                            const uint2* __restrict__ X, uint2* __restrict__ Y, uint32_t aS,
-                                           uint32_t nA, uint32_t bS, uint32_t nB) {
+                                           uint32_t nA, uint32_t bS, uint32_t nB, uint2 (&out)[E]) {
   const uint32_t m = nA + nB;
-  // at least kMinPer outputs per working thread: each thread pays one
-  // merge-path search, so small steps use few threads
-  uint32_t per = (m + kThreads - 1) / kThreads;
-  per = per < kMinPer ? kMinPer : per;
-  const uint32_t q0 = threadIdx.x * per;
+  const uint32_t q0 = threadIdx.x * E;
   if (q0 >= m) return;
-  const uint32_t q1 = q0 + per < m ? q0 + per : m;
   const uint32_t* xk = reinterpret_cast<const uint32_t*>(X);
   auto keyA = [&](uint32_t i) { return kAFromSlot ? sk[aS + i] : xk[2 * psw(i)]; };
   auto pairA = [&](uint32_t i) { return kAFromSlot ? make_uint2(sk[aS + i], sv[aS + i]) : X[psw(i)]; };
@@ -156,55 +228,72 @@ __device__ __forceinline__ void merge_step(const uint32_t* __restrict__ sk, cons
     if (key_of(keyA(mid)) <= key_of(sk[bS + q0 - 1 - mid])) lo = mid + 1; else hi = mid;
   }
   uint32_t ia = lo, ib = q0 - lo;
-  uint2 a = ia < nA ? pairA(ia) : make_uint2(0u, 0u);
-  uint2 b = ib < nB ? make_uint2(sk[bS + ib], sv[bS + ib]) : make_uint2(0u, 0u);
-  for (uint32_t q = q0; q < q1; ++q) {
-    const bool take_a = ia < nA && (ib >= nB || key_of(a.x) <= key_of(b.x));
-    if (take_a) {
-      Y[psw(q)] = a;
-      if (++ia < nA) a = pairA(ia);
-    } else {
-      Y[psw(q)] = b;
-      if (++ib < nB) b = make_uint2(sk[bS + ib], sv[bS + ib]);
+  uint2 a = make_uint2(0u, 0u), b = make_uint2(0u, 0u);
+  uint32_t ka = kSentinel, kb = kSentinel;
+  if (ia < nA) {
+    a = pairA(ia);
+    ka = key_of(a.x);
+  }
+  if (ib < nB) {
+    b = make_uint2(sk[bS + ib], sv[bS + ib]);
+    kb = key_of(b.x);
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    if (q0 + e < m) {
+      const bool take_a = ka <= kb;
+      const uint2 o = take_a ? a : b;
+      if (kToRegs) out[e] = o;
+      else Y[psw(q0 + e)] = o;
+      if (take_a) {
+        if (++ia < nA) {
+          a = pairA(ia);
+          ka = key_of(a.x);
+        } else {
+          ka = kSentinel;
+        }
+      } else {
+        if (++ib < nB) {
+          b = make_uint2(sk[bS + ib], sv[bS + ib]);
+          kb = key_of(b.x);
+        } else {
+          kb = kSentinel;
+        }
+      }
     }
   }
 }
 
-template <bool kCleanup>
-__global__ void __launch_bounds__(kThreads) fold_merge(FoldSources src, uint64_t total,
-                                                       const uint32_t* __restrict__ part,
-                                                       uint32_t* __restrict__ out_k,
-                                                       uint32_t* __restrict__ out_v,
-                                                       uint32_t* __restrict__ out_fence, uint32_t* status,
-                                                       uint64_t* lookback, uint32_t* tile_ctr,
-                                                       uint64_t* out_count, uint32_t ntiles) {
-  extern __shared__ __align__(128) uint32_t sm[];
-  __shared__ __align__(8) uint64_t s_bar;
-  __shared__ uint32_t s_rstart[kMaxSources], s_rlen[kMaxSources];
-  __shared__ uint32_t s_a0[kMaxSources], s_span[kMaxSources], s_slot[kMaxSources];
-  __shared__ uint32_t s_scan[kThreads / 32];
-  __shared__ uint32_t s_tile, s_prev_key, s_ok;
-  __shared__ uint64_t s_prefix;
+// Shared state of the tile merge (static shared memory of the kernels).
+struct MergeShared {
+  uint32_t rstart[kMaxSources], rlen[kMaxSources];
+  uint32_t a0[kMaxSources], span[kMaxSources], slot[kMaxSources];
+  uint32_t scan[kThreads / 32], last[kThreads / 32];
+  uint32_t prev_key, ok, ngap, landed;
+  FenceGap gaps[kFenceGapSlots];
+  uint64_t prefix;
+};
 
+// Merge tile `tile` of a fold whose sources are `src` (rank order), whose
+// co-ranks are part[(tile) * S + j] .. part[(tile + 1) * S + j], into
+// out_k/out_v.  `bar` is an initialised mbarrier; `parity` the phase this
+// tile's copies complete.  Returns false if a copy never arrived (the CTA
+// must then stop).  Called by all threads of the CTA.
+template <int E, bool kCleanup>
+__device__ __forceinline__ bool merge_tile(const FoldSources& src, uint64_t total, const uint32_t* __restrict__ part,
+                                           uint32_t tile, uint32_t ntiles, uint32_t* __restrict__ out_k,
+                                           uint32_t* __restrict__ out_v, uint32_t* __restrict__ out_fence,
+                                           int fshift, uint32_t* status, uint64_t* lookback, uint64_t* out_count,
+                                           uint32_t* sm, MergeShared& sh, uint64_t* bar, uint32_t parity) {
+  using G = TileGeom<E>;
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const int S = src.count;
-  if (kCleanup) {
-    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
-  } else if (tid == 0) {
-    s_tile = blockIdx.x;
-  }
-  if (tid == 0) {
-    mbar_init(&s_bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  const uint64_t obase = uint64_t(tile) * kFoldTile;
-  const uint32_t tile_n = uint32_t((total - obase) < kFoldTile ? (total - obase) : kFoldTile);
-  uint32_t* sk = sm;                                          // slot keys
-  uint32_t* sv = sm + kSlotCap;                               // slot values
-  uint2* X = reinterpret_cast<uint2*>(sm + 2 * kSlotCap);     // pair buffers
-  uint2* Y = X + kFoldTile;
+  const uint64_t obase = uint64_t(tile) * G::kTile;
+  const uint32_t tile_n = uint32_t((total - obase) < G::kTile ? (total - obase) : G::kTile);
+  uint32_t* sk = sm;                                           // slot keys
+  uint32_t* sv = sm + G::kSlotCap;                             // slot values
+  uint2* X = reinterpret_cast<uint2*>(sm + 2 * G::kSlotCap);   // pair buffers
+  uint2* Y = X + G::kTile;
 
   // Segment of each source in this tile, and its 16-byte aligned superset.
   if (warp == 0) {
@@ -224,11 +313,11 @@ __global__ void __launch_bounds__(kThreads) fold_merge(FoldSources src, uint64_t
     }
     const uint32_t slot = warp_incl_scan(span) - span;
     if (lane < uint32_t(S)) {
-      s_rstart[lane] = slot + (c0 - a0);
-      s_rlen[lane] = c1 - c0;
-      s_a0[lane] = a0;
-      s_span[lane] = span;
-      s_slot[lane] = slot;
+      sh.rstart[lane] = slot + (c0 - a0);
+      sh.rlen[lane] = c1 - c0;
+      sh.a0[lane] = a0;
+      sh.span[lane] = span;
+      sh.slot[lane] = slot;
     }
     // Key of the element just before this tile in merged order: the largest
     // key among the sources' last elements before their co-ranks.
@@ -236,119 +325,158 @@ __global__ void __launch_bounds__(kThreads) fold_merge(FoldSources src, uint64_t
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const bool any_prev = __any_sync(0xffffffffu, has_prev);
-    if (lane == 0) s_prev_key = any_prev ? mx : 0xFFFFFFFFu;  // no key equals 2^32 - 1
+    if (lane == 0) {
+      sh.prev_key = any_prev ? mx : 0xFFFFFFFFu;  // no key equals 2^32 - 1
+      sh.ngap = 0;
+    }
   }
   __syncthreads();
 
-  // Stage the segments with the TMA engine (one thread issues, all wait).
+  // Stage the segments with the TMA engine (one thread issues and waits).
   if (tid == 0) {
     uint32_t bytes = 0, ok = 1;
     for (int r = 0; r < S; ++r) {
-      if (!s_span[r]) continue;
-      const uintptr_t gk = reinterpret_cast<uintptr_t>(src.keys[r] + s_a0[r]);
-      const uintptr_t gv = reinterpret_cast<uintptr_t>(src.vals[r] + s_a0[r]);
+      if (!sh.span[r]) continue;
+      const uintptr_t gk = reinterpret_cast<uintptr_t>(src.keys[r] + sh.a0[r]);
+      const uintptr_t gv = reinterpret_cast<uintptr_t>(src.vals[r] + sh.a0[r]);
       if ((gk | gv) & 15u) ok = 0;
-      bytes += 2u * s_span[r] * 4u;
+      bytes += 2u * sh.span[r] * 4u;
     }
-    s_ok = ok;
+    sh.ok = ok;
     if (!ok) {
       atomicOr(status, kErrAlign);
       bytes = 0;
     }
-    mbar_arrive_expect_tx(&s_bar, bytes);
+    mbar_arrive_expect_tx(bar, bytes);
     if (ok) {
       for (int r = 0; r < S; ++r) {
-        if (!s_span[r]) continue;
-        bulk_g2s(sk + s_slot[r], src.keys[r] + s_a0[r], s_span[r] * 4u, &s_bar);
-        bulk_g2s(sv + s_slot[r], src.vals[r] + s_a0[r], s_span[r] * 4u, &s_bar);
+        if (!sh.span[r]) continue;
+        bulk_g2s(sk + sh.slot[r], src.keys[r] + sh.a0[r], sh.span[r] * 4u, bar);
+        bulk_g2s(sv + sh.slot[r], src.vals[r] + sh.a0[r], sh.span[r] * 4u, bar);
       }
     }
+    // One thread waits for the copies (bounded); the barrier below then
+    // releases the CTA, so the other threads do not spin on the mbarrier.
+    sh.landed = mbar_wait_bounded(bar, parity, status) ? 1u : 0u;
   }
-  const bool landed = mbar_wait_bounded(&s_bar, 0, status);
   __syncthreads();
-  if (!s_ok) {  // never expected: plain loads instead of the bulk copies
+  const bool landed = sh.landed != 0;
+  // each thread acquires the completed phase itself (returns at once)
+  if (landed) mbar_try_wait(bar, parity);
+  if (!sh.ok) {  // never expected: plain loads instead of the bulk copies
     for (int r = 0; r < S; ++r)
-      for (uint32_t i = tid; i < s_span[r]; i += kThreads) {
-        sk[s_slot[r] + i] = __ldg(src.keys[r] + s_a0[r] + i);
-        sv[s_slot[r] + i] = __ldg(src.vals[r] + s_a0[r] + i);
+      for (uint32_t i = tid; i < sh.span[r]; i += kThreads) {
+        sk[sh.slot[r] + i] = __ldg(src.keys[r] + sh.a0[r] + i);
+        sv[sh.slot[r] + i] = __ldg(src.vals[r] + sh.a0[r] + i);
       }
     __syncthreads();
   }
   if (!__syncthreads_and(landed)) {
     // A copy never completed; give it one more bounded wait before leaving
     // so that no transfer lands in shared memory after this CTA is gone.
-    if (tid == 0) mbar_wait_bounded(&s_bar, 0, status);
-    return;
+    if (tid == 0) mbar_wait_bounded(bar, parity, status);
+    return false;
   }
 
   // Left-deep merge order: X = run 0 + run 1, then X = X + run r for each
-  // further rank.  Runs grow with their rank (the batch and level 0 are the
-  // smallest), so every element moves about twice in all.
-  if (S == 1) {
-    merge_step<true>(sk, sv, nullptr, X, s_rstart[0], s_rlen[0], 0u, 0u);
+  // further rank; the last step keeps its E outputs per thread in registers.
+  // Runs grow with their rank (the batch and level 0 are the smallest), so
+  // every element moves about twice in all.
+  uint2 out[E];
+  if (S <= 2) {
+    merge_step<E, true, true>(sk, sv, nullptr, nullptr, sh.rstart[0], sh.rlen[0], S == 2 ? sh.rstart[1] : 0u,
+                              S == 2 ? sh.rlen[1] : 0u, out);
   } else {
-    merge_step<true>(sk, sv, nullptr, X, s_rstart[0], s_rlen[0], s_rstart[1], s_rlen[1]);
-  }
-  uint32_t m = s_rlen[0] + (S > 1 ? s_rlen[1] : 0u);
-  for (int r = 2; r < S; ++r) {
+    merge_step<E, true, false>(sk, sv, nullptr, X, sh.rstart[0], sh.rlen[0], sh.rstart[1], sh.rlen[1], out);
+    uint32_t m = sh.rlen[0] + sh.rlen[1];
+    for (int r = 2; r < S - 1; ++r) {
+      __syncthreads();
+      merge_step<E, false, false>(sk, sv, X, Y, 0u, m, sh.rstart[r], sh.rlen[r], out);
+      m += sh.rlen[r];
+      uint2* t = X;
+      X = Y;
+      Y = t;
+    }
     __syncthreads();
-    merge_step<false>(sk, sv, X, Y, 0u, m, s_rstart[r], s_rlen[r]);
-    m += s_rlen[r];
-    uint2* t = X;
-    X = Y;
-    Y = t;
+    merge_step<E, false, true>(sk, sv, X, nullptr, 0u, m, sh.rstart[S - 1], sh.rlen[S - 1], out);
   }
+  // Outputs q0 .. q0 + cnt - 1 are in out[]; the key before q0 in merged
+  // order comes from the thread before (a shuffle, or across warps through
+  // shared memory), or from before the tile.
+  const uint32_t q0 = tid * E;
+  const uint32_t cnt = q0 < tile_n ? ((tile_n - q0) < uint32_t(E) ? (tile_n - q0) : uint32_t(E)) : 0u;
+  uint32_t last = 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+    if (uint32_t(e) < cnt) last = out[e].x;
+  uint32_t prev_kv = __shfl_up_sync(0xffffffffu, last, 1);
+  if (lane == 31) sh.last[warp] = last;
   __syncthreads();
-  const uint32_t* xk = reinterpret_cast<const uint32_t*>(X);
+  if (lane == 0 && warp > 0) prev_kv = sh.last[warp - 1];
+  const bool has_prev = tid > 0 || sh.prev_key != 0xFFFFFFFFu;
+  // for tid 0 the previous element is the one before the tile: only its key
+  // (and so its bin) matters; rebuild a key variable with that key
+  if (tid == 0) prev_kv = sh.prev_key << 1;
 
   if (!kCleanup) {
-    // Write the tile (coalesced) and, when asked, the new level's prefix
-    // index: for every bin P after the previous element's bin up to this
-    // element's bin, fence[P] = this element's position; the last element of
-    // the fold closes the table up to bin 65536.
-    const int first_prev_bin = s_prev_key == 0xFFFFFFFFu ? -1 : int(s_prev_key >> 15);
-    for (uint32_t base = warp * 32; base < tile_n; base += kThreads) {
-      const uint32_t q = base + lane;
-      const bool valid = q < tile_n;
-      const uint2 p = valid ? X[psw(q)] : make_uint2(0u, 0u);
-      if (valid) {
-        out_k[obase + q] = p.x;
-        out_v[obase + q] = p.y;
+    if (cnt == uint32_t(E) && (E % 4) == 0 &&
+        ((reinterpret_cast<uintptr_t>(out_k + obase + q0) | reinterpret_cast<uintptr_t>(out_v + obase + q0)) &
+         15u) == 0) {
+      uint4* ok4 = reinterpret_cast<uint4*>(out_k + obase + q0);
+      uint4* ov4 = reinterpret_cast<uint4*>(out_v + obase + q0);
+#pragma unroll
+      for (int c = 0; c < E / 4; ++c) {
+        ok4[c] = make_uint4(out[4 * c].x, out[4 * c + 1].x, out[4 * c + 2].x, out[4 * c + 3].x);
+        ov4[c] = make_uint4(out[4 * c].y, out[4 * c + 1].y, out[4 * c + 2].y, out[4 * c + 3].y);
       }
-      if (out_fence) {
-        uint32_t kprev = __shfl_up_sync(0xffffffffu, p.x, 1);
-        if (lane == 0 && base > 0) kprev = xk[2 * psw(base - 1)];
-        if (valid) {
-          const int bin = int(fence_bin(p.x));
-          const int pb = q ? int(fence_bin(kprev)) : first_prev_bin;
-          for (int P = pb + 1; P <= bin; ++P) out_fence[P] = uint32_t(obase + q);
-          if (obase + q + 1 == total)
-            for (uint32_t P = uint32_t(bin) + 1; P <= kFenceBins; ++P) out_fence[P] = uint32_t(total);
+    } else {
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (uint32_t(e) < cnt) {
+          out_k[obase + q0 + e] = out[e].x;
+          out_v[obase + q0 + e] = out[e].y;
+        }
+    }
+    if (out_fence) {
+      // Prefix index of the new level: the element at position pos owns the
+      // entries between the previous element's bin and its own; the first and
+      // last elements record the populated bin range instead of the edges.
+      const uint32_t nb = fence_bins(fshift);
+      uint32_t pb = has_prev ? fence_bin(prev_kv, fshift) : 0u;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        if (uint32_t(e) < cnt) {
+          const uint32_t bin = fence_bin(out[e].x, fshift);
+          const uint64_t pos = obase + q0 + e;
+          if (pos == 0) out_fence[nb + 2] = bin;
+          else if (bin > pb) fence_write_gap(out_fence, pb, bin, uint32_t(pos), sh.gaps, &sh.ngap);
+          pb = bin;
         }
       }
+      if (cnt && obase + q0 + cnt == total) out_fence[nb + 3] = pb;
+      __syncthreads();
+      fence_fill_gaps(out_fence, sh.gaps, sh.ngap);
     }
-    return;
+    return true;
   }
 
   // Cleanup: keep the first element of each key (the newest one, §IV-E) when
   // it is regular; compact across tiles.
-  constexpr int kE = kFoldTile / kThreads;
-  const uint32_t q0 = tid * kE;
   uint32_t keep = 0, nkeep = 0;
+  uint32_t pk = has_prev ? key_of(prev_kv) : 0xFFFFFFFFu;
 #pragma unroll
-  for (int e = 0; e < kE; ++e) {
-    const uint32_t q = q0 + e;
-    if (q < tile_n) {
-      const uint32_t kv = xk[2 * psw(q)];
-      const uint32_t prev = q ? key_of(xk[2 * psw(q - 1)]) : s_prev_key;
-      if (key_of(kv) != prev && (kv & 1u)) {
+  for (int e = 0; e < E; ++e) {
+    if (uint32_t(e) < cnt) {
+      const uint32_t kv = out[e].x;
+      if (key_of(kv) != pk && (kv & 1u)) {
         keep |= 1u << e;
         ++nkeep;
       }
+      pk = key_of(kv);
     }
   }
   uint32_t tile_keep;
-  const uint32_t before = block_excl_scan<kThreads>(nkeep, s_scan, tile_keep);
+  const uint32_t before = block_excl_scan<kThreads>(nkeep, sh.scan, tile_keep);
   if (tid == 0) {
     uint64_t prefix = 0;
     if (tile == 0) {
@@ -373,19 +501,94 @@ __global__ void __launch_bounds__(kThreads) fold_merge(FoldSources src, uint64_t
       }
       st_relaxed_u64(lookback + tile, kLbIncl | (prefix + tile_keep));
     }
-    s_prefix = prefix;
+    sh.prefix = prefix;
     if (tile == ntiles - 1) *out_count = prefix + tile_keep;
   }
   __syncthreads();
-  uint64_t dst = s_prefix + before;
+  uint64_t dst = sh.prefix + before;
 #pragma unroll
-  for (int e = 0; e < kE; ++e) {
+  for (int e = 0; e < E; ++e) {
     if (keep & (1u << e)) {
-      const uint2 p = X[psw(q0 + e)];
-      out_k[dst] = p.x;
-      out_v[dst] = p.y;
+      out_k[dst] = out[e].x;
+      out_v[dst] = out[e].y;
       ++dst;
     }
+  }
+  return true;
+}
+
+template <bool kCleanup>
+__global__ void __launch_bounds__(kThreads) fold_merge(FoldSources src, uint64_t total,
+                                                       const uint32_t* __restrict__ part,
+                                                       uint32_t* __restrict__ out_k,
+                                                       uint32_t* __restrict__ out_v,
+                                                       uint32_t* __restrict__ out_fence, int fshift, uint32_t* status,
+                                                       uint64_t* lookback, uint32_t* tile_ctr,
+                                                       uint64_t* out_count, uint32_t ntiles) {
+  extern __shared__ __align__(128) uint32_t sm[];
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ MergeShared sh;
+  __shared__ uint32_t s_tile;
+  if (threadIdx.x == 0) {
+    s_tile = kCleanup ? atomicAdd(tile_ctr, 1u) : blockIdx.x;
+    mbar_init(&s_bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  merge_tile<8, kCleanup>(src, total, part, s_tile, ntiles, out_k, out_v, out_fence, fshift, status, lookback,
+                          out_count, sm, sh, &s_bar, 0);
+}
+
+// Persistent merge for every (instance, tile) of a round: each CTA takes
+// work items from an atomic counter until none is left.
+template <int E>
+__global__ void __launch_bounds__(kThreads) multi_merge(MultiFoldArgs a) {
+  extern __shared__ __align__(128) uint32_t sm[];
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ MergeShared sh;
+  __shared__ FoldSources s_src;
+  __shared__ uint64_t s_item;
+  __shared__ uint32_t s_inst;
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar, 1);
+    fence_mbar_init();
+  }
+  const int S = a.k + 1;
+  for (uint32_t iter = 0;; ++iter) {
+    __syncthreads();  // the previous item is finished with the shared state
+    if (threadIdx.x == 0) {
+      const uint64_t w = atomicAdd(a.work_ctr, 1u);
+      s_item = w;
+      if (w < a.total_tiles) s_inst = find_instance(a.tile_prefix, a.ar.n, w, 0);
+    }
+    __syncthreads();
+    const uint64_t w = s_item;
+    if (w >= a.total_tiles) break;
+    const uint32_t i = s_inst;
+    const MultiInst& in = a.ar.inst[i];
+    if (threadIdx.x < uint32_t(S)) {
+      const uint32_t *k = nullptr, *v = nullptr, *f = nullptr;
+      uint32_t n = 0;
+      int fs = 16;
+      multi_source(a.ar, in, int(threadIdx.x), k, v, f, n, fs);
+      s_src.keys[threadIdx.x] = k;
+      s_src.vals[threadIdx.x] = v;
+      s_src.fence[threadIdx.x] = f;
+      s_src.n[threadIdx.x] = n;
+      s_src.fshift[threadIdx.x] = fs;
+    }
+    if (threadIdx.x == 0) s_src.count = S;
+    __syncthreads();
+    const uint64_t total = uint64_t(in.b) << a.k;
+    const uint32_t t = uint32_t(w - a.tile_prefix[i]);
+    const uint32_t ntiles = uint32_t(a.tile_prefix[i + 1] - a.tile_prefix[i]);
+    const uint32_t* part = a.part + (a.tile_prefix[i] + i) * S;
+    uint32_t* ok = a.ar.keys + in.lvl_off[a.k];
+    uint32_t* ov = a.ar.vals + in.lvl_off[a.k];
+    uint32_t* of = a.ar.fence + in.lvl_fence[a.k];
+    if (!merge_tile<E, false>(s_src, total, part, t, ntiles, ok, ov, of, in.lvl_fshift[a.k], a.status, nullptr,
+                              nullptr, sm, sh, &s_bar, iter & 1u))
+      break;
   }
 }
 
@@ -404,15 +607,33 @@ __global__ void __launch_bounds__(256) distribute(DistributeArgs a) {
   }
 }
 
-// Prefix index of a sorted run: position i opens every bin after the bin of
-// element i - 1 up to its own; position n closes the table.
+// Prefix index of a sorted run: the element at position i owns the entries
+// between the bin of element i - 1 and its own; the first and last elements
+// record the populated bin range.
 __global__ void __launch_bounds__(256) build_fence(const uint32_t* __restrict__ keys, uint32_t n,
-                                                   uint32_t* __restrict__ fence) {
-  for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i <= n; i += uint64_t(gridDim.x) * 256ull) {
-    const uint32_t bin = i < n ? fence_bin(__ldg(keys + i)) : kFenceBins;
-    const int pb = i ? int(fence_bin(__ldg(keys + i - 1))) : -1;
-    for (int P = pb + 1; P <= int(bin); ++P) fence[P] = uint32_t(i);
+                                                   uint32_t* __restrict__ fence, int fshift) {
+  __shared__ uint32_t s_ngap;
+  __shared__ FenceGap s_gaps[kFenceGapSlots];
+  if (threadIdx.x == 0) s_ngap = 0;
+  __syncthreads();
+  const uint32_t nb = fence_bins(fshift);
+  for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < n; i += uint64_t(gridDim.x) * 256ull) {
+    const uint32_t bin = fence_bin(__ldg(keys + i), fshift);
+    if (i == 0) {
+      fence[nb + 2] = bin;
+    } else {
+      const uint32_t pb = fence_bin(__ldg(keys + i - 1), fshift);
+      if (bin > pb) fence_write_gap(fence, pb, bin, uint32_t(i), s_gaps, &s_ngap);
+    }
+    if (i + 1 == n) fence[nb + 3] = bin;
   }
+  __syncthreads();
+  fence_fill_gaps(fence, s_gaps, s_ngap);
+}
+
+template <typename K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
 }
 
 }  // namespace
@@ -422,20 +643,17 @@ cudaError_t fold_partition_launch(const FoldArgs& a, cudaStream_t st) {
   if (ntiles == 0) return cudaSuccess;
   const uint64_t pblocks = ((ntiles + 1) * 32 + 255) / 256;
   count_launches(1);
-  fold_partition<<<unsigned(pblocks), 256, 0, st>>>(a.src, a.total, uint32_t(ntiles), a.part);
+  fold_partition<<<unsigned(pblocks), 256, 0, st>>>(a.src, a.total, uint32_t(ntiles), kFoldTile, a.part);
   return cudaGetLastError();
 }
 
 cudaError_t fold_merge_launch(const FoldArgs& a, cudaStream_t st) {
   static bool attr_set = false;
   cudaError_t e;
+  constexpr size_t smem = TileGeom<8>::kSmem;
   if (!attr_set) {
-    if ((e = cudaFuncSetAttribute(fold_merge<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  int(kMergeSmem))) != cudaSuccess)
-      return e;
-    if ((e = cudaFuncSetAttribute(fold_merge<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  int(kMergeSmem))) != cudaSuccess)
-      return e;
+    if ((e = set_smem(fold_merge<false>, smem)) != cudaSuccess) return e;
+    if ((e = set_smem(fold_merge<true>, smem)) != cudaSuccess) return e;
     attr_set = true;
   }
   const uint64_t ntiles = fold_tiles(a.total);
@@ -447,14 +665,14 @@ cudaError_t fold_merge_launch(const FoldArgs& a, cudaStream_t st) {
     if ((e = cudaMemsetAsync(a.lookback, 0, sizeof(uint64_t) * ntiles, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(a.tile_ctr, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
     count_launches(1);
-    fold_merge<true><<<unsigned(ntiles), kThreads, kMergeSmem, st>>>(
-        a.src, a.total, a.part, a.out_keys, a.out_vals, nullptr, a.status, a.lookback, a.tile_ctr,
-        a.out_count, uint32_t(ntiles));
+    fold_merge<true><<<unsigned(ntiles), kThreads, smem, st>>>(a.src, a.total, a.part, a.out_keys, a.out_vals,
+                                                              nullptr, 16, a.status, a.lookback, a.tile_ctr,
+                                                              a.out_count, uint32_t(ntiles));
   } else {
     count_launches(1);
-    fold_merge<false><<<unsigned(ntiles), kThreads, kMergeSmem, st>>>(
-        a.src, a.total, a.part, a.out_keys, a.out_vals, a.out_fence, a.status, nullptr, nullptr, nullptr,
-        uint32_t(ntiles));
+    fold_merge<false><<<unsigned(ntiles), kThreads, smem, st>>>(a.src, a.total, a.part, a.out_keys, a.out_vals,
+                                                               a.out_fence, a.out_fshift, a.status, nullptr,
+                                                               nullptr, nullptr, uint32_t(ntiles));
   }
   return cudaGetLastError();
 }
@@ -463,6 +681,34 @@ cudaError_t fold_launch(const FoldArgs& a, cudaStream_t st) {
   cudaError_t e = fold_partition_launch(a, st);
   if (e != cudaSuccess) return e;
   return fold_merge_launch(a, st);
+}
+
+cudaError_t multi_fold_launch(const MultiFoldArgs& a, cudaStream_t st) {
+  static bool attr_set = false;
+  cudaError_t e;
+  if (!attr_set) {
+    if ((e = set_smem(multi_merge<8>, TileGeom<8>::kSmem)) != cudaSuccess) return e;
+    if ((e = set_smem(multi_merge<4>, TileGeom<4>::kSmem)) != cudaSuccess) return e;
+    attr_set = true;
+  }
+  if (a.total_tiles == 0) return cudaSuccess;
+  const uint64_t warps = a.total_tiles + a.ar.n;
+  count_launches(1);
+  multi_partition<<<unsigned((warps * 32 + 255) / 256), 256, 0, st>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.work_ctr, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  count_launches(1);
+  if (a.tile == int(TileGeom<4>::kTile)) {
+    const unsigned grid = unsigned(sms) * 6u;
+    multi_merge<4><<<grid, kThreads, TileGeom<4>::kSmem, st>>>(a);
+  } else {
+    const unsigned grid = unsigned(sms) * 4u;
+    multi_merge<8><<<grid, kThreads, TileGeom<8>::kSmem, st>>>(a);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t distribute_launch(const DistributeArgs& a, cudaStream_t st) {
@@ -474,11 +720,11 @@ cudaError_t distribute_launch(const DistributeArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t build_fence_launch(const uint32_t* keys, uint32_t n, uint32_t* fence, cudaStream_t st) {
+cudaError_t build_fence_launch(const uint32_t* keys, uint32_t n, uint32_t* fence, int fshift, cudaStream_t st) {
   uint64_t blocks = (uint64_t(n) + 1 + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
   count_launches(1);
-  build_fence<<<unsigned(blocks), 256, 0, st>>>(keys, n, fence);
+  build_fence<<<unsigned(blocks), 256, 0, st>>>(keys, n, fence, fshift);
   return cudaGetLastError();
 }
 

@@ -38,6 +38,8 @@ struct lsm_t {
   uint32_t* d_part = nullptr;
   uint64_t part_words = 0;
   uint32_t* d_fence = nullptr;  // prefix index per level (L tables) + the sorted batch's
+  uint64_t fence_off[kMaxLevels + 2] = {};
+  int fshift[kMaxLevels + 1] = {};  // per level; [L] = the batch
   uint32_t* d_misc = nullptr;  // [0] sticky errors [1] key check [2] tile ctr [3] tile ctr
   uint64_t* d_u64 = nullptr;   // [0] cleanup count
   uint32_t* h_status = nullptr;  // mapped pinned word: key check of the current batch
@@ -156,8 +158,8 @@ struct ProfScope {
 
 uint32_t* level_keys(lsm_t* h, int i) { return h->d_keys + h->level_off[i]; }
 uint32_t* level_vals(lsm_t* h, int i) { return h->d_vals + h->level_off[i]; }
-uint32_t* level_fence(lsm_t* h, int i) { return h->d_fence + uint64_t(i) * kFenceWords; }
-uint32_t* batch_fence(lsm_t* h) { return h->d_fence + uint64_t(h->L) * kFenceWords; }
+uint32_t* level_fence(lsm_t* h, int i) { return h->d_fence + h->fence_off[i]; }
+uint32_t* batch_fence(lsm_t* h) { return h->d_fence + h->fence_off[h->L]; }
 
 LevelSet full_levels(lsm_t* h) {
   LevelSet ls{};
@@ -166,6 +168,7 @@ LevelSet full_levels(lsm_t* h) {
     ls.keys[ls.count] = level_keys(h, i);
     ls.vals[ls.count] = level_vals(h, i);
     ls.fence[ls.count] = level_fence(h, i);
+    ls.fshift[ls.count] = h->fshift[i];
     ls.n[ls.count] = uint32_t(uint64_t(h->b) << i);
     ++ls.count;
   }
@@ -205,6 +208,7 @@ lsm_status apply_batch(lsm_t* h, int mode, const uint32_t* keys, const uint32_t*
   a.tmp_keys = h->d_tk;
   a.tmp_vals = h->d_tv;
   a.fence = k == 0 ? level_fence(h, 0) : batch_fence(h);
+  a.fshift = k == 0 ? h->fshift[0] : h->fshift[h->L];
   {
     ProfScope ps(h, LSM_PROF_SORT, 16.0 * h->b, st);
     if (checked) *reinterpret_cast<volatile uint32_t*>(h->h_status) = 0u;
@@ -216,17 +220,20 @@ lsm_status apply_batch(lsm_t* h, int mode, const uint32_t* keys, const uint32_t*
     f.src.keys[0] = h->d_bk;
     f.src.vals[0] = h->d_bv;
     f.src.fence[0] = batch_fence(h);
+    f.src.fshift[0] = h->fshift[h->L];
     f.src.n[0] = h->b;
     for (int i = 0; i < k; ++i) {
       f.src.keys[i + 1] = level_keys(h, i);
       f.src.vals[i + 1] = level_vals(h, i);
       f.src.fence[i + 1] = level_fence(h, i);
+      f.src.fshift[i + 1] = h->fshift[i];
       f.src.n[i + 1] = uint32_t(uint64_t(h->b) << i);
     }
     f.total = uint64_t(h->b) << k;
     f.out_keys = level_keys(h, k);
     f.out_vals = level_vals(h, k);
     f.out_fence = level_fence(h, k);
+    f.out_fshift = h->fshift[k];
     f.part = h->d_part;
     f.status = h->d_misc + kMiscSticky;
     f.cleanup = false;
@@ -323,7 +330,11 @@ lsm_status lsm_create(lsm_t** out, uint32_t b, uint64_t max_elements, int device
   if (e == cudaSuccess) e = dalloc(&h->sws.lookback, uint64_t(kSortPasses) * sort_tiles * 256);
   if (e == cudaSuccess && b <= kMsdMaxN) e = dalloc(&h->sws.tilecnt, kMsdTileWords);
   if (e == cudaSuccess) e = dalloc(&h->d_part, h->part_words);
-  if (e == cudaSuccess) e = dalloc(&h->d_fence, uint64_t(L + 1) * kFenceWords);
+  for (uint32_t i = 0; i <= L; ++i) {
+    h->fshift[i] = fence_shift_for(i < L ? (uint64_t(b) << i) : uint64_t(b));
+    h->fence_off[i + 1] = h->fence_off[i] + round_up(fence_words(h->fshift[i]), 64);
+  }
+  if (e == cudaSuccess) e = dalloc(&h->d_fence, h->fence_off[L + 1]);
   if (e == cudaSuccess) e = dalloc(&h->d_misc, kMiscWords);
   if (e == cudaSuccess) e = dalloc(&h->d_u64, 8);
   if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&h->h_status), 64, cudaHostAllocMapped);
@@ -497,6 +508,7 @@ lsm_status lsm_cleanup(lsm_t* h, void* stream) {
     f.src.keys[i] = ls.keys[i];
     f.src.vals[i] = ls.vals[i];
     f.src.fence[i] = ls.fence[i];
+    f.src.fshift[i] = ls.fshift[i];
     f.src.n[i] = ls.n[i];
   }
   f.total = total;
@@ -535,7 +547,8 @@ lsm_status lsm_cleanup(lsm_t* h, void* stream) {
     ProfScope ps(h, LSM_PROF_CLEANUP, 8.0 * double(d.total), st);
     LSM_TRY(distribute_launch(d, st));
     for (uint32_t i = 0; i < h->L; ++i)
-      if ((r2 >> i) & 1u) LSM_TRY(build_fence_launch(level_keys(h, i), h->b << i, level_fence(h, i), st));
+      if ((r2 >> i) & 1u)
+        LSM_TRY(build_fence_launch(level_keys(h, i), h->b << i, level_fence(h, i), h->fshift[i], st));
   }
   h->r = r2;
   return LSM_OK;

@@ -58,6 +58,51 @@ __device__ __forceinline__ uint32_t upper_bound_key(const uint32_t* __restrict__
   return lo;
 }
 
+// Entry P (0 .. 2^(32 - fshift)) of the prefix index of a sorted run of n
+// elements: the number of elements whose bin is < P.  A table is written
+// only inside its populated bin range: the two words after entry nbins hold
+// bmin and bmax, the bins of the first and last element; below (and at)
+// bmin the answer is 0, above bmax it is n.
+__device__ __forceinline__ uint32_t fence_at(const uint32_t* f, int fshift, uint32_t n, uint32_t P) {
+  const uint32_t nb = fence_bins(fshift);
+  if (P <= __ldg(f + nb + 2)) return 0u;
+  if (P > __ldg(f + nb + 3)) return n;
+  return __ldg(f + P);
+}
+
+// Writing a prefix index from consecutive elements: the element at position
+// pos with bin `bin` after an element with bin `pb` owns entries (pb, bin].
+// Small gaps are written at once; gaps wider than kFenceDirect bins go to a
+// per-CTA list that the whole CTA fills afterwards (fence_fill_gaps).
+constexpr uint32_t kFenceDirect = 256;
+constexpr int kFenceGapSlots = 64;
+struct FenceGap {
+  uint32_t lo, hi, val;
+};
+
+__device__ __forceinline__ void fence_write_gap(uint32_t* f, uint32_t pb, uint32_t bin, uint32_t pos,
+                                                FenceGap* s_gaps, uint32_t* s_ngap) {
+  if (bin - pb <= kFenceDirect) {
+    for (uint32_t P = pb + 1; P <= bin; ++P) f[P] = pos;
+    return;
+  }
+  const uint32_t slot = atomicAdd(s_ngap, 1u);
+  if (slot < uint32_t(kFenceGapSlots)) {
+    s_gaps[slot] = FenceGap{pb + 1, bin, pos};
+  } else {
+    for (uint32_t P = pb + 1; P <= bin; ++P) f[P] = pos;
+  }
+}
+
+// Called by every thread of the CTA after a __syncthreads.
+__device__ __forceinline__ void fence_fill_gaps(uint32_t* f, const FenceGap* s_gaps, uint32_t ngap) {
+  if (ngap > uint32_t(kFenceGapSlots)) ngap = kFenceGapSlots;
+  for (uint32_t g = 0; g < ngap; ++g) {
+    const FenceGap gp = s_gaps[g];
+    for (uint32_t P = gp.lo + threadIdx.x; P <= gp.hi; P += blockDim.x) f[P] = gp.val;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T x) {
 #pragma unroll

@@ -65,6 +65,7 @@ struct SortArgs {
   uint32_t* tmp_keys;   // n elements of scratch
   uint32_t* tmp_vals;
   uint32_t* fence;      // prefix index of the sorted output to write, or null
+  int fshift;
 };
 
 struct SortWorkspace {
@@ -97,19 +98,33 @@ cudaError_t check_keys_launch(const uint32_t* keys, uint64_t n, uint32_t* status
 // ------------------------------------------------------------------ fold ---
 constexpr int kFoldTile = 2048;  // output elements per merge CTA
 
-// Prefix index ("fence") of a sorted run: fence[P] = number of elements whose
-// key variable has top 16 bits < P (P = 0 .. 65536), i.e. the start of the
-// run of keys in [P * 2^15, (P + 1) * 2^15).  One table per level and one for
-// the sorted batch; written whenever the run is written.
-constexpr uint32_t kFenceBins = 65536;
-constexpr uint32_t kFenceWords = kFenceBins + 4;  // 65537 used, padded
-__host__ __device__ inline uint32_t fence_bin(uint32_t kv) { return kv >> 16; }
+// Prefix index ("fence") of a sorted run: with bin(kv) = kv >> fshift,
+// fence[P] = number of elements whose bin is < P, for P = 0 .. 2^(32-fshift):
+// the start of the run of key variables in [P << fshift, (P + 1) << fshift).
+// One table per level and one for the sorted batch, written whenever the run
+// is written.  fshift is chosen per run so that a bin holds about 8 elements
+// (a 32-byte sector of keys), between 8 and 16 (2^24 .. 2^16 bins).  Every
+// table also answers at the common 16-bit resolution: entry P16 << (16 -
+// fshift).
+constexpr uint32_t kFenceBins16 = 65536;
+constexpr int kFenceMinShift = 8, kFenceMaxShift = 16;
+__host__ __device__ inline uint32_t fence_bin(uint32_t kv, int fshift) { return kv >> fshift; }
+__host__ __device__ inline uint32_t fence_bins(int fshift) { return 1u << (32 - fshift); }
+inline int fence_shift_for(uint64_t n) {
+  int lg = 0;
+  while ((2ull << lg) <= n) ++lg;      // floor(log2 n)
+  int fb = lg - 3;                     // about 8 elements per bin
+  fb = fb < 16 ? 16 : (fb > 24 ? 24 : fb);
+  return 32 - fb;
+}
+inline uint64_t fence_words(int fshift) { return uint64_t(fence_bins(fshift)) + 4; }
 
 struct FoldSources {
   const uint32_t* keys[kMaxSources];
   const uint32_t* vals[kMaxSources];
   const uint32_t* fence[kMaxSources];
   uint32_t n[kMaxSources];
+  int fshift[kMaxSources];
   int count;  // rank order: newest first
 };
 
@@ -120,6 +135,7 @@ struct FoldArgs {
   uint32_t* out_vals;
   uint32_t* part;        // (ntiles + 1) * count co-ranks
   uint32_t* out_fence;   // prefix index of the output (plain fold), or null
+  int out_fshift;
   uint32_t* status;
   // cleanup only: keep the first element of every key if regular, compacted
   bool cleanup;
@@ -149,17 +165,59 @@ struct DistributeArgs {
 };
 cudaError_t distribute_launch(const DistributeArgs& a, cudaStream_t st);
 
+// ------------------------------------------------------ many dictionaries ---
+// The batched form: n independent dictionaries with their own batch sizes,
+// all advanced by one batch per round (so all share r and k = ffz(r)).
+constexpr int kMultiMaxLevels = 16;
+
+struct MultiInst {
+  uint64_t boff;        // start of the instance's batch in the input and sorted-batch buffers
+  uint32_t b;           // its batch size
+  uint32_t sort_tile0;  // its first sort tile
+  uint32_t sort_tiles;  // number of its sort tiles (kMsdTile elements each)
+  int32_t fshift_batch;
+  uint64_t batch_fence;                   // prefix index of the sorted batch (fence arena offset)
+  uint64_t lvl_off[kMultiMaxLevels];      // element offset of level l in the level arena
+  uint64_t lvl_fence[kMultiMaxLevels];    // fence arena offset of level l's prefix index
+  int32_t lvl_fshift[kMultiMaxLevels];
+};
+
+struct MultiArena {
+  uint32_t* keys;    // level arena
+  uint32_t* vals;
+  uint32_t* bkeys;   // sorted batches, instance i at boff_i
+  uint32_t* bvals;
+  uint32_t* fence;   // fence arena
+  const MultiInst* inst;
+  uint32_t n;
+};
+
+// One round's fold for every instance: batch + levels 0..k-1 -> level k.
+// tile_prefix[i] = merge tiles of the instances before i (n + 1 entries).
+struct MultiFoldArgs {
+  MultiArena ar;
+  int k;
+  int tile;                     // output elements per merge tile
+  const uint64_t* tile_prefix;  // device, n + 1
+  uint64_t total_tiles;
+  uint32_t* part;               // (total_tiles + n) * (k + 1) co-ranks
+  uint32_t* work_ctr;           // zeroed by the launcher
+  uint32_t* status;
+};
+cudaError_t multi_fold_launch(const MultiFoldArgs& a, cudaStream_t st);
+
 // ----------------------------------------------------------------- query ---
 struct LevelSet {
   const uint32_t* keys[kMaxLevels];
   const uint32_t* vals[kMaxLevels];
   const uint32_t* fence[kMaxLevels];
   uint32_t n[kMaxLevels];
+  int fshift[kMaxLevels];
   int count;  // full levels, newest (smallest) first
 };
 
-// Prefix index of a sorted run of n key variables (kFenceWords words).
-cudaError_t build_fence_launch(const uint32_t* keys, uint32_t n, uint32_t* fence, cudaStream_t st);
+// Prefix index of a sorted run of n key variables (fence_words(fshift) words).
+cudaError_t build_fence_launch(const uint32_t* keys, uint32_t n, uint32_t* fence, int fshift, cudaStream_t st);
 
 cudaError_t lookup_launch(const LevelSet& ls, const uint32_t* q, uint64_t nq,
                           uint32_t* val, uint8_t* found, cudaStream_t st);

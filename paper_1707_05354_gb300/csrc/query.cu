@@ -5,9 +5,10 @@
 //         for the first element whose key is >= q; if that element has key q
 //         it decides: regular -> found with its value, tombstone -> absent
 //         (and the search stops).  The top of each level's search tree is the
-//         level's prefix index, a 65536-ary splitter table (one entry per
-//         2^15 keys, 256 KB, resident in L2): two adjacent loads narrow a
-//         search to one bin, and a binary search finishes inside it.
+//         level's prefix index, a splitter table of 2^16 .. 2^24 entries
+//         (about one per 8 elements): two adjacent loads narrow a search to
+//         one bin of about one 32-byte sector, and a short binary search
+//         finishes inside it.
 //         lookup_direct takes the queries in input order (one thread each);
 //         lookup_sorted takes queries sorted by key: the first and last lane
 //         of a warp bound the warp's window in each level and every lane then
@@ -31,12 +32,13 @@ namespace {
 constexpr int kThreads = 256;
 
 // lower_bound of key variable `target` in level l: the level's prefix index
-// (a 65536-ary splitter table, one entry per 2^15 keys) gives the run of the
-// target's bin in two adjacent loads; a binary search finishes inside it.
+// (a splitter table with about one entry per 8 elements) gives the run of the
+// target's bin in two adjacent loads; a short binary search finishes inside.
 __device__ __forceinline__ uint32_t level_lower_bound(const LevelSet& ls, int l, uint32_t target) {
   const uint32_t* f = ls.fence[l];
-  const uint32_t bin = fence_bin(target);
-  return lower_bound_kv(ls.keys[l], __ldg(f + bin), __ldg(f + bin + 1), target);
+  const int fs = ls.fshift[l];
+  const uint32_t bin = fence_bin(target, fs), n = ls.n[l];
+  return lower_bound_kv(ls.keys[l], fence_at(f, fs, n, bin), fence_at(f, fs, n, bin + 1), target);
 }
 
 // Lookup of one key over the levels (newest first).

@@ -415,14 +415,25 @@ __global__ void __launch_bounds__(kThreads) msd_scatter(Loader ld, const uint32_
   }
 }
 
-// First position i in [0, m) with (a[i] >> 16) >= bin, a sorted.
-__device__ __forceinline__ uint32_t lower_bound_bin(const uint32_t* a, uint32_t m, uint32_t bin) {
+// First position i in [0, m) with (a[i] >> fshift) >= bin, a sorted.
+__device__ __forceinline__ uint32_t lower_bound_bin(const uint32_t* a, uint32_t m, uint32_t bin, int fshift) {
   uint32_t lo = 0, hi = m;
   while (lo < hi) {
     const uint32_t mid = (lo + hi) >> 1;
-    if ((a[mid] >> 16) < bin) lo = mid + 1; else hi = mid;
+    if ((a[mid] >> fshift) < bin) lo = mid + 1; else hi = mid;
   }
   return lo;
+}
+
+// Prefix-index entries of bucket d (the bins whose top byte is d) from the
+// sorted bucket a[0, m) starting at position start.
+__device__ __forceinline__ void bucket_fence(const uint32_t* a, uint32_t m, uint32_t start, uint32_t d,
+                                             uint32_t* fence, int fshift) {
+  const uint32_t per = 1u << (24 - fshift);  // bins per bucket
+  for (uint32_t i = threadIdx.x; i < per; i += blockDim.x) {
+    const uint32_t bin = d * per + i;
+    fence[bin] = start + lower_bound_bin(a, m, bin, fshift);
+  }
 }
 
 __global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort(uint32_t* __restrict__ tmp_k,
@@ -430,7 +441,7 @@ __global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort(uint32_t* __res
                                                               uint32_t* __restrict__ out_k,
                                                               uint32_t* __restrict__ out_v,
                                                               const uint32_t* __restrict__ ctl, uint32_t n,
-                                                              uint32_t* __restrict__ fence,
+                                                              uint32_t* __restrict__ fence, int fshift,
                                                               uint32_t* __restrict__ next_ctl) {
   extern __shared__ __align__(16) uint32_t bsm[];
   __shared__ uint32_t s_whist[kBucketWarps][kRadix];
@@ -483,7 +494,7 @@ __global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort(uint32_t* __res
       out_k[start + i] = sk[i];
       out_v[start + i] = sv[i];
     }
-    if (fence && tid < kRadix) fence[d * kRadix + tid] = start + lower_bound_bin(sk, m, d * kRadix + tid);
+    if (fence) bucket_fence(sk, m, start, d, fence, fshift);
   } else {
     // Chunked: three stable passes over [start, start + m) through global
     // memory, tmp -> out -> tmp -> out, kBucketCap elements at a time in order.
@@ -529,9 +540,14 @@ __global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort(uint32_t* __res
       t = srcv; srcv = dstv; dstv = t;
     }
     // after three passes the data sits in out (tmp -> out -> tmp -> out)
-    if (fence && tid < kRadix) fence[d * kRadix + tid] = start + lower_bound_bin(out_k + start, m, d * kRadix + tid);
+    if (fence) bucket_fence(out_k + start, m, start, d, fence, fshift);
   }
-  if (fence && d == kRadix - 1 && tid == 0) fence[kFenceBins] = n;
+  // the bucket sort writes every entry: the populated range is all bins
+  if (fence && d == kRadix - 1 && tid == 0) {
+    fence[fence_bins(fshift)] = n;
+    fence[fence_bins(fshift) + 2] = 0u;
+    fence[fence_bins(fshift) + 3] = fence_bins(fshift) - 1;
+  }
 }
 
 __global__ void __launch_bounds__(256) check_keys(const uint32_t* __restrict__ keys, uint64_t n,
@@ -573,7 +589,7 @@ cudaError_t bucket_sort_launch(const SortArgs& a, SortWorkspace& ws, cudaStream_
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   count_launches(1);
   bucket_sort<<<kRadix, kBucketThreads, kBucketSmem, st>>>(a.tmp_keys, a.tmp_vals, a.out_keys, a.out_vals,
-                                                          ctl, a.n, a.fence, next);
+                                                          ctl, a.n, a.fence, a.fshift, next);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   ws.flip ^= 1;
   return cudaSuccess;
@@ -620,7 +636,7 @@ cudaError_t sort_launch(const SortArgs& a, SortWorkspace& ws, cudaStream_t st, u
   ws.flip ^= 1;
   e = cudaMemsetAsync(ws.ctl + ws.flip * kSortCtlWords, 0, sizeof(uint32_t) * kSortCtlWords, st);
   if (e != cudaSuccess) return e;
-  if (a.fence) return build_fence_launch(a.out_keys, a.n, a.fence, st);
+  if (a.fence) return build_fence_launch(a.out_keys, a.n, a.fence, a.fshift, st);
   return cudaSuccess;
 }
 
