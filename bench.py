@@ -50,6 +50,12 @@ def parse_args():
     p.add_argument("--lookup-mode", type=int, default=0, help="0 auto, 1 direct, 2 sorted")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default="paper", choices=["paper", "batched"],
+                   help="paper: b=2^20 plain dictionary (default); batched: 256 dictionaries per round")
+    p.add_argument("--instances", type=int, default=256)
+    p.add_argument("--rounds", type=int, default=32)
+    p.add_argument("--no-plain", action="store_true", help="batched: skip the per-instance plain-call arm")
+    p.add_argument("--no-tune", action="store_true", help="batched: default shapes instead of the tuner's")
     return p.parse_args()
 
 
@@ -456,10 +462,225 @@ def run_e2e(args, G, h, torch, dev, keys, vals, q, c1, c2, r1, r2, world):
                     "second stream, double-buffered"}
 
 
+# ----------------------------------------------------------- batched form --
+BATCHED_METRIC = "M updates/s of the batched form (256 dictionaries, b log-uniform in [2^10, 2^18])"
+
+
+def batched_rounds(args):
+    from paper_1707_05354_gb300 import workload
+    wl = workload.BatchedWorkload(n_inst=args.instances, rounds=args.rounds)
+    return wl, [wl.round(t) for t in range(wl.rounds)]
+
+
+def batched_bytes(sizes, rounds):
+    """Algorithmic bytes of one pass over all rounds: per instance and round
+    16 * 2^k * b for the update (k = ffz(r)) and, for its b lookups, 9 B per
+    query plus 32 B per full level probed (upper bound: every full level)."""
+    tot = 0.0
+    for r in range(rounds):
+        k = (~r & (r + 1)).bit_length() - 1
+        levels = bin(r + 1).count("1")
+        for b in sizes:
+            tot += 16.0 * (1 << k) * b + b * (9.0 + 32.0 * levels)
+    return tot
+
+
+def run_batched(args):
+    import torch
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_1707_05354_gb300 import autotune
+    from paper_1707_05354_gb300 import gpulsm as G
+
+    wl, rounds = batched_rounds(args)
+    sizes = [int(x) for x in wl.sizes]
+    tot, R = wl.total, wl.rounds
+    st = torch.cuda.current_stream(dev)
+    sp = st.cuda_stream
+
+    def dev_u32(a):
+        return torch.from_numpy(a.view(np.int32)).to(dev)
+
+    dk = [dev_u32(r[0]) for r in rounds]
+    dv = [dev_u32(r[1]) for r in rounds]
+    dd = [torch.from_numpy(r[2]).to(dev) for r in rounds]
+    dq = [dev_u32(r[3]) for r in rounds]
+    off = torch.as_tensor(wl.off, dtype=torch.int64).to(dev)
+    o_val = torch.empty(tot, dtype=torch.int32, device=dev)
+    o_fnd = torch.empty(tot, dtype=torch.uint8, device=dev)
+
+    table = {} if args.no_tune else autotune.load_or_tune(local)
+    tuning = autotune.tuning_for(sizes, table)
+    m = G.MultiLSM(sizes, max_batches=R, tuning=tuning, device=local)
+
+    def step_multi():
+        m.reset()
+        for t in range(R):
+            G.lsm_multi_round(m.h, dk[t].data_ptr(), dv[t].data_ptr(), dd[t].data_ptr(), None, dq[t].data_ptr(),
+                              off.data_ptr(), tot, o_val.data_ptr(), o_fnd.data_ptr(), sp)
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize(dev)
+        evs = []
+        for _ in range(steps):
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            fn()
+            z.record(st)
+            evs.append((a, z))
+        torch.cuda.synchronize(dev)
+        return [a.elapsed_time(z) / 1000.0 for a, z in evs]
+
+    for _ in range(args.warmup):
+        step_multi()
+    status, flags = m.sync()
+    assert status == G.LSM_OK and not any(flags), "batched round error %s" % status
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.5)
+    l0 = G.kernel_launches()
+    secs = timed(step_multi, args.steps, 0)
+    launches = G.kernel_launches() - l0
+    clocks = sampler.stop()
+    status, _ = m.sync()
+    assert status == G.LSM_OK
+    per_round_kernels = G.lsm_multi_get_option(m.h, G.LSM_MULTI_OPT_GRAPH_KERNELS)
+    mult_s = statistics.median(secs)
+
+    # the same rounds as separate per-instance plain calls (one handle each)
+    plain = None
+    if not args.no_plain:
+        hs = [G.lsm_create(b, b * R, local) for b in sizes]
+        vo = [int(x) for x in wl.off]
+
+        def step_plain():
+            for h in hs:
+                G.lsm_reset(h)
+            for t in range(R):
+                kp, vp, dp, qp = dk[t].data_ptr(), dv[t].data_ptr(), dd[t].data_ptr(), dq[t].data_ptr()
+                for i, h in enumerate(hs):
+                    o = vo[i]
+                    G.lsm_update_batch(h, kp + 4 * o, vp + 4 * o, dp + o, sizes[i], sp)
+                    G.lsm_lookup(h, qp + 4 * o, sizes[i], o_val.data_ptr() + 4 * o, o_fnd.data_ptr() + o, sp)
+
+        psecs = timed(step_plain, max(1, min(args.steps, 3)), 1)
+        for h in hs:
+            G.lsm_destroy(h)
+        p_s = statistics.median(psecs)
+        plain = {"value": R * tot / p_s / 1e6, "unit": "M updates/s", "ms_per_step": 1000 * p_s,
+                 "speedup_of_batched": p_s / mult_s,
+                 "what": "one plain handle per dictionary; per round and dictionary lsm_update_batch + "
+                         "lsm_lookup (each update waits for its key check, as the plain API does)"}
+
+    # end to end: each round's inputs copied from pinned host memory into fixed
+    # device buffers (so every round replays the same graph), results read back
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(a).pin_memory()
+        hk = [pin(r[0].view(np.int32)) for r in rounds]
+        hv = [pin(r[1].view(np.int32)) for r in rounds]
+        hd = [pin(r[2]) for r in rounds]
+        hq = [pin(r[3].view(np.int32)) for r in rounds]
+        bk, bv = torch.empty(tot, dtype=torch.int32, device=dev), torch.empty(tot, dtype=torch.int32, device=dev)
+        bd, bq = torch.empty(tot, dtype=torch.uint8, device=dev), torch.empty(tot, dtype=torch.int32, device=dev)
+        hval = torch.empty(tot, dtype=torch.int32).pin_memory()
+        hfnd = torch.empty(tot, dtype=torch.uint8).pin_memory()
+
+        def step_e2e():
+            m.reset()
+            for t in range(R):
+                bk.copy_(hk[t], non_blocking=True)
+                bv.copy_(hv[t], non_blocking=True)
+                bd.copy_(hd[t], non_blocking=True)
+                bq.copy_(hq[t], non_blocking=True)
+                G.lsm_multi_round(m.h, bk.data_ptr(), bv.data_ptr(), bd.data_ptr(), None, bq.data_ptr(),
+                                  off.data_ptr(), tot, o_val.data_ptr(), o_fnd.data_ptr(), sp)
+                hval.copy_(o_val, non_blocking=True)
+                hfnd.copy_(o_fnd, non_blocking=True)
+            torch.cuda.synchronize(dev)
+
+        for _ in range(max(1, args.warmup)):
+            step_e2e()
+        K = max(1, args.steps // 2)
+        t0 = time.perf_counter()
+        for _ in range(K):
+            step_e2e()
+        e_s = (time.perf_counter() - t0) / K
+        e2e = {"value": R * tot / e_s / 1e6, "unit": "M updates/s", "h2d_bytes_per_step": R * tot * 13,
+               "d2h_bytes_per_step": R * tot * 5, "ms_per_step": 1000 * e_s, "steps": K,
+               "note": "wall clock per pass of all rounds; per round the update batch and queries are copied "
+                       "from pinned host memory and the lookup results read back"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        n_done = 0
+        o1s = [oracle.MapOracle(b) for b in sizes]
+        for t in range(min(R, 4)):
+            k, v, d, q = rounds[t]
+            for i, b in enumerate(sizes):
+                s = slice(int(wl.off[i]), int(wl.off[i + 1]))
+                o1s[i].apply_batch(k[s], v[s], d[s])
+                o1s[i].lookup(q[s])
+            n_done += tot
+        c_s = time.perf_counter() - t0
+        cpu = {"value": n_done / c_s / 1e6, "unit": "M updates/s", "cores": 1, "kind": "oracle",
+               "seconds": c_s, "sample": "std::map oracle per dictionary, single thread: the first %d rounds "
+                                         "(update batch + lookups of every dictionary)" % min(R, 4)}
+
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    abytes = batched_bytes(sizes, R)
+    achieved = abytes / mult_s / 1e9
+    m.close()
+    value = world * R * tot / mult_s / 1e6
+    if rank == 0:
+        line = {
+            "metric": BATCHED_METRIC, "value": value, "unit": "M updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * mult_s, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (seeded: b_i = round(2^U[10,18]), uniform 31-bit keys, 20% deletes of earlier "
+                    "keys, half-hit lookups; PCG64)",
+            "config": {"workload": "batched form: %d dictionaries, %d rounds of one update batch (b_i ops) and b_i "
+                                   "lookups each; %d updates per round" % (wl.n, R, tot),
+                       "instances": wl.n, "rounds": R, "updates_per_round": tot,
+                       "b_min": min(sizes), "b_max": max(sizes),
+                       "l2": "inputs larger than L2 (%.0f MB of updates per step), no flush" % (R * tot * 9 / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "lookups": {"value": world * R * tot / mult_s / 1e6, "unit": "M lookups/s",
+                        "note": "lookups run in the same graph replay as the updates; value and lookups share "
+                                "the round time"},
+            "ms_per_round": 1000 * mult_s / R,
+            "plain_calls": plain,
+            "tuning": {"table": {str(k): [v["tile"], v["bin_log2"]] for k, v in table.items()},
+                       "default": list(autotune.DEFAULT)},
+            "roofline": {"bound": "hbm", "kernel": "whole round (one graph replay)", "achieved": achieved,
+                         "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                         "peak_source": peak_kind, "algorithmic_bytes_per_step": abytes},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "graph_kernels_per_round": per_round_kernels, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_gpu(args)
 
 

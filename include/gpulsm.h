@@ -283,6 +283,123 @@ typedef struct {
 lsm_status lsm_profile(lsm_t* h, int enable);
 lsm_status lsm_profile_read(lsm_t* h, lsm_profile_entry* out);
 
+
+/* ========================================================================
+ * Batched form: many independent dictionaries advanced together
+ * ========================================================================
+ * A multi handle holds n independent GPU LSMs.  Instance i has its own batch
+ * size b_i (any integer in [1, 2^20]) and levels of b_i * 2^l elements
+ * (§III-B), its own counter r_i and the same batch semantics as a plain
+ * handle (§III-A).  A "round" gives every instance at most one batch; all
+ * instances are sorted, folded and searched by the same few kernels, and the
+ * round runs as one CUDA graph replay.  The paper treats one dictionary; the
+ * batched form is this library's extension for many small ones.
+ *
+ * Input layout of a round: instance i's ops are at positions
+ * [in_off_i, in_off_i + count_i) of the caller's d_keys / d_vals /
+ * d_is_delete arrays, with in_off_i = b_0 + ... + b_{i-1}
+ * (lsm_multi_layout returns it).  count_i = d_counts[i] (device array of n
+ * u32; 0 = no batch for i this round) or b_i for every instance when d_counts
+ * is NULL.  A short batch is padded like a plain one (copies of its last op).
+ *
+ * Errors inside a round are per instance and asynchronous: an instance whose
+ * batch has a key >= 2^31 - 1, count_i > b_i, or would need a level beyond
+ * the capacity keeps its state unchanged and the others proceed;
+ * lsm_multi_sync reports it (and per-instance error bits).
+ */
+typedef struct lsm_multi_t lsm_multi_t; /* opaque; owned by the library */
+
+/* Per-instance shape choices (see the autotuner in the Python package):
+ * tile      output elements per merge work item: 1024 or 2048;
+ * bin_log2  prefix-index resolution: about 2^bin_log2 elements per bin
+ *           (1 .. 6), the fan-out of the first step of every level search. */
+typedef struct {
+  uint32_t tile;
+  uint32_t bin_log2;
+} lsm_multi_tuning;
+
+/*
+ * lsm_multi_create - n_inst empty instances with batch sizes h_b[0 .. n-1]
+ * (host array), each able to take max_batches batches (levels 0 .. L - 1
+ * with 2^L > max_batches, L <= 16; b_i * 2^(L-1) < 2^31).  h_tuning: n
+ * entries or NULL (tile 2048, bin_log2 3).  Allocates every level, fence and
+ * scratch buffer up front (about 2 * max_batches * b_i * 8 bytes per
+ * instance plus 4 * b_i * 8 bytes of batch scratch).
+ * Errors: LSM_ERR_ARG (bad sizes), LSM_ERR_OOM, LSM_ERR_CUDA.
+ */
+lsm_status lsm_multi_create(lsm_multi_t** out, uint32_t n_inst, const uint32_t* h_b, uint32_t max_batches,
+                            const lsm_multi_tuning* h_tuning, int device);
+void lsm_multi_destroy(lsm_multi_t* h);
+
+/*
+ * lsm_multi_update - one round of update batches (layout above): for every
+ * instance with count_i > 0, encode + pad + stable sort of its batch
+ * (§IV-A) and the cascade fold of the batch and levels 0 .. k_i - 1 into
+ * level k_i = ffz(r_i) (§III-B, §IV-A); r_i += 1.  d_vals may be NULL (all
+ * values 0), d_is_delete NULL (all inserts).  Asynchronous on `stream`; the
+ * first call with a given set of pointers captures the round into a CUDA
+ * graph, later calls with the same pointers replay it.
+ */
+lsm_status lsm_multi_update(lsm_multi_t* h, const uint32_t* d_keys, const uint32_t* d_vals,
+                            const uint8_t* d_is_delete, const uint32_t* d_counts, void* stream);
+
+/*
+ * lsm_multi_lookup - LOOKUP (§III-D) for queries of many instances: query g
+ * (0 <= g < nq) belongs to instance i with d_qoff[i] <= g < d_qoff[i + 1]
+ * (device array of n + 1 u64, d_qoff[n] = nq).  Outputs as lsm_lookup.
+ */
+lsm_status lsm_multi_lookup(lsm_multi_t* h, const uint32_t* d_q, const uint64_t* d_qoff, uint64_t nq,
+                            uint32_t* d_val, uint8_t* d_found, void* stream);
+
+/*
+ * lsm_multi_round - lsm_multi_update followed by lsm_multi_lookup (the
+ * lookups see the round's batches), as ONE graph replay on `stream`.
+ */
+lsm_status lsm_multi_round(lsm_multi_t* h, const uint32_t* d_keys, const uint32_t* d_vals,
+                           const uint8_t* d_is_delete, const uint32_t* d_counts, const uint32_t* d_q,
+                           const uint64_t* d_qoff, uint64_t nq, uint32_t* d_val, uint8_t* d_found,
+                           void* stream);
+
+/*
+ * lsm_multi_sync - synchronises `stream`, returns the first error seen by the
+ * rounds since the last sync (LSM_ERR_TIMEOUT, LSM_ERR_KEY_RANGE,
+ * LSM_ERR_ARG, LSM_ERR_FULL in that priority) and clears it.  h_flags (n u32
+ * or NULL) receives the last round's per-instance bits: 1 bad key,
+ * 8 count > b, 16 full.
+ */
+lsm_status lsm_multi_sync(lsm_multi_t* h, void* stream, uint32_t* h_flags);
+
+/* Counter r_i, batch size b_i and resident elements r_i * b_i of instance i
+ * (synchronous device read). */
+lsm_status lsm_multi_stats(const lsm_multi_t* h, uint32_t i, uint64_t* r, uint32_t* b, uint64_t* resident);
+
+/* Input offset, merge tile, level-0 prefix-index shift and level count of
+ * instance i (host values; any pointer may be NULL). */
+lsm_status lsm_multi_layout(const lsm_multi_t* h, uint32_t i, uint64_t* in_off, uint32_t* tile,
+                            int32_t* fence_shift0, uint32_t* levels);
+
+/* Full levels of instance i, ascending, as key variables and values into host
+ * arrays of r_i * b_i entries (synchronises the device; tests). */
+lsm_status lsm_multi_dump_levels(const lsm_multi_t* h, uint32_t i, uint32_t* h_keys, uint32_t* h_vals);
+
+/* Empties every instance (r_i = 0) on `stream`; buffers are kept. */
+lsm_status lsm_multi_reset(lsm_multi_t* h, void* stream);
+
+/*
+ *   LSM_MULTI_OPT_GRAPH          1 (default) = rounds run as CUDA graph
+ *                                replays, 0 = plain launches.
+ *   LSM_MULTI_OPT_GRAPH_KERNELS  read-only: kernel nodes of the last round replayed.
+ *   LSM_MULTI_OPT_DEVICE_BYTES   read-only: device memory held by the handle.
+ */
+typedef enum {
+  LSM_MULTI_OPT_GRAPH = 1,
+  LSM_MULTI_OPT_GRAPH_KERNELS = 2,
+  LSM_MULTI_OPT_DEVICE_BYTES = 3
+} lsm_multi_option;
+
+lsm_status lsm_multi_set_option(lsm_multi_t* h, int opt, int64_t value);
+lsm_status lsm_multi_get_option(const lsm_multi_t* h, int opt, int64_t* value);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,8 +57,8 @@ static_assert(TileGeom<8>::kTile == kFoldTile, "the plain fold uses 8 outputs pe
 // consecutive pairs stay a permutation of one 128-byte row.
 __device__ __forceinline__ uint32_t psw(uint32_t q) { return q ^ ((q >> 4) & 15u); }
 
-// Sum over the sources of fence_j at 16-bit bin P (lanes >= S contribute 0);
-// cs = 16 - fshift of the lane's source.
+// Sum over the sources of their counts below bin P at the common shift
+// (lanes >= S contribute 0); cs = common shift - the lane's own shift.
 __device__ __forceinline__ uint64_t fence_sum(const uint32_t* f, bool act, uint32_t P, int cs, int fs,
                                               uint32_t n) {
   return warp_sum<uint64_t>(act ? fence_at(f, fs, n, P << cs) : 0u);
@@ -68,20 +68,26 @@ __device__ __forceinline__ uint64_t fence_sum(const uint32_t* f, bool act, uint3
 // holds source j when act).
 __device__ __forceinline__ uint32_t corank_lane(bool act, const uint32_t* a, const uint32_t* f, int fs,
                                                 uint32_t n, uint64_t p, uint64_t total) {
-  const int cs = 16 - fs;
+  // The search runs at the coarsest of the sources' prefix-index resolutions
+  // (shift fc), which every source's table can answer.
+  int fc = act ? fs : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) fc = max(fc, __shfl_xor_sync(0xffffffffu, fc, o));
+  const int cs = fc - fs;
+  const uint32_t nbins = 1u << (32 - fc);
   // 1. The bin: largest P with C(P) <= p, C(P) = sum of fence_j[P]
-  //    (C(0) = 0 <= p < C(65536) = total).  Start from the proportional
+  //    (C(0) = 0 <= p < C(nbins) = total).  Start from the proportional
   //    guess, gallop to a bracket, then bisect.
   uint32_t lo, hi;
   {
-    uint32_t g = uint32_t((p * kFenceBins16) / total);
-    if (g >= kFenceBins16) g = kFenceBins16 - 1;
+    uint32_t g = uint32_t((p * nbins) / total);
+    if (g >= nbins) g = nbins - 1;
     if (fence_sum(f, act, g, cs, fs, n) <= p) {
       lo = g;
       uint32_t step = 1;
       while (true) {
-        hi = lo + step < kFenceBins16 ? lo + step : kFenceBins16;
-        if (hi == kFenceBins16 || fence_sum(f, act, hi, cs, fs, n) > p) break;
+        hi = lo + step < nbins ? lo + step : nbins;
+        if (hi == nbins || fence_sum(f, act, hi, cs, fs, n) > p) break;
         lo = hi;
         step <<= 1;
       }
@@ -102,8 +108,9 @@ __device__ __forceinline__ uint32_t corank_lane(bool act, const uint32_t* a, con
   }
   // 2. Smallest key x in the bin with #{key <= x} > p.  Invariant per lane:
   //    blo = #{key <= xlo - 1}, bhi = #{key <= xhi} in this lane's source.
+  //    A bin at shift fc holds the keys [P << (fc - 1), (P + 1) << (fc - 1)).
   uint32_t blo = act ? fence_at(f, fs, n, lo << cs) : 0u, bhi = act ? fence_at(f, fs, n, (lo + 1) << cs) : 0u;
-  uint32_t xlo = lo << 15, xhi = ((lo + 1) << 15) - 1;
+  uint32_t xlo = lo << (fc - 1), xhi = ((lo + 1) << (fc - 1)) - 1;
   while (xlo < xhi) {
     const uint32_t mid = xlo + ((xhi - xlo) >> 1);
     const uint32_t u = act ? upper_bound_key(a, blo, bhi, mid) : 0u;
@@ -145,8 +152,8 @@ __global__ void __launch_bounds__(256) fold_partition(FoldSources src, uint64_t 
   if (act) out[lane] = c;
 }
 
-// Sources of instance i's fold in round k: its sorted batch, then levels
-// 0 .. k-1 (lane j describes source j).
+// Source j of instance `in`'s fold into level k: the sorted batch (j = 0),
+// then levels 0 .. k - 1.
 __device__ __forceinline__ void multi_source(const MultiArena& ar, const MultiInst& in, int j,
                                              const uint32_t*& keys, const uint32_t*& vals, const uint32_t*& fence,
                                              uint32_t& n, int& fshift) {
@@ -155,7 +162,7 @@ __device__ __forceinline__ void multi_source(const MultiArena& ar, const MultiIn
     vals = ar.bvals + in.boff;
     fence = ar.fence + in.batch_fence;
     n = in.b;
-    fshift = in.fshift_batch;
+    fshift = in.fshift0;
   } else {
     keys = ar.keys + in.lvl_off[j - 1];
     vals = ar.vals + in.lvl_off[j - 1];
@@ -165,39 +172,33 @@ __device__ __forceinline__ void multi_source(const MultiArena& ar, const MultiIn
   }
 }
 
-// Largest i with prefix[i] + i * extra <= w (prefix has n + 1 entries).
-__device__ __forceinline__ uint32_t find_instance(const uint64_t* prefix, uint32_t n, uint64_t w, uint64_t extra) {
-  uint32_t lo = 0, hi = n;  // answer in [lo, hi)
-  while (hi - lo > 1) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (prefix[mid] + mid * extra <= w) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
-__global__ void __launch_bounds__(256) multi_partition(MultiFoldArgs a) {
-  const uint64_t w = (uint64_t(blockIdx.x) * 256u + threadIdx.x) >> 5;
-  const uint32_t n_inst = a.ar.n;
-  if (w >= a.total_tiles + n_inst) return;  // whole warp leaves together
-  const uint32_t i = find_instance(a.tile_prefix, n_inst, w, 1);
-  const MultiInst& in = a.ar.inst[i];
-  const uint32_t t = uint32_t(w - (a.tile_prefix[i] + i));
+// Co-ranks of every tile boundary of every instance that folds this round
+// (one warp per boundary, grid-stride over part_prefix[n] boundaries).
+__global__ void __launch_bounds__(256) multi_partition(MultiArena ar) {
   const uint32_t lane = lane_id();
-  const int S = a.k + 1;
-  const bool act = lane < uint32_t(S);
-  const uint32_t *keys = nullptr, *vals = nullptr, *fence = nullptr;
-  uint32_t n = 0;
-  int fs = 16;
-  if (act) multi_source(a.ar, in, int(lane), keys, vals, fence, n, fs);
-  const uint64_t total = uint64_t(in.b) << a.k;
-  const uint64_t p = uint64_t(t) * a.tile < total ? uint64_t(t) * a.tile : total;
-  uint32_t* out = a.part + (a.tile_prefix[i] + i + t) * S;
-  if (p >= total) {
-    if (act) out[lane] = n;
-    return;
+  const uint64_t total_items = *reinterpret_cast<volatile const uint64_t*>(ar.part_prefix + ar.n);
+  const uint64_t nwarps = uint64_t(gridDim.x) * 8u;
+  for (uint64_t w = (uint64_t(blockIdx.x) * 256u + threadIdx.x) >> 5; w < total_items; w += nwarps) {
+    const uint32_t i = find_instance(ar.part_prefix, ar.n, w);
+    const MultiInst& in = ar.inst[i];
+    const int k = ar.k[i];
+    const uint32_t t = uint32_t(w - ar.part_prefix[i]);
+    const int S = k + 1;
+    const bool act = lane < uint32_t(S);
+    const uint32_t *keys = nullptr, *vals = nullptr, *fence = nullptr;
+    uint32_t n = 0;
+    int fs = 16;
+    if (act) multi_source(ar, in, int(lane), keys, vals, fence, n, fs);
+    const uint64_t total = uint64_t(in.b) << k;
+    const uint64_t p = uint64_t(t) * in.tile < total ? uint64_t(t) * in.tile : total;
+    uint32_t* out = ar.part + w * kMultiPartStride;
+    if (p >= total) {
+      if (act) out[lane] = n;
+      continue;
+    }
+    const uint32_t c = corank_lane(act, keys, fence, fs, n, p, total);
+    if (act) out[lane] = c;
   }
-  const uint32_t c = corank_lane(act, keys, fence, fs, n, p, total);
-  if (act) out[lane] = c;
 }
 
 // One merge step of the tile: output[0, nA + nB) = merge of run A (the
@@ -275,13 +276,13 @@ struct MergeShared {
 };
 
 // Merge tile `tile` of a fold whose sources are `src` (rank order), whose
-// co-ranks are part[(tile) * S + j] .. part[(tile + 1) * S + j], into
-// out_k/out_v.  `bar` is an initialised mbarrier; `parity` the phase this
+// co-ranks are part[tile * pstride + j] .. part[(tile + 1) * pstride + j],
+// into out_k/out_v.  `bar` is an initialised mbarrier; `parity` the phase this
 // tile's copies complete.  Returns false if a copy never arrived (the CTA
 // must then stop).  Called by all threads of the CTA.
 template <int E, bool kCleanup>
 __device__ __forceinline__ bool merge_tile(const FoldSources& src, uint64_t total, const uint32_t* __restrict__ part,
-                                           uint32_t tile, uint32_t ntiles, uint32_t* __restrict__ out_k,
+                                           uint32_t pstride, uint32_t tile, uint32_t ntiles, uint32_t* __restrict__ out_k,
                                            uint32_t* __restrict__ out_v, uint32_t* __restrict__ out_fence,
                                            int fshift, uint32_t* status, uint64_t* lookback, uint64_t* out_count,
                                            uint32_t* sm, MergeShared& sh, uint64_t* bar, uint32_t parity) {
@@ -300,8 +301,8 @@ __device__ __forceinline__ bool merge_tile(const FoldSources& src, uint64_t tota
     uint32_t c0 = 0, c1 = 0, a0 = 0, span = 0, prev = 0;
     bool has_prev = false;
     if (lane < uint32_t(S)) {
-      c0 = part[uint64_t(tile) * S + lane];
-      c1 = part[uint64_t(tile + 1) * S + lane];
+      c0 = part[uint64_t(tile) * pstride + lane];
+      c1 = part[uint64_t(tile + 1) * pstride + lane];
       if (c1 > c0) {
         a0 = c0 & ~3u;
         span = ((c1 + 3u) & ~3u) - a0;
@@ -535,14 +536,14 @@ __global__ void __launch_bounds__(kThreads) fold_merge(FoldSources src, uint64_t
     fence_mbar_init();
   }
   __syncthreads();
-  merge_tile<8, kCleanup>(src, total, part, s_tile, ntiles, out_k, out_v, out_fence, fshift, status, lookback,
+  merge_tile<8, kCleanup>(src, total, part, uint32_t(src.count), s_tile, ntiles, out_k, out_v, out_fence, fshift, status, lookback,
                           out_count, sm, sh, &s_bar, 0);
 }
 
 // Persistent merge for every (instance, tile) of a round: each CTA takes
-// work items from an atomic counter until none is left.
-template <int E>
-__global__ void __launch_bounds__(kThreads) multi_merge(MultiFoldArgs a) {
+// work items from an atomic counter until none is left.  An instance's tile
+// size (1024 or 2048 outputs) selects the tile code per item.
+__global__ void __launch_bounds__(kThreads) multi_merge(MultiArena ar) {
   extern __shared__ __align__(128) uint32_t sm[];
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ MergeShared sh;
@@ -553,25 +554,27 @@ __global__ void __launch_bounds__(kThreads) multi_merge(MultiFoldArgs a) {
     mbar_init(&s_bar, 1);
     fence_mbar_init();
   }
-  const int S = a.k + 1;
+  const uint64_t total_items = *reinterpret_cast<volatile const uint64_t*>(ar.tile_prefix + ar.n);
   for (uint32_t iter = 0;; ++iter) {
     __syncthreads();  // the previous item is finished with the shared state
     if (threadIdx.x == 0) {
-      const uint64_t w = atomicAdd(a.work_ctr, 1u);
+      const uint64_t w = atomicAdd(ar.work_ctr, 1u);
       s_item = w;
-      if (w < a.total_tiles) s_inst = find_instance(a.tile_prefix, a.ar.n, w, 0);
+      if (w < total_items) s_inst = find_instance(ar.tile_prefix, ar.n, w);
     }
     __syncthreads();
     const uint64_t w = s_item;
-    if (w >= a.total_tiles) break;
+    if (w >= total_items) break;
     const uint32_t i = s_inst;
-    const MultiInst& in = a.ar.inst[i];
+    const MultiInst& in = ar.inst[i];
+    const int k = ar.k[i];
+    const int S = k + 1;
     if (threadIdx.x < uint32_t(S)) {
-      const uint32_t *k = nullptr, *v = nullptr, *f = nullptr;
+      const uint32_t *kk = nullptr, *v = nullptr, *f = nullptr;
       uint32_t n = 0;
       int fs = 16;
-      multi_source(a.ar, in, int(threadIdx.x), k, v, f, n, fs);
-      s_src.keys[threadIdx.x] = k;
+      multi_source(ar, in, int(threadIdx.x), kk, v, f, n, fs);
+      s_src.keys[threadIdx.x] = kk;
       s_src.vals[threadIdx.x] = v;
       s_src.fence[threadIdx.x] = f;
       s_src.n[threadIdx.x] = n;
@@ -579,16 +582,91 @@ __global__ void __launch_bounds__(kThreads) multi_merge(MultiFoldArgs a) {
     }
     if (threadIdx.x == 0) s_src.count = S;
     __syncthreads();
-    const uint64_t total = uint64_t(in.b) << a.k;
-    const uint32_t t = uint32_t(w - a.tile_prefix[i]);
-    const uint32_t ntiles = uint32_t(a.tile_prefix[i + 1] - a.tile_prefix[i]);
-    const uint32_t* part = a.part + (a.tile_prefix[i] + i) * S;
-    uint32_t* ok = a.ar.keys + in.lvl_off[a.k];
-    uint32_t* ov = a.ar.vals + in.lvl_off[a.k];
-    uint32_t* of = a.ar.fence + in.lvl_fence[a.k];
-    if (!merge_tile<E, false>(s_src, total, part, t, ntiles, ok, ov, of, in.lvl_fshift[a.k], a.status, nullptr,
-                              nullptr, sm, sh, &s_bar, iter & 1u))
-      break;
+    const uint64_t total = uint64_t(in.b) << k;
+    const uint32_t t = uint32_t(w - ar.tile_prefix[i]);
+    const uint32_t ntiles = uint32_t(ar.tile_prefix[i + 1] - ar.tile_prefix[i]);
+    const uint32_t* part = ar.part + ar.part_prefix[i] * kMultiPartStride;
+    uint32_t* ok = ar.keys + in.lvl_off[k];
+    uint32_t* ov = ar.vals + in.lvl_off[k];
+    uint32_t* of = ar.fence + in.lvl_fence[k];
+    const int fs = in.lvl_fshift[k];
+    const bool done =
+        in.tile == TileGeom<4>::kTile
+            ? merge_tile<4, false>(s_src, total, part, kMultiPartStride, t, ntiles, ok, ov, of, fs, ar.status,
+                                   nullptr, nullptr, sm, sh, &s_bar, iter & 1u)
+            : merge_tile<8, false>(s_src, total, part, kMultiPartStride, t, ntiles, ok, ov, of, fs, ar.status,
+                                   nullptr, nullptr, sm, sh, &s_bar, iter & 1u);
+    if (!done) break;
+  }
+}
+
+// The round's plan, one CTA: for every instance with a batch this round,
+// the fold's target level k = ffz(r) (§III-B) and r += 1, or the reason the
+// batch is refused; then the prefix sums of merge tiles and partition
+// boundaries over the instances, and the merge queue reset.
+__global__ void __launch_bounds__(1024) multi_prep(MultiArena ar, MultiBatch in) {
+  __shared__ uint64_t s_w1[32], s_w2[32];
+  __shared__ uint64_t s_carry_t, s_carry_p;
+  __shared__ uint32_t s_err;
+  const uint32_t tid = threadIdx.x;
+  if (tid == 0) {
+    s_carry_t = 0;
+    s_carry_p = 0;
+    s_err = 0;
+  }
+  __syncthreads();
+  for (uint32_t base = 0; base < ar.n; base += 1024) {
+    const uint32_t i = base + tid;
+    uint64_t nt = 0, np = 0;
+    if (i < ar.n) {
+      const MultiInst& d = ar.inst[i];
+      const uint32_t nops = in.counts ? __ldg(in.counts + i) : d.b;
+      uint32_t fl = 0;
+      int k = -1;
+      if (nops > d.b) {
+        fl = kErrArg;
+      } else if (nops > 0) {
+        if (ar.badkey[i]) {
+          fl = kErrBadKey;
+        } else {
+          const uint32_t r = ar.r[i];
+          const int kk = (~r) ? __ffs(~r) - 1 : 32;
+          if (kk >= int(d.levels)) {
+            fl = kErrFull;
+          } else {
+            k = kk;
+            ar.r[i] = r + 1;
+            if (k > 0) {
+              nt = ((uint64_t(d.b) << k) + d.tile - 1) / d.tile;
+              np = nt + 1;
+            }
+          }
+        }
+      }
+      ar.badkey[i] = 0;
+      ar.k[i] = k;
+      ar.flags[i] = fl;
+      if (fl) atomicOr(&s_err, fl);
+    }
+    uint64_t tt, tp;
+    const uint64_t et = block_excl_scan<1024, uint64_t>(nt, s_w1, tt);
+    const uint64_t ep = block_excl_scan<1024, uint64_t>(np, s_w2, tp);
+    if (i < ar.n) {
+      ar.tile_prefix[i] = s_carry_t + et;
+      ar.part_prefix[i] = s_carry_p + ep;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      s_carry_t += tt;
+      s_carry_p += tp;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    ar.tile_prefix[ar.n] = s_carry_t;
+    ar.part_prefix[ar.n] = s_carry_p;
+    *ar.work_ctr = 0u;
+    if (s_err) atomicOr(ar.status, s_err);
   }
 }
 
@@ -683,31 +761,45 @@ cudaError_t fold_launch(const FoldArgs& a, cudaStream_t st) {
   return fold_merge_launch(a, st);
 }
 
-cudaError_t multi_fold_launch(const MultiFoldArgs& a, cudaStream_t st) {
-  static bool attr_set = false;
+cudaError_t multi_prep_launch(const MultiArena& ar, const MultiBatch& in, cudaStream_t st) {
+  count_launches(1);
+  multi_prep<<<1, 1024, 0, st>>>(ar, in);
+  return cudaGetLastError();
+}
+
+cudaError_t multi_update_launch(const MultiArena& ar, const MultiBatch& in, cudaStream_t st) {
   cudaError_t e;
-  if (!attr_set) {
-    if ((e = set_smem(multi_merge<8>, TileGeom<8>::kSmem)) != cudaSuccess) return e;
-    if ((e = set_smem(multi_merge<4>, TileGeom<4>::kSmem)) != cudaSuccess) return e;
-    attr_set = true;
-  }
-  if (a.total_tiles == 0) return cudaSuccess;
-  const uint64_t warps = a.total_tiles + a.ar.n;
+  if ((e = multi_sort_count_launch(ar, in, st)) != cudaSuccess) return e;
+  if ((e = multi_prep_launch(ar, in, st)) != cudaSuccess) return e;
+  if ((e = multi_sort_launch(ar, in, st)) != cudaSuccess) return e;
+  return multi_fold_launch(ar, st);
+}
+
+static int g_merge_per_sm = 0;  // resident multi_merge CTAs per SM
+
+cudaError_t multi_prepare_kernels() {
+  cudaError_t e;
+  if ((e = multi_sort_prepare()) != cudaSuccess) return e;
+  constexpr size_t smem = TileGeom<8>::kSmem;
+  if ((e = set_smem(multi_merge, smem)) != cudaSuccess) return e;
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, multi_merge, kThreads, smem)) != cudaSuccess)
+    return e;
+  g_merge_per_sm = per_sm < 1 ? 1 : per_sm;
+  return cudaSuccess;
+}
+
+cudaError_t multi_fold_launch(const MultiArena& ar, cudaStream_t st) {
+  cudaError_t e;
+  if (g_merge_per_sm == 0 && (e = multi_prepare_kernels()) != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   count_launches(1);
-  multi_partition<<<unsigned((warps * 32 + 255) / 256), 256, 0, st>>>(a);
+  multi_partition<<<unsigned(sms) * 8u, 256, 0, st>>>(ar);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(a.work_ctr, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
-  int dev = 0, sms = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   count_launches(1);
-  if (a.tile == int(TileGeom<4>::kTile)) {
-    const unsigned grid = unsigned(sms) * 6u;
-    multi_merge<4><<<grid, kThreads, TileGeom<4>::kSmem, st>>>(a);
-  } else {
-    const unsigned grid = unsigned(sms) * 4u;
-    multi_merge<8><<<grid, kThreads, TileGeom<8>::kSmem, st>>>(a);
-  }
+  multi_merge<<<unsigned(sms) * unsigned(g_merge_per_sm), kThreads, TileGeom<8>::kSmem, st>>>(ar);
   return cudaGetLastError();
 }
 

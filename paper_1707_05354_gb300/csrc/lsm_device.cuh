@@ -103,6 +103,18 @@ __device__ __forceinline__ void fence_fill_gaps(uint32_t* f, const FenceGap* s_g
   }
 }
 
+// Largest i < n with prefix[i] <= w, for w < prefix[n] (prefix has n + 1
+// non-decreasing entries, so the instance found owns item w even when
+// instances with no items share its prefix value).
+__device__ __forceinline__ uint32_t find_instance(const uint64_t* prefix, uint32_t n, uint64_t w) {
+  uint32_t lo = 0, hi = n;  // answer in [lo, hi)
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(prefix + mid) <= w) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T x) {
 #pragma unroll

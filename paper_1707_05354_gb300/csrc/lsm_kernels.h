@@ -102,19 +102,17 @@ constexpr int kFoldTile = 2048;  // output elements per merge CTA
 // fence[P] = number of elements whose bin is < P, for P = 0 .. 2^(32-fshift):
 // the start of the run of key variables in [P << fshift, (P + 1) << fshift).
 // One table per level and one for the sorted batch, written whenever the run
-// is written.  fshift is chosen per run so that a bin holds about 8 elements
-// (a 32-byte sector of keys), between 8 and 16 (2^24 .. 2^16 bins).  Every
-// table also answers at the common 16-bit resolution: entry P16 << (16 -
-// fshift).
-constexpr uint32_t kFenceBins16 = 65536;
-constexpr int kFenceMinShift = 8, kFenceMaxShift = 16;
+// is written.  fshift is chosen per run so that a bin holds about 2^e
+// elements (e = 3: a 32-byte sector of keys), with between 2^lo and 2^24
+// bins.  A table at shift s also answers at any coarser shift s' >= s: entry
+// P' << (s' - s).
 __host__ __device__ inline uint32_t fence_bin(uint32_t kv, int fshift) { return kv >> fshift; }
 __host__ __device__ inline uint32_t fence_bins(int fshift) { return 1u << (32 - fshift); }
-inline int fence_shift_for(uint64_t n) {
+inline int fence_shift_for(uint64_t n, int e = 3, int lo = 16) {
   int lg = 0;
   while ((2ull << lg) <= n) ++lg;      // floor(log2 n)
-  int fb = lg - 3;                     // about 8 elements per bin
-  fb = fb < 16 ? 16 : (fb > 24 ? 24 : fb);
+  int fb = lg - e;
+  fb = fb < lo ? lo : (fb > 24 ? 24 : fb);
   return 32 - fb;
 }
 inline uint64_t fence_words(int fshift) { return uint64_t(fence_bins(fshift)) + 4; }
@@ -166,45 +164,95 @@ struct DistributeArgs {
 cudaError_t distribute_launch(const DistributeArgs& a, cudaStream_t st);
 
 // ------------------------------------------------------ many dictionaries ---
-// The batched form: n independent dictionaries with their own batch sizes,
-// all advanced by one batch per round (so all share r and k = ffz(r)).
-constexpr int kMultiMaxLevels = 16;
+// The batched form: n independent dictionaries, each with its own batch size
+// b_i and levels b_i * 2^l, advanced together.  A round gives every instance
+// at most one batch; all per-round decisions (which level each fold fills,
+// how many tiles it has) are taken on the device from the instances' counters
+// r_i, so one captured sequence of launches serves every round.
+constexpr int kMultiMaxLevels = 16;            // levels per instance
+constexpr int kMultiPartStride = kMultiMaxLevels + 1;  // co-rank words per tile boundary
+constexpr uint32_t kMultiMaxB = 1u << 20;      // largest per-instance batch
+constexpr uint32_t kMultiSortTile = 4096;      // elements per sort tile (count/scatter CTA)
 
-struct MultiInst {
-  uint64_t boff;        // start of the instance's batch in the input and sorted-batch buffers
-  uint32_t b;           // its batch size
-  uint32_t sort_tile0;  // its first sort tile
-  uint32_t sort_tiles;  // number of its sort tiles (kMsdTile elements each)
-  int32_t fshift_batch;
-  uint64_t batch_fence;                   // prefix index of the sorted batch (fence arena offset)
-  uint64_t lvl_off[kMultiMaxLevels];      // element offset of level l in the level arena
-  uint64_t lvl_fence[kMultiMaxLevels];    // fence arena offset of level l's prefix index
+// Per-instance error bits of a round (also ORed into the device status word).
+constexpr uint32_t kErrArg = 8u;     // more ops than the batch size
+constexpr uint32_t kErrFull = 16u;   // the fold would need a level beyond the capacity
+
+struct MultiInst {           // fixed at creation
+  uint64_t in_off;           // first op of its batch in the caller's input arrays (sum of earlier b)
+  uint64_t boff;             // its sorted batch / sort scratch start (a multiple of kLevelAlign)
+  uint32_t b;                // batch size
+  uint32_t levels;           // allocated levels: a batch is refused once ffz(r) >= levels
+  uint32_t msd_bits;         // d: the batch sort's buckets are the top d bits of the key variable
+  uint32_t tile;             // merge tile: 1024 or 2048 output elements
+  uint32_t stile0;           // first global sort tile
+  uint32_t bucket0;          // first global bucket
+  int32_t fshift0;           // prefix-index shift of the sorted batch and level 0
+  uint32_t pad_;
+  uint64_t batch_fence;      // fence arena offset of the sorted batch's prefix index
+  uint64_t lvl_off[kMultiMaxLevels];    // level arena offset of level l
+  uint64_t lvl_fence[kMultiMaxLevels];  // fence arena offset of level l's prefix index
   int32_t lvl_fshift[kMultiMaxLevels];
 };
 
 struct MultiArena {
-  uint32_t* keys;    // level arena
-  uint32_t* vals;
-  uint32_t* bkeys;   // sorted batches, instance i at boff_i
-  uint32_t* bvals;
-  uint32_t* fence;   // fence arena
-  const MultiInst* inst;
+  const MultiInst* inst;     // n descriptors
   uint32_t n;
+  uint32_t* keys;            // level arena
+  uint32_t* vals;
+  uint32_t* bkeys;           // sorted batches (at boff)
+  uint32_t* bvals;
+  uint32_t* tkeys;           // bucket scatter scratch (at boff)
+  uint32_t* tvals;
+  uint32_t* fence;           // fence arena
+  const uint64_t* stile_prefix;   // n + 1: sort tiles before instance i
+  const uint64_t* bucket_prefix;  // n + 1: buckets before instance i
+  uint64_t total_stiles, total_buckets;
+  uint32_t* tilecnt;         // per sort tile 256 bucket counts, then 256 output offsets
+  uint32_t* bstart;          // per global bucket: start in the instance's batch
+  uint32_t* bcnt;            // per global bucket: element count
+  // device state
+  uint32_t* r;               // batches applied per instance
+  int32_t* k;                // this round's fold target level, -1 when the instance has no batch
+  uint32_t* badkey;          // per instance: a key out of range this round (cleared by the prep kernel)
+  uint32_t* flags;           // per instance: error bits of the last round
+  uint64_t* tile_prefix;     // n + 1: merge tiles before instance i this round
+  uint64_t* part_prefix;     // n + 1: partition boundaries before instance i
+  uint32_t* part;            // co-ranks, kMultiPartStride words per boundary
+  uint32_t* work_ctr;        // head of the persistent merge's work queue
+  uint32_t* status;          // sticky device status word
 };
 
-// One round's fold for every instance: batch + levels 0..k-1 -> level k.
-// tile_prefix[i] = merge tiles of the instances before i (n + 1 entries).
-struct MultiFoldArgs {
-  MultiArena ar;
-  int k;
-  int tile;                     // output elements per merge tile
-  const uint64_t* tile_prefix;  // device, n + 1
-  uint64_t total_tiles;
-  uint32_t* part;               // (total_tiles + n) * (k + 1) co-ranks
-  uint32_t* work_ctr;           // zeroed by the launcher
-  uint32_t* status;
+// One round's input: instance i's ops are keys/vals/del[in_off_i ..
+// in_off_i + counts[i]); counts null means b_i ops for every instance.
+struct MultiBatch {
+  const uint32_t* keys;
+  const uint32_t* vals;      // null: values 0 (pure deletes need none)
+  const uint8_t* del;        // null: every op an insert
+  const uint32_t* counts;
 };
-cudaError_t multi_fold_launch(const MultiFoldArgs& a, cudaStream_t st);
+
+// Enqueues one round of updates for every instance: bucket counts, the
+// round's plan (prep), offsets, scatter, bucket sort (into level 0 when
+// k_i = 0, else the sorted-batch buffer), co-rank partition and the
+// persistent merge.  Launch shapes depend only on the arena, never on the
+// device state, so the sequence can be captured once and replayed.
+cudaError_t multi_update_launch(const MultiArena& ar, const MultiBatch& in, cudaStream_t st);
+
+// Sets the kernels' launch attributes once (before any capture).
+cudaError_t multi_prepare_kernels();
+cudaError_t multi_sort_prepare();
+
+// The parts of multi_update_launch (exposed for the launch list and tests).
+cudaError_t multi_sort_count_launch(const MultiArena& ar, const MultiBatch& in, cudaStream_t st);
+cudaError_t multi_prep_launch(const MultiArena& ar, const MultiBatch& in, cudaStream_t st);
+cudaError_t multi_sort_launch(const MultiArena& ar, const MultiBatch& in, cudaStream_t st);
+cudaError_t multi_fold_launch(const MultiArena& ar, cudaStream_t st);
+
+// Lookups: query g belongs to the instance i with qoff[i] <= g < qoff[i + 1]
+// (qoff has n + 1 entries, qoff[n] = nq).
+cudaError_t multi_lookup_launch(const MultiArena& ar, const uint32_t* q, const uint64_t* qoff, uint64_t nq,
+                                uint32_t* val, uint8_t* found, cudaStream_t st);
 
 // ----------------------------------------------------------------- query ---
 struct LevelSet {

@@ -297,6 +297,47 @@ unsigned persistent_grid(uint64_t work, int per_block, unsigned cap) {
   return unsigned(b ? b : 1);
 }
 
+// Lookup in the batched form: query g belongs to instance i with
+// qoff[i] <= g < qoff[i + 1] and searches that instance's full levels (the
+// set bits of r_i), newest first, exactly as lookup_one does.
+__global__ void __launch_bounds__(kThreads) multi_lookup(MultiArena ar, const uint32_t* __restrict__ q,
+                                                         const uint64_t* __restrict__ qoff, uint64_t nq,
+                                                         uint32_t* __restrict__ out_v,
+                                                         uint8_t* __restrict__ out_f) {
+  for (uint64_t g = blockIdx.x * uint64_t(kThreads) + threadIdx.x; g < nq; g += uint64_t(gridDim.x) * kThreads) {
+    const uint32_t i = find_instance(qoff, ar.n, g);
+    const MultiInst& d = ar.inst[i];
+    const uint32_t key = __ldg(q + g);
+    uint32_t val = 0;
+    uint8_t found = 0;
+    if (key <= kMaxUserKey) {
+      const uint32_t target = key << 1;
+      uint32_t r = ar.r[i];
+      while (r) {
+        const int l = __ffs(r) - 1;
+        r &= r - 1;
+        const uint32_t* keys = ar.keys + d.lvl_off[l];
+        const uint32_t* f = ar.fence + d.lvl_fence[l];
+        const int fs = d.lvl_fshift[l];
+        const uint32_t n = d.b << l, bin = fence_bin(target, fs);
+        const uint32_t pos = lower_bound_kv(keys, fence_at(f, fs, n, bin), fence_at(f, fs, n, bin + 1), target);
+        if (pos < n) {
+          const uint32_t kv = __ldg(keys + pos);
+          if (key_of(kv) == key) {
+            if (kv & 1u) {
+              found = 1;
+              val = __ldg(ar.vals + d.lvl_off[l] + pos);
+            }
+            break;
+          }
+        }
+      }
+    }
+    out_v[g] = val;
+    out_f[g] = found;
+  }
+}
+
 }  // namespace
 
 cudaError_t lookup_launch(const LevelSet& ls, const uint32_t* q, uint64_t nq, uint32_t* val, uint8_t* found,
@@ -352,6 +393,15 @@ cudaError_t range_emit_launch(const LevelSet& ls, uint64_t nq, const uint32_t* b
   else if (ls.count <= 8) range_emit<8><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals);
   else if (ls.count <= 16) range_emit<16><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals);
   else range_emit<kMaxLevels><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals);
+  return cudaGetLastError();
+}
+
+
+cudaError_t multi_lookup_launch(const MultiArena& ar, const uint32_t* q, const uint64_t* qoff, uint64_t nq,
+                                uint32_t* val, uint8_t* found, cudaStream_t st) {
+  if (nq == 0) return cudaSuccess;
+  count_launches(1);
+  multi_lookup<<<persistent_grid(nq, kThreads, 152 * 8), kThreads, 0, st>>>(ar, q, qoff, nq, val, found);
   return cudaGetLastError();
 }
 

@@ -425,37 +425,32 @@ __device__ __forceinline__ uint32_t lower_bound_bin(const uint32_t* a, uint32_t 
   return lo;
 }
 
-// Prefix-index entries of bucket d (the bins whose top byte is d) from the
-// sorted bucket a[0, m) starting at position start.
-__device__ __forceinline__ void bucket_fence(const uint32_t* a, uint32_t m, uint32_t start, uint32_t d,
-                                             uint32_t* fence, int fshift) {
-  const uint32_t per = 1u << (24 - fshift);  // bins per bucket
-  for (uint32_t i = threadIdx.x; i < per; i += blockDim.x) {
-    const uint32_t bin = d * per + i;
-    fence[bin] = start + lower_bound_bin(a, m, bin, fshift);
-  }
+// Prefix-index entries of bins [bin0, bin0 + nbins) from the sorted run
+// a[0, m) that starts at position start and holds exactly those bins.
+__device__ __forceinline__ void bucket_fence(const uint32_t* a, uint32_t m, uint32_t start, uint32_t bin0,
+                                             uint32_t nbins, uint32_t* fence, int fshift) {
+  for (uint32_t i = threadIdx.x; i < nbins; i += blockDim.x)
+    fence[bin0 + i] = start + lower_bound_bin(a, m, bin0 + i, fshift);
 }
 
-__global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort(uint32_t* __restrict__ tmp_k,
-                                                              uint32_t* __restrict__ tmp_v,
-                                                              uint32_t* __restrict__ out_k,
-                                                              uint32_t* __restrict__ out_v,
-                                                              const uint32_t* __restrict__ ctl, uint32_t n,
-                                                              uint32_t* __restrict__ fence, int fshift,
-                                                              uint32_t* __restrict__ next_ctl) {
-  extern __shared__ __align__(16) uint32_t bsm[];
+// One bucket, one CTA of kBucketThreads: sorts tmp[start, start + m) by bits
+// 0 .. 8 npass - 1 of the key variable (stable 8-bit passes) into
+// out[start, start + m), and writes the prefix-index entries of the bucket's
+// bins [bin0, bin0 + nbins) when fence is given.  Up to kBucketCap elements
+// are sorted in shared memory (bsm: 4 kBucketCap words); a larger bucket
+// (heavy duplicate keys) is sorted in chunks through global memory, still
+// stably.
+__device__ __forceinline__ void bucket_body(uint32_t* tmp_k, uint32_t* tmp_v, uint32_t* out_k, uint32_t* out_v,
+                                            uint32_t start, uint32_t m, int npass, uint32_t* __restrict__ fence,
+                                            int fshift, uint32_t bin0, uint32_t nbins, uint32_t* bsm,
+                                            uint32_t* s_scan) {
   __shared__ uint32_t s_whist[kBucketWarps][kRadix];
-  __shared__ uint32_t s_excl[kRadix], s_run[kRadix], s_tot[kRadix], s_scan[kBucketWarps];
+  __shared__ uint32_t s_excl[kRadix], s_run[kRadix], s_tot[kRadix];
   uint32_t* ak = bsm;
   uint32_t* av = bsm + kBucketCap;
   uint32_t* bk = bsm + 2 * kBucketCap;
   uint32_t* bv = bsm + 3 * kBucketCap;
-  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5, d = blockIdx.x;
-  // the control block of the next sort starts zeroed (it is idle now)
-  if (d == 0)
-    for (uint32_t i = tid; i < uint32_t(kSortCtlWords); i += kBucketThreads) next_ctl[i] = 0u;
-  const uint32_t start = bucket_start<kBucketThreads>(ctl, d, s_scan);
-  const uint32_t m = ctl[3 * kRadix + d];
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint32_t wbase = warp * (32 * kBucketIPT);
   uint32_t kv[kBucketIPT], v[kBucketIPT], rank[kBucketIPT];
 
@@ -466,7 +461,7 @@ __global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort(uint32_t* __res
     }
     __syncthreads();
     uint32_t *sk = ak, *sv = av, *dk = bk, *dv = bv;
-    for (int pass = 0; pass < 3; ++pass) {
+    for (int pass = 0; pass < npass; ++pass) {
       const int shift = 8 * pass;
 #pragma unroll
       for (int j = 0; j < kBucketIPT; ++j) {
@@ -494,54 +489,82 @@ __global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort(uint32_t* __res
       out_k[start + i] = sk[i];
       out_v[start + i] = sv[i];
     }
-    if (fence) bucket_fence(sk, m, start, d, fence, fshift);
-  } else {
-    // Chunked: three stable passes over [start, start + m) through global
-    // memory, tmp -> out -> tmp -> out, kBucketCap elements at a time in order.
-    uint32_t* srck = tmp_k;
-    uint32_t* srcv = tmp_v;
-    uint32_t* dstk = out_k;
-    uint32_t* dstv = out_v;
-    for (int pass = 0; pass < 3; ++pass) {
-      const int shift = 8 * pass;
-      if (tid < kRadix) s_tot[tid] = 0;
-      __syncthreads();
-      for (uint32_t i = tid; i < m; i += kBucketThreads) atomicAdd(&s_tot[(srck[start + i] >> shift) & 255u], 1u);
-      __syncthreads();
-      uint32_t all;
-      const uint32_t ex = block_excl_scan<kBucketThreads>(tid < kRadix ? s_tot[tid] : 0u, s_scan, all);
-      if (tid < kRadix) s_run[tid] = ex;
-      __syncthreads();
-      for (uint32_t c0 = 0; c0 < m; c0 += kBucketCap) {
-        const uint32_t cm = (m - c0) < kBucketCap ? (m - c0) : kBucketCap;
-#pragma unroll
-        for (int j = 0; j < kBucketIPT; ++j) {
-          const uint32_t p = wbase + j * 32 + lane;
-          kv[j] = p < cm ? srck[start + c0 + p] : 0u;
-          v[j] = p < cm ? srcv[start + c0 + p] : 0u;
-        }
-        rank_block<kBucketThreads, kBucketIPT>(kv, cm, wbase, shift, rank, s_whist, s_excl, s_scan, s_tot);
-#pragma unroll
-        for (int j = 0; j < kBucketIPT; ++j) {
-          const uint32_t p = wbase + j * 32 + lane;
-          if (p < cm) {
-            const uint32_t dg = (kv[j] >> shift) & 255u;
-            const uint32_t pos = s_run[dg] + s_whist[warp][dg] + rank[j];
-            dstk[start + pos] = kv[j];
-            dstv[start + pos] = v[j];
-          }
-        }
-        __syncthreads();
-        if (tid < kRadix) s_run[tid] += s_tot[tid];
-        __syncthreads();
-      }
-      uint32_t* t;
-      t = srck; srck = dstk; dstk = t;
-      t = srcv; srcv = dstv; dstv = t;
-    }
-    // after three passes the data sits in out (tmp -> out -> tmp -> out)
-    if (fence) bucket_fence(out_k + start, m, start, d, fence, fshift);
+    if (fence) bucket_fence(sk, m, start, bin0, nbins, fence, fshift);
+    return;
   }
+  // Chunked: npass stable passes over [start, start + m) through global
+  // memory, alternating tmp -> out -> tmp ..., kBucketCap elements at a time
+  // in order; an even pass count ends in tmp and is copied to out.
+  const uint32_t* srck = tmp_k;
+  const uint32_t* srcv = tmp_v;
+  uint32_t* dstk = out_k;
+  uint32_t* dstv = out_v;
+  for (int pass = 0; pass < npass; ++pass) {
+    const int shift = 8 * pass;
+    if (tid < kRadix) s_tot[tid] = 0;
+    __syncthreads();
+    for (uint32_t i = tid; i < m; i += kBucketThreads) atomicAdd(&s_tot[(srck[start + i] >> shift) & 255u], 1u);
+    __syncthreads();
+    uint32_t all;
+    const uint32_t ex = block_excl_scan<kBucketThreads>(tid < kRadix ? s_tot[tid] : 0u, s_scan, all);
+    if (tid < kRadix) s_run[tid] = ex;
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < m; c0 += kBucketCap) {
+      const uint32_t cm = (m - c0) < kBucketCap ? (m - c0) : kBucketCap;
+#pragma unroll
+      for (int j = 0; j < kBucketIPT; ++j) {
+        const uint32_t p = wbase + j * 32 + lane;
+        kv[j] = p < cm ? srck[start + c0 + p] : 0u;
+        v[j] = p < cm ? srcv[start + c0 + p] : 0u;
+      }
+      rank_block<kBucketThreads, kBucketIPT>(kv, cm, wbase, shift, rank, s_whist, s_excl, s_scan, s_tot);
+#pragma unroll
+      for (int j = 0; j < kBucketIPT; ++j) {
+        const uint32_t p = wbase + j * 32 + lane;
+        if (p < cm) {
+          const uint32_t dg = (kv[j] >> shift) & 255u;
+          const uint32_t pos = s_run[dg] + s_whist[warp][dg] + rank[j];
+          dstk[start + pos] = kv[j];
+          dstv[start + pos] = v[j];
+        }
+      }
+      __syncthreads();
+      if (tid < kRadix) s_run[tid] += s_tot[tid];
+      __syncthreads();
+    }
+    if (pass & 1) {
+      srck = tmp_k; srcv = tmp_v; dstk = out_k; dstv = out_v;
+    } else {
+      srck = out_k; srcv = out_v; dstk = tmp_k; dstv = tmp_v;
+    }
+  }
+  if (!(npass & 1)) {
+    for (uint32_t i = tid; i < m; i += kBucketThreads) {
+      out_k[start + i] = tmp_k[start + i];
+      out_v[start + i] = tmp_v[start + i];
+    }
+    __syncthreads();
+  }
+  if (fence) bucket_fence(out_k + start, m, start, bin0, nbins, fence, fshift);
+}
+
+__global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort(uint32_t* __restrict__ tmp_k,
+                                                              uint32_t* __restrict__ tmp_v,
+                                                              uint32_t* __restrict__ out_k,
+                                                              uint32_t* __restrict__ out_v,
+                                                              const uint32_t* __restrict__ ctl, uint32_t n,
+                                                              uint32_t* __restrict__ fence, int fshift,
+                                                              uint32_t* __restrict__ next_ctl) {
+  extern __shared__ __align__(16) uint32_t bsm[];
+  __shared__ uint32_t s_scan[kBucketWarps];
+  const uint32_t tid = threadIdx.x, d = blockIdx.x;
+  // the control block of the next sort starts zeroed (it is idle now)
+  if (d == 0)
+    for (uint32_t i = tid; i < uint32_t(kSortCtlWords); i += kBucketThreads) next_ctl[i] = 0u;
+  const uint32_t start = bucket_start<kBucketThreads>(ctl, d, s_scan);
+  const uint32_t m = ctl[3 * kRadix + d];
+  const uint32_t per = fence ? 1u << (24 - fshift) : 0u;  // bins per bucket
+  bucket_body(tmp_k, tmp_v, out_k, out_v, start, m, 3, fence, fshift, d * per, per, bsm, s_scan);
   // the bucket sort writes every entry: the populated range is all bins
   if (fence && d == kRadix - 1 && tid == 0) {
     fence[fence_bins(fshift)] = n;
@@ -556,6 +579,184 @@ __global__ void __launch_bounds__(256) check_keys(const uint32_t* __restrict__ k
   for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < n; i += uint64_t(gridDim.x) * 256ull)
     bad |= __ldg(keys + i) > kMaxUserKey;
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kErrBadKey);
+}
+
+// ---------------------------------------------------------------------------
+// The batch sort of the batched form: the same bucket scheme on every
+// instance's batch at once.  Instance i splits on the top d_i bits of the key
+// variable (2^d_i buckets of about 4096 elements); its batch is cut into
+// kMultiSortTile-element tiles; one launch per phase covers every tile or
+// bucket of every instance.  Instances without a batch this round (count 0,
+// or refused by the prep kernel) leave at once.
+// ---------------------------------------------------------------------------
+constexpr int kMultiIPT = int(kMultiSortTile) / kThreads;  // 16
+static_assert(kMultiIPT * kThreads == int(kMultiSortTile), "tile");
+
+__device__ __forceinline__ uint32_t multi_ops(const MultiBatch& in, const MultiInst& d, uint32_t i) {
+  return in.counts ? __ldg(in.counts + i) : d.b;
+}
+
+// Element p (< b) of instance d's reversed padded batch: op min(b-1-p, n-1).
+__device__ __forceinline__ uint32_t multi_load_key(const MultiBatch& in, const MultiInst& d, uint32_t nops,
+                                                   uint32_t p, bool& bad) {
+  uint64_t s = uint64_t(d.b) - 1 - p;
+  if (s >= nops) s = nops - 1;
+  s += d.in_off;
+  const uint32_t k = __ldg(in.keys + s);
+  const bool is_del = in.del && __ldg(in.del + s) != 0;
+  bad = k > kMaxUserKey;
+  return bad ? kPlaceboKv : ((k << 1) | (is_del ? 0u : 1u));
+}
+__device__ __forceinline__ void multi_load(const MultiBatch& in, const MultiInst& d, uint32_t nops, uint32_t p,
+                                           uint32_t& kv, uint32_t& v) {
+  uint64_t s = uint64_t(d.b) - 1 - p;
+  if (s >= nops) s = nops - 1;
+  s += d.in_off;
+  const uint32_t k = __ldg(in.keys + s);
+  const bool is_del = in.del && __ldg(in.del + s) != 0;
+  const bool bad = k > kMaxUserKey;
+  kv = bad ? kPlaceboKv : ((k << 1) | (is_del ? 0u : 1u));
+  v = (is_del || bad || !in.vals) ? 0u : __ldg(in.vals + s);
+}
+
+__global__ void __launch_bounds__(kThreads) mseg_count(MultiArena ar, MultiBatch in) {
+  __shared__ uint32_t s_h[kRadix];
+  const uint32_t tid = threadIdx.x, gt = blockIdx.x;
+  const uint32_t i = find_instance(ar.stile_prefix, ar.n, gt);
+  const MultiInst& d = ar.inst[i];
+  const uint32_t nops = multi_ops(in, d, i);
+  if (nops == 0 || nops > d.b) return;  // whole CTA: no batch, or refused
+  s_h[tid] = 0;
+  __syncthreads();
+  const uint32_t t0 = (gt - d.stile0) * kMultiSortTile;
+  const uint32_t m = (d.b - t0) < kMultiSortTile ? (d.b - t0) : kMultiSortTile;
+  const int shift = 32 - int(d.msd_bits);
+  bool bad_any = false;
+#pragma unroll 4
+  for (int j = 0; j < kMultiIPT; ++j) {
+    const uint32_t p = j * kThreads + tid;
+    if (p < m) {
+      bool bad;
+      const uint32_t kv = multi_load_key(in, d, nops, t0 + p, bad);
+      bad_any |= bad;
+      atomicAdd(&s_h[kv >> shift], 1u);
+    }
+  }
+  const int any_bad = __syncthreads_or(bad_any);
+  ar.tilecnt[uint64_t(gt) * 512 + tid] = s_h[tid];
+  if (any_bad && tid == 0) atomicOr(ar.badkey + i, 1u);
+}
+
+// Per instance (one CTA, thread = bucket): where each tile's run of each
+// bucket goes, relative to the instance's batch start.
+__global__ void __launch_bounds__(kThreads) mseg_offsets(MultiArena ar) {
+  __shared__ uint32_t s_scan[kWarps];
+  const uint32_t i = blockIdx.x, tid = threadIdx.x;
+  if (ar.k[i] < 0) return;
+  const MultiInst& d = ar.inst[i];
+  const uint32_t nbk = 1u << d.msd_bits;
+  const uint32_t ntiles = (d.b + kMultiSortTile - 1) / kMultiSortTile;
+  uint32_t* tc = ar.tilecnt + uint64_t(d.stile0) * 512;
+  uint32_t total = 0;
+  if (tid < nbk)
+    for (uint32_t t = 0; t < ntiles; ++t) total += tc[t * 512 + tid];
+  uint32_t all;
+  const uint32_t start = block_excl_scan<kThreads>(total, s_scan, all);
+  if (tid < nbk) {
+    uint32_t run = start;
+    for (uint32_t t = 0; t < ntiles; ++t) {
+      const uint32_t c = tc[t * 512 + tid];
+      tc[t * 512 + 256 + tid] = run;
+      run += c;
+    }
+    ar.bstart[d.bucket0 + tid] = start;
+    ar.bcnt[d.bucket0 + tid] = total;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) mseg_scatter(MultiArena ar, MultiBatch in) {
+  __shared__ __align__(16) uint32_t s_keys[kMultiSortTile];
+  __shared__ __align__(16) uint32_t s_vals[kMultiSortTile];
+  __shared__ uint32_t s_whist[kWarps][kRadix];
+  __shared__ uint32_t s_excl[kRadix], s_gbase[kRadix], s_scan[kWarps];
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5, gt = blockIdx.x;
+  const uint32_t i = find_instance(ar.stile_prefix, ar.n, gt);
+  if (ar.k[i] < 0) return;  // whole CTA
+  const MultiInst& d = ar.inst[i];
+  const uint32_t nops = multi_ops(in, d, i);
+  const uint32_t t0 = (gt - d.stile0) * kMultiSortTile;
+  const uint32_t m = (d.b - t0) < kMultiSortTile ? (d.b - t0) : kMultiSortTile;
+  const int shift = 32 - int(d.msd_bits);
+  const uint32_t base = warp * (32 * kMultiIPT);
+  uint32_t kv[kMultiIPT], v[kMultiIPT], rank[kMultiIPT];
+#pragma unroll
+  for (int j = 0; j < kMultiIPT; ++j) {
+    const uint32_t p = base + j * 32 + lane;
+    kv[j] = 0;
+    v[j] = 0;
+    if (p < m) multi_load(in, d, nops, t0 + p, kv[j], v[j]);
+  }
+  s_gbase[tid] = ar.tilecnt[uint64_t(gt) * 512 + 256 + tid];
+  rank_block<kThreads, kMultiIPT>(kv, m, base, shift, rank, s_whist, s_excl, s_scan, nullptr);
+#pragma unroll
+  for (int j = 0; j < kMultiIPT; ++j) {
+    const uint32_t p = base + j * 32 + lane;
+    if (p < m) {
+      const uint32_t dg = kv[j] >> shift;
+      const uint32_t pos = s_excl[dg] + s_whist[warp][dg] + rank[j];
+      s_keys[pos] = kv[j];
+      s_vals[pos] = v[j];
+    }
+  }
+  __syncthreads();
+  uint32_t* tk = ar.tkeys + d.boff;
+  uint32_t* tv = ar.tvals + d.boff;
+  for (uint32_t e = tid; e < m; e += kThreads) {
+    const uint32_t k = s_keys[e];
+    const uint32_t dg = k >> shift;
+    const uint32_t dst = s_gbase[dg] + (e - s_excl[dg]);
+    if (dst < d.b) {
+      tk[dst] = k;
+      tv[dst] = s_vals[e];
+    }
+  }
+}
+
+// One bucket of one instance per CTA: sorted on the bits below the top d
+// into level 0 (when the round's fold target is level 0) or the sorted-batch
+// buffer, with that run's prefix-index entries.
+__global__ void __launch_bounds__(kBucketThreads, 2) mseg_bucket(MultiArena ar) {
+  extern __shared__ __align__(16) uint32_t bsm[];
+  __shared__ uint32_t s_scan[kBucketWarps];
+  const uint32_t gb = blockIdx.x;
+  const uint32_t i = find_instance(ar.bucket_prefix, ar.n, gb);
+  const int k = ar.k[i];
+  if (k < 0) return;  // whole CTA
+  const MultiInst& d = ar.inst[i];
+  const uint32_t bucket = gb - d.bucket0;
+  const uint32_t start = ar.bstart[gb], m = ar.bcnt[gb];
+  uint32_t *ok, *ov, *of;
+  if (k == 0) {
+    ok = ar.keys + d.lvl_off[0];
+    ov = ar.vals + d.lvl_off[0];
+    of = ar.fence + d.lvl_fence[0];
+  } else {
+    ok = ar.bkeys + d.boff;
+    ov = ar.bvals + d.boff;
+    of = ar.fence + d.batch_fence;
+  }
+  const int fs = d.fshift0;
+  const int rest = 32 - int(d.msd_bits);              // bits below the bucket bits
+  const int npass = (rest + 7) / 8;
+  const uint32_t per = 1u << (rest - fs);             // bins per bucket
+  bucket_body(ar.tkeys + d.boff, ar.tvals + d.boff, ok, ov, start, m, npass, of, fs, bucket * per, per, bsm,
+              s_scan);
+  if (bucket == (1u << d.msd_bits) - 1 && threadIdx.x == 0) {
+    const uint32_t nb = fence_bins(fs);
+    of[nb] = d.b;
+    of[nb + 2] = 0u;
+    of[nb + 3] = nb - 1;
+  }
 }
 
 }  // namespace
@@ -646,6 +847,32 @@ cudaError_t check_keys_launch(const uint32_t* keys, uint64_t n, uint32_t* status
   if (blocks > 8 * 152) blocks = 8 * 152;
   count_launches(1);
   check_keys<<<unsigned(blocks), 256, 0, st>>>(keys, n, status);
+  return cudaGetLastError();
+}
+
+
+cudaError_t multi_sort_count_launch(const MultiArena& ar, const MultiBatch& in, cudaStream_t st) {
+  if (ar.total_stiles == 0) return cudaSuccess;
+  count_launches(1);
+  mseg_count<<<unsigned(ar.total_stiles), kThreads, 0, st>>>(ar, in);
+  return cudaGetLastError();
+}
+
+cudaError_t multi_sort_prepare() {
+  return cudaFuncSetAttribute(mseg_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBucketSmem));
+}
+
+cudaError_t multi_sort_launch(const MultiArena& ar, const MultiBatch& in, cudaStream_t st) {
+  cudaError_t e;
+  if (ar.total_stiles == 0) return cudaSuccess;
+  count_launches(1);
+  mseg_offsets<<<ar.n, kThreads, 0, st>>>(ar);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  count_launches(1);
+  mseg_scatter<<<unsigned(ar.total_stiles), kThreads, 0, st>>>(ar, in);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  count_launches(1);
+  mseg_bucket<<<unsigned(ar.total_buckets), kBucketThreads, kBucketSmem, st>>>(ar);
   return cudaGetLastError();
 }
 

@@ -31,7 +31,14 @@ LSM_OK, LSM_ERR_ARG, LSM_ERR_KEY_RANGE, LSM_ERR_FULL = 0, 1, 2, 3
 LSM_ERR_OOM, LSM_ERR_BUDGET, LSM_ERR_CAPACITY, LSM_ERR_CUDA, LSM_ERR_TIMEOUT = 4, 5, 6, 7, 8
 LSM_OPT_LOOKUP_MODE, LSM_OPT_DEVICE_ERROR, LSM_OPT_KERNEL_LAUNCHES = 1, 2, 3
 LOOKUP_AUTO, LOOKUP_DIRECT, LOOKUP_SORTED = 0, 1, 2
+LSM_MULTI_OPT_GRAPH, LSM_MULTI_OPT_GRAPH_KERNELS, LSM_MULTI_OPT_DEVICE_BYTES = 1, 2, 3
+MULTI_FLAG_BAD_KEY, MULTI_FLAG_ARG, MULTI_FLAG_FULL = 1, 8, 16
 PROF_GROUPS = ("sort", "partition", "merge", "lookup", "count", "emit", "cleanup")
+
+
+class MultiTuning(ctypes.Structure):
+    """lsm_multi_tuning: merge tile (1024 | 2048) and prefix-index bin_log2."""
+    _fields_ = [("tile", ctypes.c_uint32), ("bin_log2", ctypes.c_uint32)]
 
 
 class ProfileEntry(ctypes.Structure):
@@ -62,6 +69,19 @@ _SIGS = {
     "lsm_profile": ([_vp, _i32], _i32),
     "lsm_profile_read": ([_vp, ctypes.POINTER(ProfileEntry)], _i32),
     "lsm_sort_pairs_noalloc": ([_vp, _vp, _vp, _vp, _u64, _vp], _i32),
+    "lsm_multi_create": ([ctypes.POINTER(_vp), _u32, _vp, _u32, _vp, _i32], _i32),
+    "lsm_multi_destroy": ([_vp], None),
+    "lsm_multi_update": ([_vp, _vp, _vp, _vp, _vp, _vp], _i32),
+    "lsm_multi_lookup": ([_vp, _vp, _vp, _u64, _vp, _vp, _vp], _i32),
+    "lsm_multi_round": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp], _i32),
+    "lsm_multi_sync": ([_vp, _vp, _vp], _i32),
+    "lsm_multi_stats": ([_vp, _u32, ctypes.POINTER(_u64), ctypes.POINTER(_u32), ctypes.POINTER(_u64)], _i32),
+    "lsm_multi_layout": ([_vp, _u32, ctypes.POINTER(_u64), ctypes.POINTER(_u32), ctypes.POINTER(ctypes.c_int32),
+                          ctypes.POINTER(_u32)], _i32),
+    "lsm_multi_dump_levels": ([_vp, _u32, _vp, _vp], _i32),
+    "lsm_multi_reset": ([_vp, _vp], _i32),
+    "lsm_multi_set_option": ([_vp, _i32, _i64], _i32),
+    "lsm_multi_get_option": ([_vp, _i32, ctypes.POINTER(_i64)], _i32),
 }
 SORT_NOALLOC_MAX_PAIRS = 1 << 20
 for _name, (_args, _res) in _SIGS.items():
@@ -186,6 +206,77 @@ def lsm_profile_read(h):
     _check(_lib.lsm_profile_read(h, arr), "lsm_profile_read")
     return {n: dict(launches=int(e.launches), ms=float(e.ms), bytes=float(e.bytes))
             for n, e in zip(PROF_GROUPS, arr)}
+
+
+# batched form ----------------------------------------------------------
+def lsm_multi_create(b_list, max_batches, tuning=None, device=0):
+    """b_list: batch size per instance; tuning: None or [(tile, bin_log2)] per instance."""
+    n = len(b_list)
+    bs = (_u32 * n)(*[int(x) for x in b_list])
+    tun = None
+    if tuning is not None:
+        tun = (MultiTuning * n)(*[MultiTuning(int(t), int(e)) for t, e in tuning])
+    h = _vp()
+    _check(_lib.lsm_multi_create(ctypes.byref(h), n, bs, max_batches, tun, device), "lsm_multi_create")
+    return h.value
+
+
+def lsm_multi_destroy(h):
+    _lib.lsm_multi_destroy(h)
+
+
+def lsm_multi_update(h, d_keys, d_vals, d_is_delete, d_counts, stream=None):
+    return _check(_lib.lsm_multi_update(h, d_keys, d_vals, d_is_delete, d_counts, stream), "lsm_multi_update")
+
+
+def lsm_multi_lookup(h, d_q, d_qoff, nq, d_val, d_found, stream=None):
+    return _check(_lib.lsm_multi_lookup(h, d_q, d_qoff, nq, d_val, d_found, stream), "lsm_multi_lookup")
+
+
+def lsm_multi_round(h, d_keys, d_vals, d_is_delete, d_counts, d_q, d_qoff, nq, d_val, d_found, stream=None):
+    return _check(_lib.lsm_multi_round(h, d_keys, d_vals, d_is_delete, d_counts, d_q, d_qoff, nq, d_val,
+                                       d_found, stream), "lsm_multi_round")
+
+
+def lsm_multi_sync(h, stream=None, n_flags=0):
+    """Returns (status, per-instance flags as a list or None); never raises on
+    the round errors it reports."""
+    flags = (_u32 * n_flags)() if n_flags else None
+    s = _lib.lsm_multi_sync(h, stream, flags)
+    if s in (LSM_ERR_CUDA, LSM_ERR_OOM):
+        raise LSMError(s, "lsm_multi_sync")
+    return s, (list(flags) if flags is not None else None)
+
+
+def lsm_multi_stats(h, i):
+    r, b, res = _u64(), _u32(), _u64()
+    _check(_lib.lsm_multi_stats(h, i, ctypes.byref(r), ctypes.byref(b), ctypes.byref(res)), "lsm_multi_stats")
+    return dict(r=r.value, b=b.value, resident=res.value)
+
+
+def lsm_multi_layout(h, i):
+    off, tile, fs, lv = _u64(), _u32(), ctypes.c_int32(), _u32()
+    _check(_lib.lsm_multi_layout(h, i, ctypes.byref(off), ctypes.byref(tile), ctypes.byref(fs), ctypes.byref(lv)),
+           "lsm_multi_layout")
+    return dict(in_off=off.value, tile=tile.value, fence_shift0=fs.value, levels=lv.value)
+
+
+def lsm_multi_dump_levels(h, i, h_keys, h_vals):
+    return _check(_lib.lsm_multi_dump_levels(h, i, h_keys, h_vals), "lsm_multi_dump_levels")
+
+
+def lsm_multi_reset(h, stream=None):
+    return _check(_lib.lsm_multi_reset(h, stream), "lsm_multi_reset")
+
+
+def lsm_multi_set_option(h, opt, value):
+    return _check(_lib.lsm_multi_set_option(h, opt, value), "lsm_multi_set_option")
+
+
+def lsm_multi_get_option(h, opt):
+    v = _i64()
+    _check(_lib.lsm_multi_get_option(h, opt, ctypes.byref(v)), "lsm_multi_get_option")
+    return v.value
 
 
 def kernel_launches():
@@ -343,3 +434,76 @@ class LSM:
 
     def device_errors(self):
         return lsm_get_option(self.h, LSM_OPT_DEVICE_ERROR)
+
+
+class MultiLSM:
+    """n independent GPU LSMs with batch sizes b_list, advanced a round at a
+    time (lsm_multi_*).  Batches of a round are laid out back to back in
+    instance order (instance i at offset sum(b_list[:i]))."""
+
+    def __init__(self, b_list, max_batches, tuning=None, device=0):
+        import numpy as np
+        self.device = device
+        self.b = np.asarray(b_list, dtype=np.int64)
+        self.n = len(b_list)
+        self.in_off = np.concatenate([[0], np.cumsum(self.b)])
+        self.h = lsm_multi_create(b_list, max_batches, tuning, device)
+
+    def close(self):
+        if self.h:
+            lsm_multi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update(self, keys, vals, is_delete=None, counts=None):
+        """keys/vals: sum(b) entries (instance i's ops first in its slot);
+        counts: ops per instance (None = full batches).  Asynchronous; call
+        sync() for errors."""
+        k, v = as_device_u32(keys, self.device), as_device_u32(vals, self.device)
+        d = None if is_delete is None else as_device_u8(is_delete, self.device)
+        c = None if counts is None else as_device_u32(counts, self.device)
+        self._keep = (k, v, d, c)
+        lsm_multi_update(self.h, _ptr(k), _ptr(v), _ptr(d), _ptr(c), _stream(self.device))
+
+    def lookup(self, q, qoff):
+        torch = _torch()
+        qd = as_device_u32(q, self.device)
+        off = torch.as_tensor(qoff, dtype=torch.int64).to(self.device)
+        n = qd.numel()
+        val = torch.empty(n, dtype=torch.int32, device=self.device)
+        found = torch.empty(n, dtype=torch.uint8, device=self.device)
+        lsm_multi_lookup(self.h, _ptr(qd), _ptr(off), n, _ptr(val), _ptr(found), _stream(self.device))
+        return val, found
+
+    def sync(self):
+        return lsm_multi_sync(self.h, _stream(self.device), self.n)
+
+    def stats(self, i):
+        return lsm_multi_stats(self.h, i)
+
+    def levels(self, i):
+        """Full levels of instance i: {l: (key variables, values)} as uint32."""
+        import numpy as np
+        st = self.stats(i)
+        r, b = st["r"], st["b"]
+        hk = np.zeros(max(1, r * b), np.uint32)
+        hv = np.zeros(max(1, r * b), np.uint32)
+        lsm_multi_dump_levels(self.h, i, hk.ctypes.data, hv.ctypes.data)
+        out, pos = {}, 0
+        for l in range(32):
+            if (r >> l) & 1:
+                n = b << l
+                out[l] = (hk[pos:pos + n].copy(), hv[pos:pos + n].copy())
+                pos += n
+        return out
+
+    def reset(self):
+        lsm_multi_reset(self.h, _stream(self.device))
+
+    def set_graph(self, on):
+        lsm_multi_set_option(self.h, LSM_MULTI_OPT_GRAPH, 1 if on else 0)

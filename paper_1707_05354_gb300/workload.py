@@ -185,3 +185,86 @@ def sweep_updates(seed, b, total, delete_frac, dist):
 def sweep_width(expected_result, n_estimate, key_space=SWEEP_KEY_SPACE):
     """Query width giving `expected_result` hits at uniform density n/key_space."""
     return max(1, int(round(expected_result * key_space / max(1, n_estimate))))
+
+
+# --------------------------------------------------------------------------
+# Configuration "batched": many dictionaries with uneven batch sizes.
+# --------------------------------------------------------------------------
+BATCHED_SEED = 1707053504
+
+
+def batched_sizes(seed=BATCHED_SEED, n_inst=256, lo_log2=10, hi_log2=18):
+    """Batch size per instance: round(2^U[lo, hi]) (log-uniform integers)."""
+    g = rng(seed, _STREAM_MISC, 0)
+    return np.rint(np.exp2(g.uniform(lo_log2, hi_log2, size=n_inst))).astype(np.int64)
+
+
+class BatchedWorkload:
+    """Configuration 4: rounds of one update batch and b_i lookups per
+    instance.  Round 0 inserts b_i fresh keys; later rounds delete
+    round(delete_frac * b_i) keys drawn uniformly from the instance's earlier
+    inserts and insert fresh keys for the rest, shuffled.  Keys uniform in
+    [0, 2^31 - 1), values uniform u32.  Lookups: half drawn from the
+    instance's inserts so far, half uniform.
+
+    Arrays of a round hold instance i's entries at [off[i], off[i] + b_i)."""
+
+    def __init__(self, seed=BATCHED_SEED, n_inst=256, rounds=32, delete_frac=0.2, lo_log2=10, hi_log2=18,
+                 sizes=None):
+        self.seed = seed
+        self.sizes = (np.asarray(sizes, np.int64) if sizes is not None
+                      else batched_sizes(seed, n_inst, lo_log2, hi_log2))
+        self.n = len(self.sizes)
+        self.rounds = rounds
+        self.delete_frac = delete_frac
+        self.off = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        self.total = int(self.off[-1])
+        self._hist = [[] for _ in range(self.n)]
+        self._hlen = [[] for _ in range(self.n)]
+
+    def round(self, t):
+        """(keys, vals, is_delete, queries) of round t; rounds must be drawn
+        in order 0, 1, 2, ... (deletes sample the earlier rounds)."""
+        keys = np.empty(self.total, np.uint32)
+        vals = np.empty(self.total, np.uint32)
+        dele = np.empty(self.total, np.uint8)
+        q = np.empty(self.total, np.uint32)
+        for i in range(self.n):
+            b = int(self.sizes[i])
+            g = rng(self.seed, _STREAM_UPDATE, t * 65536 + i)
+            n_del = 0 if t == 0 else int(round(b * self.delete_frac))
+            n_ins = b - n_del
+            ins_k = u32(g, n_ins, 0, KEY_LIMIT)
+            ins_v = u32(g, n_ins)
+            if n_del:
+                cum = np.cumsum(self._hlen[i])
+                idx = g.integers(0, int(cum[-1]), size=n_del)
+                which = np.searchsorted(cum, idx, side="right")
+                start = np.concatenate([[0], cum[:-1]])
+                del_k = np.empty(n_del, np.uint32)
+                for w in np.unique(which):
+                    sel = which == w
+                    del_k[sel] = self._hist[i][w][idx[sel] - start[w]]
+            else:
+                del_k = np.zeros(0, np.uint32)
+            kk = np.concatenate([ins_k, del_k])
+            vv = np.concatenate([ins_v, np.zeros(n_del, np.uint32)])
+            dd = np.concatenate([np.zeros(n_ins, np.uint8), np.ones(n_del, np.uint8)])
+            perm = g.permutation(b)
+            s = slice(int(self.off[i]), int(self.off[i]) + b)
+            keys[s], vals[s], dele[s] = kk[perm], vv[perm], dd[perm]
+            self._hist[i].append(ins_k)
+            self._hlen[i].append(n_ins)
+            gq = rng(self.seed, _STREAM_QUERY, t * 65536 + i)
+            half = b // 2
+            cum = np.cumsum(self._hlen[i])
+            idx = gq.integers(0, int(cum[-1]), size=half)
+            which = np.searchsorted(cum, idx, side="right")
+            start = np.concatenate([[0], cum[:-1]])
+            hits = np.empty(half, np.uint32)
+            for w in np.unique(which):
+                sel = which == w
+                hits[sel] = self._hist[i][w][idx[sel] - start[w]]
+            qq = np.concatenate([hits, u32(gq, b - half, 0, KEY_LIMIT)])
+            q[s] = qq[gq.permutation(b)]
+        return keys, vals, dele, q
