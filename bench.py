@@ -241,6 +241,7 @@ def run_gpu(args):
         ev[0].record(st)
         for t in range(nb):
             G.lsm_insert_batch(h, kp + 4 * t * b, vp + 4 * t * b, b, sp)
+        G.lsm_stream_wait(h, sp)   # the last folds run on the handle's internal stream
         ev[1].record(st)
         G.lsm_lookup(h, d_q.data_ptr(), nq, o_val.data_ptr(), o_found.data_ptr(), sp)
         ev[2].record(st)

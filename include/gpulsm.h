@@ -16,6 +16,14 @@
  *    stream).  Work is enqueued on it; outputs are valid once the stream has
  *    reached that point.  Calls that must read a device value on the host
  *    (documented below) synchronise with the stream before returning.
+ *  - Update calls sort each batch on `stream` and fold it into the levels on
+ *    an internal stream of the handle, so that the next batch's sort can
+ *    overlap the fold.  Once `stream` has passed an update call, the call's
+ *    inputs have been consumed; the fold may still be running.  Every later
+ *    call that reads or rewrites the levels (lookup, count, range, cleanup,
+ *    dump) first orders its stream after the handle's folds, so results are
+ *    always those of every update issued before; lsm_stream_wait orders any
+ *    other work (a timing event, a copy) the same way.
  *  - Keys are 32-bit unsigned integers; user keys must be < 2^31 - 1.  The key
  *    2^31 - 1 is reserved for the placebo tombstones written by cleanup (§IV-E).
  *    Values are arbitrary 32-bit unsigned integers.
@@ -85,8 +93,9 @@ void lsm_destroy(lsm_t* h);
  *                   batches of b ops, a final short batch padded with copies of
  *                   its last op (§IV-A).  n = 0 is a no-op.
  * Each batch is sorted on the full key variable and cascade-merged into level
- * ffz(r), r the number of resident batches.  Keys are checked on the device;
- * the call waits for that check (not for the merge) and returns
+ * ffz(r), r the number of resident batches (the merge on the handle's
+ * internal stream; see the conventions above).  Keys are checked on the
+ * device; the call waits for that check (not for the merge) and returns
  * LSM_ERR_KEY_RANGE with nothing applied if any key is >= 2^31 - 1.
  * Errors: LSM_ERR_ARG, LSM_ERR_KEY_RANGE, LSM_ERR_FULL, LSM_ERR_CUDA.
  */
@@ -108,6 +117,19 @@ lsm_status lsm_delete_batch(lsm_t* h, const uint32_t* d_keys, uint64_t n, void* 
  */
 lsm_status lsm_update_batch(lsm_t* h, const uint32_t* d_keys, const uint32_t* d_vals,
                             const uint8_t* d_is_delete, uint64_t n, void* stream);
+
+/*
+ * lsm_update_batch_ordered - one mixed batch of n <= b ops that take effect
+ * in input order: the last op on a key decides, so a delete followed by an
+ * insert of the same key leaves it inserted (applying the ops one by one).
+ * Not in the paper, whose rule 6 (§III-A) lets a delete win inside a batch;
+ * this is how the serving engine coalesces requests into one batch.  Before
+ * the usual sort, every op on a key is replaced on the device by a copy of
+ * the last op on that key.  d_vals may be NULL (values 0), d_is_delete NULL
+ * (all inserts).  Same checks, errors and asynchrony as lsm_update_batch.
+ */
+lsm_status lsm_update_batch_ordered(lsm_t* h, const uint32_t* d_keys, const uint32_t* d_vals,
+                                    const uint8_t* d_is_delete, uint64_t n, void* stream);
 
 /*
  * lsm_lookup - point queries (§III-D, §IV-B, Fig. 2(b)).
@@ -180,9 +202,17 @@ lsm_status lsm_dump_levels(const lsm_t* h, uint32_t* h_keys, uint32_t* h_vals, v
 
 /*
  * lsm_reset - drop every element (r = 0).  Host-side only, no device work; the
- * level memory is reused by later batches.  Waits for nothing.
+ * level memory is reused by later batches (after any fold still in flight,
+ * which the handle's stream order guarantees).  Waits for nothing.
  */
 lsm_status lsm_reset(lsm_t* h);
+
+/*
+ * lsm_stream_wait - make `stream` wait (on the device, without blocking the
+ * host) until every fold the handle has enqueued so far has finished.  Not in
+ * the paper: it exposes the library's two-stream pipelining of updates.
+ */
+lsm_status lsm_stream_wait(lsm_t* h, void* stream);
 
 /* Number of elements in the level array (all allocated levels, with padding). */
 uint64_t lsm_capacity(const lsm_t* h);

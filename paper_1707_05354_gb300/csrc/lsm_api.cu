@@ -1,9 +1,17 @@
 // Host orchestrator and C ABI of the GPU LSM (include/gpulsm.h).
 //
 // The host owns the binary counter r (§III-B): level i is full iff bit i of r
-// is set, and an update batch lands in level ffz(r).  All device work is
-// enqueued on the caller's stream; the host waits only where the interface
-// says so (the key check of an update, the totals of range and cleanup).
+// is set, and an update batch lands in level ffz(r).  The host waits only
+// where the interface says so (the key check of an update, the totals of
+// range and cleanup).
+//
+// Two streams.  A batch is sorted on the caller's stream into one of three
+// sorted-batch buffers; its fold into level k runs on the handle's internal
+// stream, so the next batch's sort overlaps it.  A batch that lands in level
+// 0 (k = 0) is not copied: its buffer becomes level 0 until the next fold
+// consumes it.  Every call that reads or rewrites the levels first makes the
+// caller's stream wait for the internal one; a buffer is reused only after
+// the fold that read it (an event per buffer).
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
@@ -11,7 +19,7 @@
 #include <vector>
 
 #include "gpulsm.h"
-#include "lsm_kernels.h"
+#include "lsm_internal.h"
 
 using namespace gpulsm;
 
@@ -30,16 +38,24 @@ struct lsm_t {
   uint64_t capacity = 0;
   uint32_t* d_keys = nullptr;
   uint32_t* d_vals = nullptr;
-  uint32_t* d_bk = nullptr;  // sorted batch (b + slack)
+  uint32_t* d_bk = nullptr;  // kBatchBufs sorted-batch buffers of bpad elements
   uint32_t* d_bv = nullptr;
+  uint64_t bpad = 0;
+  int l0_buf = -1;           // the buffer holding level 0, or -1 (level 0 in the level array)
+  int last_buf = 0;          // buffer of the latest batch
+  cudaStream_t side = nullptr;           // folds
+  cudaEvent_t ev_sorted = nullptr;       // caller's stream, after a batch's sort
+  cudaEvent_t ev_side = nullptr;         // internal stream, after its latest work
+  cudaEvent_t ev_free[3] = {};           // internal stream, after the fold that read buffer j
+  bool side_pending = false;
   uint32_t* d_tk = nullptr;  // sort ping-pong (b + slack)
   uint32_t* d_tv = nullptr;
   SortWorkspace sws{};
   uint32_t* d_part = nullptr;
   uint64_t part_words = 0;
   uint32_t* d_fence = nullptr;  // prefix index per level (L tables) + the sorted batch's
-  uint64_t fence_off[kMaxLevels + 2] = {};
-  int fshift[kMaxLevels + 1] = {};  // per level; [L] = the batch
+  uint64_t fence_off[kMaxLevels + 4] = {};  // L levels, then the batch buffers
+  int fshift[kMaxLevels + 4] = {};  // per level; [L ..] = the batch buffers
   uint32_t* d_misc = nullptr;  // [0] sticky errors [1] key check [2] tile ctr [3] tile ctr
   uint64_t* d_u64 = nullptr;   // [0] cleanup count
   uint32_t* h_status = nullptr;  // mapped pinned word: key check of the current batch
@@ -117,6 +133,11 @@ void free_all(lsm_t* h) {
                    h->d_q, h->qsws.lookback, h->qsws.tilecnt, h->d_qctl};
   for (void* p : dptrs)
     if (p) cudaFree(p);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_sorted) cudaEventDestroy(h->ev_sorted);
+  if (h->ev_side) cudaEventDestroy(h->ev_side);
+  for (cudaEvent_t e : h->ev_free)
+    if (e) cudaEventDestroy(e);
   if (h->h_status) cudaFreeHost(h->h_status);
   if (h->h_u64) cudaFreeHost(h->h_u64);
   if (h->ev) cudaEventDestroy(h->ev);
@@ -156,10 +177,27 @@ struct ProfScope {
   }
 };
 
-uint32_t* level_keys(lsm_t* h, int i) { return h->d_keys + h->level_off[i]; }
-uint32_t* level_vals(lsm_t* h, int i) { return h->d_vals + h->level_off[i]; }
-uint32_t* level_fence(lsm_t* h, int i) { return h->d_fence + h->fence_off[i]; }
-uint32_t* batch_fence(lsm_t* h) { return h->d_fence + h->fence_off[h->L]; }
+constexpr int kBatchBufs = 3;
+
+uint32_t* buf_keys(const lsm_t* h, int j) { return h->d_bk + uint64_t(j) * h->bpad; }
+uint32_t* buf_vals(const lsm_t* h, int j) { return h->d_bv + uint64_t(j) * h->bpad; }
+uint32_t* buf_fence(const lsm_t* h, int j) { return h->d_fence + h->fence_off[h->L + j]; }
+// Level i's storage; level 0 may be a sorted-batch buffer.
+uint32_t* level_keys(const lsm_t* h, int i) {
+  return (i == 0 && h->l0_buf >= 0) ? buf_keys(h, h->l0_buf) : h->d_keys + h->level_off[i];
+}
+uint32_t* level_vals(const lsm_t* h, int i) {
+  return (i == 0 && h->l0_buf >= 0) ? buf_vals(h, h->l0_buf) : h->d_vals + h->level_off[i];
+}
+uint32_t* level_fence(const lsm_t* h, int i) {
+  return (i == 0 && h->l0_buf >= 0) ? buf_fence(h, h->l0_buf) : h->d_fence + h->fence_off[i];
+}
+
+// Orders `st` after the folds in flight on the internal stream.
+cudaError_t join_side(const lsm_t* h, cudaStream_t st) {
+  if (!h->side_pending) return cudaSuccess;
+  return cudaStreamWaitEvent(st, h->ev_side, 0);
+}
 
 LevelSet full_levels(lsm_t* h) {
   LevelSet ls{};
@@ -189,13 +227,59 @@ cudaError_t ensure_q(lsm_t* h, size_t bytes) {
   return e;
 }
 
+// Stable sort of (keys[i], i) for i < n into the query scratch (grown on
+// demand, `extra` more words kept after the four sort arrays); returns the
+// sorted keys and positions.
+cudaError_t sort_positions(lsm_t* h, const uint32_t* keys, uint64_t n, uint64_t extra, cudaStream_t st,
+                           uint32_t** sk, uint32_t** sv) {
+  const uint64_t tiles = (n + kSortTile - 1) / kSortTile;
+  const uint64_t npad = round_up(n, kLevelAlign) + kSlack;
+  cudaError_t e;
+  if ((e = ensure_q(h, (4 * npad + extra) * sizeof(uint32_t))) != cudaSuccess) return e;
+  if (!h->qsws.lookback || h->qsws.max_tiles < tiles) {
+    if (h->qsws.lookback) cudaFree(h->qsws.lookback);
+    h->qsws.lookback = nullptr;
+    if ((e = dalloc(&h->qsws.lookback, uint64_t(kSortPasses) * tiles * 256)) != cudaSuccess) return e;
+    if ((e = cudaMemset(h->qsws.lookback, 0, sizeof(uint64_t) * kSortPasses * tiles * 256)) != cudaSuccess)
+      return e;
+    h->qsws.max_tiles = uint32_t(tiles);
+    h->qsws.epoch = 0;
+  }
+  if (!h->d_qctl) {
+    if ((e = dalloc(&h->d_qctl, 2 * kSortCtlWords)) != cudaSuccess) return e;
+    if ((e = cudaMemset(h->d_qctl, 0, sizeof(uint32_t) * 2 * kSortCtlWords)) != cudaSuccess) return e;
+    h->qsws.flip = 0;
+  }
+  if (!h->qsws.tilecnt && (e = dalloc(&h->qsws.tilecnt, kMsdTileWords)) != cudaSuccess) return e;
+  h->qsws.ctl = h->d_qctl;
+  h->qsws.sticky = h->d_misc + kMiscSticky;
+  uint32_t* base = reinterpret_cast<uint32_t*>(h->d_q);
+  SortArgs a{};
+  a.mode = kSortQueries;
+  a.in_keys = keys;
+  a.n_in = n;
+  a.n = uint32_t(n);
+  a.out_keys = base;
+  a.out_vals = base + npad;
+  a.tmp_keys = base + 2 * npad;
+  a.tmp_vals = base + 3 * npad;
+  *sk = a.out_keys;
+  *sv = a.out_vals;
+  return sort_launch(a, h->qsws, st, nullptr, nullptr);
+}
+
 // One batch of n_in <= b ops into level ffz(r).  With `checked`, waits for
-// the device key check of this batch and leaves r alone if it failed (the
-// batch only ever wrote the empty level ffz(r) and scratch).
+// the device key check of this batch and leaves the dictionary alone if it
+// failed (the batch only wrote a free sorted-batch buffer).
 lsm_status apply_batch(lsm_t* h, int mode, const uint32_t* keys, const uint32_t* vals, const uint8_t* del,
                        uint64_t n_in, cudaStream_t st, bool checked) {
   const int k = ffz(h->r);
   if (k >= int(h->L)) return LSM_ERR_FULL;
+  // next buffer in rotation that does not hold level 0; wait for the fold
+  // that last read it
+  int j = (h->last_buf + 1) % kBatchBufs;
+  if (j == h->l0_buf) j = (j + 1) % kBatchBufs;
+  LSM_TRY(cudaStreamWaitEvent(st, h->ev_free[j], 0));
   SortArgs a{};
   a.mode = mode;
   a.in_keys = keys;
@@ -203,51 +287,67 @@ lsm_status apply_batch(lsm_t* h, int mode, const uint32_t* keys, const uint32_t*
   a.in_del = del;
   a.n_in = n_in;
   a.n = h->b;
-  a.out_keys = k == 0 ? level_keys(h, 0) : h->d_bk;
-  a.out_vals = k == 0 ? level_vals(h, 0) : h->d_bv;
+  a.out_keys = buf_keys(h, j);
+  a.out_vals = buf_vals(h, j);
   a.tmp_keys = h->d_tk;
   a.tmp_vals = h->d_tv;
-  a.fence = k == 0 ? level_fence(h, 0) : batch_fence(h);
-  a.fshift = k == 0 ? h->fshift[0] : h->fshift[h->L];
+  a.fence = buf_fence(h, j);
+  a.fshift = h->fshift[0];
   {
     ProfScope ps(h, LSM_PROF_SORT, 16.0 * h->b, st);
     if (checked) *reinterpret_cast<volatile uint32_t*>(h->h_status) = 0u;
     LSM_TRY(sort_launch(a, h->sws, st, checked ? h->d_status_map : nullptr, h->ev));
   }
-  if (k > 0) {
-    FoldArgs f{};
-    f.src.count = k + 1;
-    f.src.keys[0] = h->d_bk;
-    f.src.vals[0] = h->d_bv;
-    f.src.fence[0] = batch_fence(h);
-    f.src.fshift[0] = h->fshift[h->L];
-    f.src.n[0] = h->b;
-    for (int i = 0; i < k; ++i) {
-      f.src.keys[i + 1] = level_keys(h, i);
-      f.src.vals[i + 1] = level_vals(h, i);
-      f.src.fence[i + 1] = level_fence(h, i);
-      f.src.fshift[i + 1] = h->fshift[i];
-      f.src.n[i + 1] = uint32_t(uint64_t(h->b) << i);
-    }
-    f.total = uint64_t(h->b) << k;
-    f.out_keys = level_keys(h, k);
-    f.out_vals = level_vals(h, k);
-    f.out_fence = level_fence(h, k);
-    f.out_fshift = h->fshift[k];
-    f.part = h->d_part;
-    f.status = h->d_misc + kMiscSticky;
-    f.cleanup = false;
-    {
-      ProfScope ps(h, LSM_PROF_PARTITION, 0.0, st);
-      LSM_TRY(fold_partition_launch(f, st));
-    }
-    ProfScope ps(h, LSM_PROF_MERGE, 16.0 * double(f.total), st);
-    LSM_TRY(fold_merge_launch(f, st));
-  }
   if (checked) {
     LSM_TRY(cudaEventSynchronize(h->ev));
     if (*reinterpret_cast<volatile uint32_t*>(h->h_status) & kErrBadKey) return LSM_ERR_KEY_RANGE;
   }
+  h->last_buf = j;
+  if (k == 0) {
+    h->l0_buf = j;  // the sorted batch is level 0
+    h->r += 1;
+    return LSM_OK;
+  }
+  LSM_TRY(cudaEventRecord(h->ev_sorted, st));
+  cudaStream_t side = h->side;
+  LSM_TRY(cudaStreamWaitEvent(side, h->ev_sorted, 0));
+  FoldArgs f{};
+  f.src.count = k + 1;
+  f.src.keys[0] = buf_keys(h, j);
+  f.src.vals[0] = buf_vals(h, j);
+  f.src.fence[0] = buf_fence(h, j);
+  f.src.fshift[0] = h->fshift[0];
+  f.src.n[0] = h->b;
+  for (int i = 0; i < k; ++i) {
+    f.src.keys[i + 1] = level_keys(h, i);
+    f.src.vals[i + 1] = level_vals(h, i);
+    f.src.fence[i + 1] = level_fence(h, i);
+    f.src.fshift[i + 1] = h->fshift[i];
+    f.src.n[i + 1] = uint32_t(uint64_t(h->b) << i);
+  }
+  f.total = uint64_t(h->b) << k;
+  f.out_keys = h->d_keys + h->level_off[k];
+  f.out_vals = h->d_vals + h->level_off[k];
+  f.out_fence = h->d_fence + h->fence_off[k];
+  f.out_fshift = h->fshift[k];
+  f.part = h->d_part;
+  f.status = h->d_misc + kMiscSticky;
+  f.cleanup = false;
+  {
+    ProfScope ps(h, LSM_PROF_PARTITION, 0.0, side);
+    LSM_TRY(fold_partition_launch(f, side));
+  }
+  {
+    ProfScope ps(h, LSM_PROF_MERGE, 16.0 * double(f.total), side);
+    LSM_TRY(fold_merge_launch(f, side));
+  }
+  LSM_TRY(cudaEventRecord(h->ev_free[j], side));
+  if (h->l0_buf >= 0) {
+    LSM_TRY(cudaEventRecord(h->ev_free[h->l0_buf], side));
+    h->l0_buf = -1;  // level 0 was consumed
+  }
+  LSM_TRY(cudaEventRecord(h->ev_side, side));
+  h->side_pending = true;
   h->r += 1;
   return LSM_OK;
 }
@@ -279,6 +379,40 @@ lsm_status apply_call(lsm_t* h, int mode, const uint32_t* keys, const uint32_t* 
 }
 
 }  // namespace
+
+// ------------------------------------------------ hooks for the serving engine
+namespace gpulsm {
+
+LevelSet dict_levels(lsm_t* h) { return full_levels(h); }
+
+cudaError_t dict_join(lsm_t* h, cudaStream_t st) { return join_side(h, st); }
+
+lsm_status dict_update_ordered(lsm_t* h, const uint32_t* keys, const uint32_t* vals, const uint8_t* del,
+                               uint64_t n, cudaStream_t st, bool checked) {
+  if (n == 0) return LSM_OK;
+  const uint64_t npad = round_up(n, kLevelAlign) + kSlack;
+  uint32_t* sk = nullptr;
+  uint32_t* sv = nullptr;
+  LSM_TRY(sort_positions(h, keys, n, 3 * npad, st, &sk, &sv));
+  uint32_t* rk = reinterpret_cast<uint32_t*>(h->d_q) + 4 * npad;
+  uint32_t* rv = rk + npad;
+  uint8_t* rd = reinterpret_cast<uint8_t*>(rv + npad);
+  LSM_TRY(resolve_last_launch(sk, sv, uint32_t(n), keys, vals, del, rk, rv, rd, st));
+  return apply_batch(h, kSortUpdate, rk, rv, rd, n, st, checked);
+}
+
+cudaError_t dict_record_applied(lsm_t* h, cudaEvent_t ev, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = cudaEventRecord(h->ev_sorted, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(h->side, h->ev_sorted, 0)) != cudaSuccess) return e;
+  return cudaEventRecord(ev, h->side);
+}
+
+uint64_t dict_r(const lsm_t* h) { return h->r; }
+uint32_t dict_L(const lsm_t* h) { return h->L; }
+uint32_t* dict_status_word(lsm_t* h) { return h->d_misc + kMiscSticky; }
+
+}  // namespace gpulsm
 
 extern "C" {
 
@@ -321,8 +455,9 @@ lsm_status lsm_create(lsm_t** out, uint32_t b, uint64_t max_elements, int device
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = dalloc(&h->d_keys, h->capacity + kSlack);
   if (e == cudaSuccess) e = dalloc(&h->d_vals, h->capacity + kSlack);
-  if (e == cudaSuccess) e = dalloc(&h->d_bk, bpad);
-  if (e == cudaSuccess) e = dalloc(&h->d_bv, bpad);
+  h->bpad = bpad;
+  if (e == cudaSuccess) e = dalloc(&h->d_bk, kBatchBufs * bpad);
+  if (e == cudaSuccess) e = dalloc(&h->d_bv, kBatchBufs * bpad);
   if (e == cudaSuccess) e = dalloc(&h->d_tk, bpad);
   if (e == cudaSuccess) e = dalloc(&h->d_tv, bpad);
   if (e == cudaSuccess) e = dalloc(&h->sws.ctl, 2 * kSortCtlWords);
@@ -330,11 +465,11 @@ lsm_status lsm_create(lsm_t** out, uint32_t b, uint64_t max_elements, int device
   if (e == cudaSuccess) e = dalloc(&h->sws.lookback, uint64_t(kSortPasses) * sort_tiles * 256);
   if (e == cudaSuccess && b <= kMsdMaxN) e = dalloc(&h->sws.tilecnt, kMsdTileWords);
   if (e == cudaSuccess) e = dalloc(&h->d_part, h->part_words);
-  for (uint32_t i = 0; i <= L; ++i) {
+  for (uint32_t i = 0; i < L + kBatchBufs; ++i) {
     h->fshift[i] = fence_shift_for(i < L ? (uint64_t(b) << i) : uint64_t(b));
     h->fence_off[i + 1] = h->fence_off[i] + round_up(fence_words(h->fshift[i]), 64);
   }
-  if (e == cudaSuccess) e = dalloc(&h->d_fence, h->fence_off[L + 1]);
+  if (e == cudaSuccess) e = dalloc(&h->d_fence, h->fence_off[L + kBatchBufs]);
   if (e == cudaSuccess) e = dalloc(&h->d_misc, kMiscWords);
   if (e == cudaSuccess) e = dalloc(&h->d_u64, 8);
   if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&h->h_status), 64, cudaHostAllocMapped);
@@ -343,8 +478,13 @@ lsm_status lsm_create(lsm_t** out, uint32_t b, uint64_t max_elements, int device
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemset(h->d_keys, 0, sizeof(uint32_t) * (h->capacity + kSlack));
   if (e == cudaSuccess) e = cudaMemset(h->d_vals, 0, sizeof(uint32_t) * (h->capacity + kSlack));
-  if (e == cudaSuccess) e = cudaMemset(h->d_bk, 0, sizeof(uint32_t) * bpad);
-  if (e == cudaSuccess) e = cudaMemset(h->d_bv, 0, sizeof(uint32_t) * bpad);
+  if (e == cudaSuccess) e = cudaMemset(h->d_bk, 0, sizeof(uint32_t) * kBatchBufs * bpad);
+  if (e == cudaSuccess) e = cudaMemset(h->d_bv, 0, sizeof(uint32_t) * kBatchBufs * bpad);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_sorted, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_side, cudaEventDisableTiming);
+  for (int j = 0; j < kBatchBufs; ++j)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_free[j], cudaEventDisableTiming);
   if (e == cudaSuccess)
     e = cudaMemset(h->sws.lookback, 0, sizeof(uint64_t) * kSortPasses * uint64_t(sort_tiles) * 256);
   if (e == cudaSuccess) e = cudaMemset(h->d_misc, 0, sizeof(uint32_t) * kMiscWords);
@@ -386,12 +526,23 @@ lsm_status lsm_update_batch(lsm_t* h, const uint32_t* d_keys, const uint32_t* d_
   return apply_batch(h, kSortUpdate, d_keys, d_vals, d_is_delete, n, static_cast<cudaStream_t>(stream), true);
 }
 
+lsm_status lsm_update_batch_ordered(lsm_t* h, const uint32_t* d_keys, const uint32_t* d_vals,
+                                    const uint8_t* d_is_delete, uint64_t n, void* stream) {
+  if (!h || (n && !d_keys) || n > h->b) return LSM_ERR_ARG;
+  if (n == 0) return LSM_OK;
+  DeviceGuard g(h->device);
+  // Every op takes the content of the last op on its key (input order), so
+  // the batch rules of §III-A see one kind of op per key.
+  return dict_update_ordered(h, d_keys, d_vals, d_is_delete, n, static_cast<cudaStream_t>(stream), true);
+}
+
 lsm_status lsm_lookup(lsm_t* h, const uint32_t* d_q, uint64_t nq, uint32_t* d_val, uint8_t* d_found,
                       void* stream) {
   if (!h || (nq && (!d_q || !d_val || !d_found))) return LSM_ERR_ARG;
   if (nq == 0) return LSM_OK;
   DeviceGuard g(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  LSM_TRY(join_side(h, st));
   const LevelSet ls = full_levels(h);
   if (ls.count == 0) {
     LSM_TRY(cudaMemsetAsync(d_val, 0, sizeof(uint32_t) * nq, st));
@@ -402,38 +553,10 @@ lsm_status lsm_lookup(lsm_t* h, const uint32_t* d_q, uint64_t nq, uint32_t* d_va
   ProfScope ps(h, LSM_PROF_LOOKUP, double(nq) * (9.0 + 32.0 * ls.count), st);
   if (!sorted) return cuda_status(lookup_launch(ls, d_q, nq, d_val, d_found, st));
   // Sorted mode: radix sort (key, position), then warp-cooperative search.
-  const uint64_t n = nq;
-  const uint64_t tiles = (n + kSortTile - 1) / kSortTile;
-  const uint64_t npad = round_up(n, kLevelAlign) + kSlack;
-  LSM_TRY(ensure_q(h, 4 * npad * sizeof(uint32_t)));
-  if (!h->qsws.lookback || h->qsws.max_tiles < tiles) {
-    if (h->qsws.lookback) cudaFree(h->qsws.lookback);
-    h->qsws.lookback = nullptr;
-    LSM_TRY(dalloc(&h->qsws.lookback, uint64_t(kSortPasses) * tiles * 256));
-    LSM_TRY(cudaMemset(h->qsws.lookback, 0, sizeof(uint64_t) * kSortPasses * tiles * 256));
-    h->qsws.max_tiles = uint32_t(tiles);
-    h->qsws.epoch = 0;
-  }
-  if (!h->d_qctl) {
-    LSM_TRY(dalloc(&h->d_qctl, 2 * kSortCtlWords));
-    LSM_TRY(cudaMemset(h->d_qctl, 0, sizeof(uint32_t) * 2 * kSortCtlWords));
-    h->qsws.flip = 0;
-  }
-  if (!h->qsws.tilecnt) LSM_TRY(dalloc(&h->qsws.tilecnt, kMsdTileWords));
-  h->qsws.ctl = h->d_qctl;
-  h->qsws.sticky = h->d_misc + kMiscSticky;
-  uint32_t* base = reinterpret_cast<uint32_t*>(h->d_q);
-  SortArgs a{};
-  a.mode = kSortQueries;
-  a.in_keys = d_q;
-  a.n_in = n;
-  a.n = uint32_t(n);
-  a.out_keys = base;
-  a.out_vals = base + npad;
-  a.tmp_keys = base + 2 * npad;
-  a.tmp_vals = base + 3 * npad;
-  LSM_TRY(sort_launch(a, h->qsws, st, nullptr, nullptr));
-  return cuda_status(lookup_sorted_launch(ls, a.out_keys, a.out_vals, n, d_val, d_found, st));
+  uint32_t* sk = nullptr;
+  uint32_t* sv = nullptr;
+  LSM_TRY(sort_positions(h, d_q, nq, 0, st, &sk, &sv));
+  return cuda_status(lookup_sorted_launch(ls, sk, sv, nq, d_val, d_found, st));
 }
 
 lsm_status lsm_count(lsm_t* h, const uint32_t* d_k1, const uint32_t* d_k2, uint64_t nq, uint32_t* d_count,
@@ -442,6 +565,7 @@ lsm_status lsm_count(lsm_t* h, const uint32_t* d_k1, const uint32_t* d_k2, uint6
   if (nq == 0) return LSM_OK;
   DeviceGuard g(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  LSM_TRY(join_side(h, st));
   const LevelSet ls = full_levels(h);
   if (ls.count == 0) return cuda_status(cudaMemsetAsync(d_count, 0, sizeof(uint32_t) * nq, st));
   ProfScope ps(h, LSM_PROF_COUNT, double(nq) * (12.0 + 64.0 * ls.count), st);
@@ -453,6 +577,7 @@ lsm_status lsm_range(lsm_t* h, const uint32_t* d_k1, const uint32_t* d_k2, uint6
   if (!h || !d_offsets || !total_out || (nq && (!d_k1 || !d_k2))) return LSM_ERR_ARG;
   DeviceGuard g(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  LSM_TRY(join_side(h, st));
   const LevelSet ls = full_levels(h);
   if (nq == 0 || ls.count == 0) {
     LSM_TRY(cudaMemsetAsync(d_offsets, 0, sizeof(uint64_t) * (nq + 1), st));
@@ -487,6 +612,7 @@ lsm_status lsm_cleanup(lsm_t* h, void* stream) {
   if (h->r == 0) return LSM_OK;
   DeviceGuard g(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  LSM_TRY(join_side(h, st));
   const uint64_t total = h->r * h->b;
   if (h->clean_cap < total) {
     if (h->d_ck) cudaFree(h->d_ck);
@@ -529,6 +655,7 @@ lsm_status lsm_cleanup(lsm_t* h, void* stream) {
   const uint64_t n_live = *h->h_u64;
   if (n_live > total) return LSM_ERR_CUDA;
   const uint64_t r2 = (n_live + h->b - 1) / h->b;
+  h->l0_buf = -1;  // every level is rewritten in the level array
   DistributeArgs d{};
   d.src_keys = h->d_ck;
   d.src_vals = h->d_cv;
@@ -580,7 +707,14 @@ uint64_t lsm_capacity(const lsm_t* h) { return h ? h->capacity : 0; }
 lsm_status lsm_reset(lsm_t* h) {
   if (!h) return LSM_ERR_ARG;
   h->r = 0;
+  h->l0_buf = -1;
   return LSM_OK;
+}
+
+lsm_status lsm_stream_wait(lsm_t* h, void* stream) {
+  if (!h) return LSM_ERR_ARG;
+  DeviceGuard g(h->device);
+  return cuda_status(join_side(h, static_cast<cudaStream_t>(stream)));
 }
 
 lsm_status lsm_profile(lsm_t* h, int enable) {
@@ -620,11 +754,12 @@ lsm_status lsm_dump_levels(const lsm_t* h, uint32_t* h_keys, uint32_t* h_vals, v
   if (!h || !h_keys || !h_vals) return LSM_ERR_ARG;
   DeviceGuard g(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  LSM_TRY(join_side(h, st));
   for (uint32_t i = 0; i < h->L; ++i) {
     if (!((h->r >> i) & 1u)) continue;
     const uint64_t off = h->level_off[i], n = uint64_t(h->b) << i;
-    LSM_TRY(cudaMemcpyAsync(h_keys + off, h->d_keys + off, n * 4, cudaMemcpyDeviceToHost, st));
-    LSM_TRY(cudaMemcpyAsync(h_vals + off, h->d_vals + off, n * 4, cudaMemcpyDeviceToHost, st));
+    LSM_TRY(cudaMemcpyAsync(h_keys + off, level_keys(h, int(i)), n * 4, cudaMemcpyDeviceToHost, st));
+    LSM_TRY(cudaMemcpyAsync(h_vals + off, level_vals(h, int(i)), n * 4, cudaMemcpyDeviceToHost, st));
   }
   return cuda_status(cudaStreamSynchronize(st));
 }

@@ -254,6 +254,21 @@ cudaError_t multi_fold_launch(const MultiArena& ar, cudaStream_t st);
 cudaError_t multi_lookup_launch(const MultiArena& ar, const uint32_t* q, const uint64_t* qoff, uint64_t nq,
                                 uint32_t* val, uint8_t* found, cudaStream_t st);
 
+// --------------------------------------------------------------- serving ---
+// Ordered batch: (sk, sv) = the batch's keys sorted stably with their input
+// positions; op p of the output is a copy of the last op (input order) on
+// key(p).  vals / del may be null (0 / insert).
+cudaError_t resolve_last_launch(const uint32_t* sk, const uint32_t* sv, uint32_t n, const uint32_t* keys,
+                                const uint32_t* vals, const uint8_t* del, uint32_t* out_k, uint32_t* out_v,
+                                uint8_t* out_d, cudaStream_t st);
+
+// Gathers windows of device-resident payload arrays: for request j,
+// dst[dst_off[j] + t] = src[start[j] + t], t < size[j] (up to two arrays at
+// once; src_b / dst_b may be null).
+cudaError_t gather_windows_launch(const uint32_t* src_a, const uint32_t* src_b, const uint64_t* start,
+                                  const uint32_t* size, const uint64_t* dst_off, uint32_t nreq, uint32_t* dst_a,
+                                  uint32_t* dst_b, cudaStream_t st);
+
 // ----------------------------------------------------------------- query ---
 struct LevelSet {
   const uint32_t* keys[kMaxLevels];

@@ -53,6 +53,7 @@ _SIGS = {
     "lsm_insert_batch": ([_vp, _vp, _vp, _u64, _vp], _i32),
     "lsm_delete_batch": ([_vp, _vp, _u64, _vp], _i32),
     "lsm_update_batch": ([_vp, _vp, _vp, _vp, _u64, _vp], _i32),
+    "lsm_update_batch_ordered": ([_vp, _vp, _vp, _vp, _u64, _vp], _i32),
     "lsm_lookup": ([_vp, _vp, _u64, _vp, _vp, _vp], _i32),
     "lsm_count": ([_vp, _vp, _vp, _u64, _vp, _vp], _i32),
     "lsm_range": ([_vp, _vp, _vp, _u64, _vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp], _i32),
@@ -66,6 +67,7 @@ _SIGS = {
     "lsm_set_option": ([_vp, _i32, _i64], _i32),
     "lsm_get_option": ([_vp, _i32, ctypes.POINTER(_i64)], _i32),
     "lsm_reset": ([_vp], _i32),
+    "lsm_stream_wait": ([_vp, _vp], _i32),
     "lsm_profile": ([_vp, _i32], _i32),
     "lsm_profile_read": ([_vp, ctypes.POINTER(ProfileEntry)], _i32),
     "lsm_sort_pairs_noalloc": ([_vp, _vp, _vp, _vp, _u64, _vp], _i32),
@@ -128,6 +130,11 @@ def lsm_delete_batch(h, d_keys, n, stream=None):
 
 def lsm_update_batch(h, d_keys, d_vals, d_is_delete, n, stream=None):
     return _check(_lib.lsm_update_batch(h, d_keys, d_vals, d_is_delete, n, stream), "lsm_update_batch")
+
+
+def lsm_update_batch_ordered(h, d_keys, d_vals, d_is_delete, n, stream=None):
+    return _check(_lib.lsm_update_batch_ordered(h, d_keys, d_vals, d_is_delete, n, stream),
+                  "lsm_update_batch_ordered")
 
 
 def lsm_lookup(h, d_q, nq, d_val, d_found, stream=None):
@@ -194,6 +201,10 @@ def lsm_sort_pairs_noalloc(d_kin, d_vin, d_kout, d_vout, n, stream=None):
 
 def lsm_reset(h):
     return _check(_lib.lsm_reset(h), "lsm_reset")
+
+
+def lsm_stream_wait(h, stream=None):
+    return _check(_lib.lsm_stream_wait(h, stream), "lsm_stream_wait")
 
 
 def lsm_profile(h, enable):
@@ -357,6 +368,11 @@ class LSM:
         k, v = as_device_u32(keys, self.device), as_device_u32(vals, self.device)
         d = as_device_u8(is_delete, self.device)
         lsm_update_batch(self.h, _ptr(k), _ptr(v), _ptr(d), k.numel(), _stream(self.device))
+
+    def update_ordered(self, keys, vals, is_delete):
+        k, v = as_device_u32(keys, self.device), as_device_u32(vals, self.device)
+        d = as_device_u8(is_delete, self.device)
+        lsm_update_batch_ordered(self.h, _ptr(k), _ptr(v), _ptr(d), k.numel(), _stream(self.device))
 
     def call(self, kind, keys, vals=None, is_delete=None):
         if kind == "insert":
