@@ -50,8 +50,14 @@ def parse_args():
     p.add_argument("--lookup-mode", type=int, default=0, help="0 auto, 1 direct, 2 sorted")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="paper", choices=["paper", "batched"],
-                   help="paper: b=2^20 plain dictionary (default); batched: 256 dictionaries per round")
+    p.add_argument("--workload", default="paper", choices=["paper", "batched", "serving"],
+                   help="paper: b=2^20 plain dictionary (default); batched: 256 dictionaries per round; "
+                        "serving: a Poisson stream of mixed requests through the serving engine")
+    p.add_argument("--requests", type=int, default=10 ** 6, help="serving: requests in the trace")
+    p.add_argument("--rate", type=float, default=3.0e5, help="serving: arrivals per second")
+    p.add_argument("--flush-us", type=float, default=1000.0, help="serving: longest wait of a partial batch")
+    p.add_argument("--preload-log2", type=int, default=28, help="serving: dictionary size before the stream")
+    p.add_argument("--budget-gb", type=float, default=64.0, help="serving: HBM admission budget (GiB)")
     p.add_argument("--instances", type=int, default=256)
     p.add_argument("--rounds", type=int, default=32)
     p.add_argument("--no-plain", action="store_true", help="batched: skip the per-instance plain-call arm")
@@ -676,8 +682,111 @@ def run_batched(args):
     return 0
 
 
+# ---------------------------------------------------------------- serving --
+SERVING_METRIC = "serving: M keys/s and p50/p99 request latency (mixed stream, 64 GB HBM budget)"
+
+
+def latency_stats(out, arrival):
+    lat = (out["done_us"] - arrival) / 1000.0
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "max_ms": float(lat.max())}
+
+
+def run_serving(args):
+    import torch
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1707_05354_gb300 import gpulsm as G
+    from paper_1707_05354_gb300 import workload
+
+    b = 1 << args.b_log2
+    pool_n = 1 << 26
+    pa, pb, pc = workload.serving_pools(n=pool_n)
+    kind, arrival, start, size = workload.serving_trace(n_req=args.requests, rate=args.rate, pool_n=pool_n)
+    wk, wa, ws, wz = workload.serving_trace(seed=workload.SERVING_SEED + 1, n_req=max(1000, args.requests // 100),
+                                            rate=args.rate, pool_n=pool_n)
+    keys_total = int(size.astype(np.int64).sum())
+    # preload: uniform keys drawn on the device (setup, not timed)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(workload.SERVING_SEED)
+    npre = 1 << args.preload_log2
+    pre_k = torch.randint(0, (1 << 31) - 1, (npre,), device=dev, dtype=torch.int64, generator=gen).to(torch.int32)
+    pre_v = torch.randint(0, 1 << 31, (npre,), device=dev, dtype=torch.int64, generator=gen).to(torch.int32)
+    budget = int(args.budget_gb * (1 << 30))
+    res = {}
+    clocks = None
+    launches = 0
+    for name, policy in (("continuous", G.SERVE_CONTINUOUS), ("fixed", G.SERVE_FIXED)):
+        srv = G.Server(b, budget, flush_us=args.flush_us, group_keys=1 << 20, slots=3, range_cap=1 << 25,
+                       policy=policy, device=local)
+        srv.set_pool(pa, pb, pc)
+        srv.preload(pre_k, pre_v)
+        for _ in range(max(1, args.warmup)):
+            srv.run(wk, wa, ws, wz)       # warm-up: a short trace of the same mix
+        st0 = srv.stats()
+        sampler = ClockSampler(local) if name == "continuous" else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        l0 = G.kernel_launches()
+        out = srv.run(kind, arrival, start, size)
+        if name == "continuous":
+            launches = G.kernel_launches() - l0
+        if sampler:
+            clocks = sampler.stop()
+        st1 = srv.stats()
+        wall_s = out["wall_us"] / 1e6
+        res[name] = dict(latency=latency_stats(out, arrival), requests_per_s=len(kind) / wall_s,
+                         M_keys_per_s=keys_total / wall_s / 1e6, wall_s=wall_s,
+                         update_batches=int(out["update_batches"]), padded_ops=int(out["padded_ops"]),
+                         retrieval_groups=int(out["retrieval_groups"]), cleanups=int(out["cleanups"]),
+                         refused=int(out["refused"]), range_results=int(out["range_total"]),
+                         levels=st0["levels"], device_bytes=st0["device_bytes"],
+                         resident_before=st0["resident"], resident_after=st1["resident"],
+                         all_ok=bool((out["status"] == 0).all()))
+        srv.close()
+        del srv
+        torch.cuda.synchronize(dev)
+    c = res["continuous"]
+    span_s = float(arrival[-1]) / 1e6
+    if rank == 0:
+        line = {
+            "metric": SERVING_METRIC, "value": c["M_keys_per_s"], "unit": "M keys/s", "n_gpus": world,
+            "steps": 1, "warmup": max(1, args.warmup), "ms_per_step": 1000 * c["wall_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (seeded Poisson arrivals, kinds 40/10/35/5/10 %, sizes round(2^U[0,16]) keys; "
+                    "payload windows of device-resident pools of 2^26 uniform keys; preload 2^%d uniform keys)"
+                    % args.preload_log2,
+            "config": {"workload": "serving: %d requests at %.0f/s (%.2f s of arrivals, %d keys), b=2^%d, "
+                                   "%.0f GiB HBM budget, flush %.0f us, 3 slots"
+                                   % (len(kind), args.rate, span_s, keys_total, args.b_log2, args.budget_gb,
+                                      args.flush_us),
+                       "requests": len(kind), "rate_per_s": args.rate, "b": b, "budget_gib": args.budget_gb,
+                       "l2": "payload pools (768 MB) and dictionary (>= 2 GB) larger than L2",
+                       "parallelism": "single GPU"},
+            "latency_ms": {"p50": c["latency"]["p50_ms"], "p99": c["latency"]["p99_ms"]},
+            "continuous": c, "fixed_batching": res["fixed"],
+            "vs_fixed": {"p50_ratio": res["fixed"]["latency"]["p50_ms"] / max(1e-9, c["latency"]["p50_ms"]),
+                         "p99_ratio": res["fixed"]["latency"]["p99_ms"] / max(1e-9, c["latency"]["p99_ms"]),
+                         "throughput_ratio": c["M_keys_per_s"] / max(1e-9, res["fixed"]["M_keys_per_s"])},
+            "roofline": None, "cpu_baseline": None,
+            "e2e": {"value": c["M_keys_per_s"], "unit": "M keys/s", "h2d_bytes_per_step": 21 * len(kind),
+                    "d2h_bytes_per_step": None,
+                    "note": "the serving loop itself is end to end: request descriptors go host to device per "
+                            "group, results come back to pinned host memory before a request completes"},
+            "gpu_launches": int(launches), "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":

@@ -430,6 +430,103 @@ typedef enum {
 lsm_status lsm_multi_set_option(lsm_multi_t* h, int opt, int64_t value);
 lsm_status lsm_multi_get_option(const lsm_multi_t* h, int opt, int64_t* value);
 
+
+/* ========================================================================
+ * Serving form: a continuous-batching request loop over one dictionary
+ * ========================================================================
+ * Not in the paper.  A server owns a dictionary of batch size b and replays
+ * a trace of requests (insert, delete, lookup, count, range; each naming a
+ * window of device-resident payload pools) in real time: requests become
+ * visible at their arrival times, wait in an update queue and a retrieval
+ * queue, and are admitted as groups into a few in-flight slots while earlier
+ * groups still run:
+ *   - an update group is whole update requests, up to b ops, applied as one
+ *     ordered batch (lsm_update_batch_ordered), admitted when b ops are
+ *     pending, when its oldest request has waited flush_us, or at the end of
+ *     the trace (a short batch is padded);
+ *   - a retrieval group is every pending lookup / count / range request up
+ *     to group_keys keys, admitted as soon as a slot is free.
+ * Requests are linearised in admission order: each sees exactly the updates
+ * of the groups admitted before its own (result->order gives the group
+ * sequence number of every request).  Device memory is admitted against
+ * hbm_budget: the dictionary gets the largest level count whose levels,
+ * cleanup scratch and batch scratch fit beside the slots' buffers; an update
+ * group that would need a level beyond it triggers a cleanup (§III-F) first,
+ * and is refused (LSM_ERR_BUDGET for its requests) if the live data still
+ * fills every level.  Policy LSM_SERVE_FIXED is the comparison point:
+ * requests wait until b ops are pending (or the trace has ended), then all
+ * pending work runs to completion before anything else is admitted.
+ */
+typedef struct lsm_server_t lsm_server_t;
+
+enum { LSM_REQ_INSERT = 0, LSM_REQ_DELETE = 1, LSM_REQ_LOOKUP = 2, LSM_REQ_COUNT = 3, LSM_REQ_RANGE = 4 };
+enum { LSM_SERVE_CONTINUOUS = 0, LSM_SERVE_FIXED = 1 };
+
+typedef struct {
+  uint32_t b;           /* device batch size, 1 .. 2^20 */
+  uint64_t hbm_budget;  /* bytes of device memory the server may hold */
+  double flush_us;      /* longest wait of an update before its partial batch is admitted */
+  uint32_t group_keys;  /* keys (lookup keys + count/range intervals) per retrieval group */
+  uint32_t slots;       /* groups in flight (continuous policy), 1 .. 16 */
+  uint32_t range_cap;   /* range results one retrieval group may produce */
+  int policy;           /* LSM_SERVE_CONTINUOUS or LSM_SERVE_FIXED */
+  int device;
+} lsm_server_config;
+
+typedef struct {
+  uint64_t n;                /* requests */
+  const uint8_t* kind;       /* LSM_REQ_* per request */
+  const double* arrival_us;  /* non-decreasing, microseconds after the start of the run */
+  const uint64_t* start;     /* request i uses pool entries [start[i], start[i] + size[i]) */
+  const uint32_t* size;      /* 1 .. group_keys (and <= b for updates) */
+} lsm_trace;
+
+typedef struct {
+  /* required, n entries each */
+  double* done_us;           /* when the server saw the request's group complete */
+  int32_t* status;           /* LSM_OK or LSM_ERR_BUDGET (refused update) */
+  uint64_t* order;           /* admission sequence number of the request's group, or NULL */
+  /* optional results (NULL: dropped once copied to the server's host buffers) */
+  const uint64_t* res_off;   /* n: first per-key result slot of request i */
+  uint32_t* val;             /* lookup value / count / range result count, per key */
+  uint8_t* found;            /* lookup found flag, per key */
+  uint64_t* range_start;     /* range: first result of each interval in rk/rv */
+  uint32_t* rk;              /* range results, original keys ascending per interval */
+  uint32_t* rv;
+  uint64_t range_cap;        /* entries of rk/rv */
+  /* filled by the run */
+  uint64_t range_total;
+  uint64_t update_batches, padded_ops, retrieval_groups, cleanups, refused;
+  double wall_us;
+} lsm_trace_result;
+
+/* Creates the server and its dictionary.  Errors: LSM_ERR_ARG,
+ * LSM_ERR_BUDGET (not even one level fits), LSM_ERR_OOM, LSM_ERR_CUDA. */
+lsm_status lsm_server_create(lsm_server_t** out, const lsm_server_config* cfg);
+void lsm_server_destroy(lsm_server_t* s);
+
+/* Registers the payload pools (device arrays of n u32, kept by the caller
+ * while the server runs): d_a = keys of updates and lookups and the lower
+ * bounds of count/range intervals, d_b = insert values, d_c = upper bounds.
+ * Every key of d_a must be < 2^31 - 1 (checked here once, so that update
+ * batches need no per-batch check): else LSM_ERR_KEY_RANGE. */
+lsm_status lsm_server_set_pool(lsm_server_t* s, const uint32_t* d_a, const uint32_t* d_b, const uint32_t* d_c,
+                               uint64_t n);
+
+/* Inserts n pairs into the dictionary before a run (synchronous). */
+lsm_status lsm_server_preload(lsm_server_t* s, const uint32_t* d_keys, const uint32_t* d_vals, uint64_t n);
+
+/* Replays the trace in real time (blocking until every request completed). */
+lsm_status lsm_server_run(lsm_server_t* s, const lsm_trace* t, lsm_trace_result* r);
+
+/* Dictionary counter and resident elements, level count chosen for the
+ * budget, and the device bytes the budget accounts for. */
+lsm_status lsm_server_stats(const lsm_server_t* s, uint64_t* r, uint64_t* resident, uint32_t* levels,
+                            uint64_t* device_bytes);
+
+/* The server's dictionary (owned by the server), for queries between runs. */
+lsm_t* lsm_server_dict(lsm_server_t* s);
+
 #ifdef __cplusplus
 }
 #endif

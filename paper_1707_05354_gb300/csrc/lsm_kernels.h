@@ -269,6 +269,12 @@ cudaError_t gather_windows_launch(const uint32_t* src_a, const uint32_t* src_b, 
                                   const uint32_t* size, const uint64_t* dst_off, uint32_t nreq, uint32_t* dst_a,
                                   uint32_t* dst_b, cudaStream_t st);
 
+// Gathers whole update requests into a batch: keys from pool_k, values from
+// pool_v (0 for a delete request), the request's delete flag per op.
+cudaError_t gather_update_launch(const uint32_t* pool_k, const uint32_t* pool_v, const uint64_t* start,
+                                 const uint32_t* size, const uint64_t* dst_off, const uint8_t* is_del, uint32_t nreq,
+                                 uint32_t* out_k, uint32_t* out_v, uint8_t* out_d, cudaStream_t st);
+
 // ----------------------------------------------------------------- query ---
 struct LevelSet {
   const uint32_t* keys[kMaxLevels];

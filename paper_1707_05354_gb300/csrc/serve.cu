@@ -55,7 +55,39 @@ __global__ void __launch_bounds__(256) gather_windows(const uint32_t* __restrict
   }
 }
 
+// One CTA per update request: its keys, its values (0 for a delete) and
+// its delete flag, at its offset in the batch.
+__global__ void __launch_bounds__(256) gather_update(const uint32_t* __restrict__ pool_k,
+                                                     const uint32_t* __restrict__ pool_v,
+                                                     const uint64_t* __restrict__ start,
+                                                     const uint32_t* __restrict__ size,
+                                                     const uint64_t* __restrict__ dst_off,
+                                                     const uint8_t* __restrict__ is_del, uint32_t nreq,
+                                                     uint32_t* __restrict__ out_k, uint32_t* __restrict__ out_v,
+                                                     uint8_t* __restrict__ out_d) {
+  for (uint32_t j = blockIdx.x; j < nreq; j += gridDim.x) {
+    const uint64_t s = __ldg(start + j), d = __ldg(dst_off + j);
+    const uint32_t m = __ldg(size + j);
+    const uint8_t del = __ldg(is_del + j);
+    for (uint32_t t = threadIdx.x; t < m; t += 256u) {
+      out_k[d + t] = __ldg(pool_k + s + t);
+      out_v[d + t] = del ? 0u : __ldg(pool_v + s + t);
+      out_d[d + t] = del;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t gather_update_launch(const uint32_t* pool_k, const uint32_t* pool_v, const uint64_t* start,
+                                 const uint32_t* size, const uint64_t* dst_off, const uint8_t* is_del, uint32_t nreq,
+                                 uint32_t* out_k, uint32_t* out_v, uint8_t* out_d, cudaStream_t st) {
+  if (nreq == 0) return cudaSuccess;
+  const uint32_t blocks = nreq < 152 * 16 ? nreq : 152 * 16;
+  count_launches(1);
+  gather_update<<<blocks, 256, 0, st>>>(pool_k, pool_v, start, size, dst_off, is_del, nreq, out_k, out_v, out_d);
+  return cudaGetLastError();
+}
 
 cudaError_t resolve_last_launch(const uint32_t* sk, const uint32_t* sv, uint32_t n, const uint32_t* keys,
                                 const uint32_t* vals, const uint8_t* del, uint32_t* out_k, uint32_t* out_v,

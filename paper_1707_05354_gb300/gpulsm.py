@@ -32,6 +32,8 @@ LSM_ERR_OOM, LSM_ERR_BUDGET, LSM_ERR_CAPACITY, LSM_ERR_CUDA, LSM_ERR_TIMEOUT = 4
 LSM_OPT_LOOKUP_MODE, LSM_OPT_DEVICE_ERROR, LSM_OPT_KERNEL_LAUNCHES = 1, 2, 3
 LOOKUP_AUTO, LOOKUP_DIRECT, LOOKUP_SORTED = 0, 1, 2
 LSM_MULTI_OPT_GRAPH, LSM_MULTI_OPT_GRAPH_KERNELS, LSM_MULTI_OPT_DEVICE_BYTES = 1, 2, 3
+REQ_INSERT, REQ_DELETE, REQ_LOOKUP, REQ_COUNT, REQ_RANGE = 0, 1, 2, 3, 4
+SERVE_CONTINUOUS, SERVE_FIXED = 0, 1
 MULTI_FLAG_BAD_KEY, MULTI_FLAG_ARG, MULTI_FLAG_FULL = 1, 8, 16
 PROF_GROUPS = ("sort", "partition", "merge", "lookup", "count", "emit", "cleanup")
 
@@ -39,6 +41,30 @@ PROF_GROUPS = ("sort", "partition", "merge", "lookup", "count", "emit", "cleanup
 class MultiTuning(ctypes.Structure):
     """lsm_multi_tuning: merge tile (1024 | 2048) and prefix-index bin_log2."""
     _fields_ = [("tile", ctypes.c_uint32), ("bin_log2", ctypes.c_uint32)]
+
+
+class ServerConfig(ctypes.Structure):
+    """lsm_server_config."""
+    _fields_ = [("b", ctypes.c_uint32), ("hbm_budget", ctypes.c_uint64), ("flush_us", ctypes.c_double),
+                ("group_keys", ctypes.c_uint32), ("slots", ctypes.c_uint32), ("range_cap", ctypes.c_uint32),
+                ("policy", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class Trace(ctypes.Structure):
+    """lsm_trace."""
+    _fields_ = [("n", ctypes.c_uint64), ("kind", ctypes.c_void_p), ("arrival_us", ctypes.c_void_p),
+                ("start", ctypes.c_void_p), ("size", ctypes.c_void_p)]
+
+
+class TraceResult(ctypes.Structure):
+    """lsm_trace_result."""
+    _fields_ = [("done_us", ctypes.c_void_p), ("status", ctypes.c_void_p), ("order", ctypes.c_void_p),
+                ("res_off", ctypes.c_void_p), ("val", ctypes.c_void_p), ("found", ctypes.c_void_p),
+                ("range_start", ctypes.c_void_p), ("rk", ctypes.c_void_p), ("rv", ctypes.c_void_p),
+                ("range_cap", ctypes.c_uint64), ("range_total", ctypes.c_uint64),
+                ("update_batches", ctypes.c_uint64), ("padded_ops", ctypes.c_uint64),
+                ("retrieval_groups", ctypes.c_uint64), ("cleanups", ctypes.c_uint64), ("refused", ctypes.c_uint64),
+                ("wall_us", ctypes.c_double)]
 
 
 class ProfileEntry(ctypes.Structure):
@@ -83,6 +109,14 @@ _SIGS = {
     "lsm_multi_dump_levels": ([_vp, _u32, _vp, _vp], _i32),
     "lsm_multi_reset": ([_vp, _vp], _i32),
     "lsm_multi_set_option": ([_vp, _i32, _i64], _i32),
+    "lsm_server_create": ([ctypes.POINTER(_vp), ctypes.POINTER(ServerConfig)], _i32),
+    "lsm_server_destroy": ([_vp], None),
+    "lsm_server_set_pool": ([_vp, _vp, _vp, _vp, _u64], _i32),
+    "lsm_server_preload": ([_vp, _vp, _vp, _u64], _i32),
+    "lsm_server_run": ([_vp, ctypes.POINTER(Trace), ctypes.POINTER(TraceResult)], _i32),
+    "lsm_server_stats": ([_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u32),
+                          ctypes.POINTER(_u64)], _i32),
+    "lsm_server_dict": ([_vp], _vp),
     "lsm_multi_get_option": ([_vp, _i32, ctypes.POINTER(_i64)], _i32),
 }
 SORT_NOALLOC_MAX_PAIRS = 1 << 20
@@ -288,6 +322,42 @@ def lsm_multi_get_option(h, opt):
     v = _i64()
     _check(_lib.lsm_multi_get_option(h, opt, ctypes.byref(v)), "lsm_multi_get_option")
     return v.value
+
+
+# serving form ----------------------------------------------------------
+def lsm_server_create(b, hbm_budget, flush_us=200.0, group_keys=1 << 20, slots=3, range_cap=1 << 25,
+                      policy=0, device=0):
+    cfg = ServerConfig(b, hbm_budget, flush_us, group_keys, slots, range_cap, policy, device)
+    h = _vp()
+    _check(_lib.lsm_server_create(ctypes.byref(h), ctypes.byref(cfg)), "lsm_server_create")
+    return h.value
+
+
+def lsm_server_destroy(h):
+    _lib.lsm_server_destroy(h)
+
+
+def lsm_server_set_pool(h, d_a, d_b, d_c, n):
+    return _check(_lib.lsm_server_set_pool(h, d_a, d_b, d_c, n), "lsm_server_set_pool")
+
+
+def lsm_server_preload(h, d_keys, d_vals, n):
+    return _check(_lib.lsm_server_preload(h, d_keys, d_vals, n), "lsm_server_preload")
+
+
+def lsm_server_run(h, trace, result):
+    return _check(_lib.lsm_server_run(h, ctypes.byref(trace), ctypes.byref(result)), "lsm_server_run")
+
+
+def lsm_server_stats(h):
+    r, res, lv, by = _u64(), _u64(), _u32(), _u64()
+    _check(_lib.lsm_server_stats(h, ctypes.byref(r), ctypes.byref(res), ctypes.byref(lv), ctypes.byref(by)),
+           "lsm_server_stats")
+    return dict(r=r.value, resident=res.value, levels=lv.value, device_bytes=by.value)
+
+
+def lsm_server_dict(h):
+    return _lib.lsm_server_dict(h)
 
 
 def kernel_launches():
@@ -523,3 +593,74 @@ class MultiLSM:
 
     def set_graph(self, on):
         lsm_multi_set_option(self.h, LSM_MULTI_OPT_GRAPH, 1 if on else 0)
+
+
+class Server:
+    """Serving engine (lsm_server_*) over one dictionary of batch size b.
+
+    ``pools``: (a, b, c) device tensors (int32 bits of u32) of equal length;
+    ``run(kind, arrival_us, start, size, keep_results)`` replays a trace and
+    returns a dict of per-request numpy arrays (done_us, status, order, and,
+    with keep_results, the results)."""
+
+    def __init__(self, b, hbm_budget, flush_us=200.0, group_keys=1 << 20, slots=3, range_cap=1 << 25,
+                 policy=SERVE_CONTINUOUS, device=0):
+        self.device = device
+        self.h = lsm_server_create(b, hbm_budget, flush_us, group_keys, slots, range_cap, policy, device)
+        self._pools = None
+
+    def close(self):
+        if self.h:
+            lsm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_pool(self, a, b, c):
+        self._pools = tuple(as_device_u32(x, self.device) for x in (a, b, c))
+        pa, pb, pc = self._pools
+        lsm_server_set_pool(self.h, _ptr(pa), _ptr(pb), _ptr(pc), pa.numel())
+
+    def preload(self, keys, vals):
+        k, v = as_device_u32(keys, self.device), as_device_u32(vals, self.device)
+        lsm_server_preload(self.h, _ptr(k), _ptr(v), k.numel())
+
+    def stats(self):
+        return lsm_server_stats(self.h)
+
+    def run(self, kind, arrival_us, start, size, keep_results=False, range_cap=None):
+        import numpy as np
+        n = len(kind)
+        kind = np.ascontiguousarray(kind, np.uint8)
+        arr = np.ascontiguousarray(arrival_us, np.float64)
+        start = np.ascontiguousarray(start, np.uint64)
+        size = np.ascontiguousarray(size, np.uint32)
+        tr = Trace(n, kind.ctypes.data, arr.ctypes.data, start.ctypes.data, size.ctypes.data)
+        out = dict(done_us=np.zeros(n, np.float64), status=np.zeros(n, np.int32), order=np.zeros(n, np.uint64))
+        res = TraceResult()
+        res.done_us, res.status, res.order = (out["done_us"].ctypes.data, out["status"].ctypes.data,
+                                              out["order"].ctypes.data)
+        if keep_results:
+            off = np.concatenate([[0], np.cumsum(size.astype(np.uint64))]).astype(np.uint64)
+            tot = int(off[-1])
+            out["res_off"] = off[:-1].copy()
+            out["val"] = np.zeros(max(1, tot), np.uint32)
+            out["found"] = np.zeros(max(1, tot), np.uint8)
+            out["range_start"] = np.zeros(max(1, tot), np.uint64)
+            cap = int(range_cap if range_cap is not None else 16 * tot)
+            out["rk"] = np.zeros(max(1, cap), np.uint32)
+            out["rv"] = np.zeros(max(1, cap), np.uint32)
+            res.res_off, res.val, res.found = (out["res_off"].ctypes.data, out["val"].ctypes.data,
+                                               out["found"].ctypes.data)
+            res.range_start, res.rk, res.rv = (out["range_start"].ctypes.data, out["rk"].ctypes.data,
+                                               out["rv"].ctypes.data)
+            res.range_cap = cap
+        lsm_server_run(self.h, tr, res)
+        out.update(range_total=res.range_total, update_batches=res.update_batches, padded_ops=res.padded_ops,
+                   retrieval_groups=res.retrieval_groups, cleanups=res.cleanups, refused=res.refused,
+                   wall_us=res.wall_us)
+        return out

@@ -268,3 +268,38 @@ class BatchedWorkload:
             qq = np.concatenate([hits, u32(gq, b - half, 0, KEY_LIMIT)])
             q[s] = qq[gq.permutation(b)]
         return keys, vals, dele, q
+
+
+# --------------------------------------------------------------------------
+# Configuration "serving": a Poisson stream of mixed requests.
+# --------------------------------------------------------------------------
+SERVING_SEED = 1707053505
+SERVING_MIX = (0.40, 0.10, 0.35, 0.05, 0.10)   # insert, delete, lookup, count, range
+
+
+def serving_pools(seed=SERVING_SEED, n=1 << 26, key_space=KEY_LIMIT, width=8):
+    """Payload pools: a = keys uniform in [0, key_space) (update and lookup
+    keys, count/range lower bounds), b = values uniform u32, c = a + width - 1
+    (count/range upper bounds, clamped below 2^31 - 1)."""
+    g = rng(seed, _STREAM_MISC, 1)
+    a = u32(g, n, 0, key_space)
+    b = u32(g, n)
+    c = np.minimum(a.astype(np.int64) + width - 1, KEY_LIMIT - 1).astype(np.uint32)
+    return a, b, c
+
+
+def serving_trace(seed=SERVING_SEED, n_req=10 ** 6, rate=3.0e5, pool_n=1 << 26, size_lo_log2=0.0,
+                  size_hi_log2=16.0, mix=SERVING_MIX):
+    """Requests of configuration 5: Poisson arrivals at `rate` per second
+    (exponential gaps, microseconds), kinds drawn with probabilities `mix`
+    (insert, delete, lookup, count, range), sizes round(2^U[lo, hi]) keys,
+    each request a window of that many consecutive pool entries starting at
+    a uniform position."""
+    g = rng(seed, _STREAM_QUERY, 7)
+    gaps = g.exponential(1e6 / rate, size=n_req)
+    arrival = np.cumsum(gaps) - gaps[0]
+    kind = g.choice(5, size=n_req, p=np.asarray(mix) / np.sum(mix)).astype(np.uint8)
+    size = np.rint(np.exp2(g.uniform(size_lo_log2, size_hi_log2, size=n_req))).astype(np.int64)
+    size = np.maximum(size, 1)
+    start = (g.random(n_req) * (pool_n - size + 1)).astype(np.int64)
+    return kind, arrival, start.astype(np.uint64), size.astype(np.uint32)

@@ -302,3 +302,39 @@ def test_max_user_key_and_lookup_mode_agreement(g):
         np.testing.assert_array_equal(found.cpu().numpy(), ef)
         np.testing.assert_array_equal(u32(val), ev)
     assert u32(lsm.count([0], [2**32 - 1])).tolist() == [4]
+
+
+@pytest.mark.parametrize("b,key_space,nb", [(1, 4, 30), (7, 6, 20), (64, 40, 25), (1000, 300, 12), (4096, 2000, 6)])
+def test_ordered_update_batches(g, b, key_space, nb):
+    """lsm_update_batch_ordered: the ops of a batch take effect in input
+    order (the last op on a key decides, a delete then an insert leaves the
+    key inserted), i.e. the batch equals applying its ops one by one to the
+    ordered map.  The levels equal those of the plain update batch whose ops
+    were pre-resolved to the last op on each key (written out with numpy)."""
+    rs = np.random.default_rng(b * 31 + key_space)
+    lsm = g.LSM(b, nb * b + b)
+    o1 = oracle.MapOracle(b)
+    s = oracle.StructuralOracle(b)
+    for t in range(nb):
+        n = int(rs.integers(1, b + 1))
+        keys = rs.integers(0, key_space, size=n).astype(np.uint32)
+        vals = rs.integers(0, 1 << 32, size=n, dtype=np.uint64).astype(np.uint32)
+        dele = (rs.random(n) < 0.4).astype(np.uint8)
+        lsm.update_ordered(keys, vals, dele)
+        for i in range(n):   # one op at a time
+            o1.apply_batch(keys[i:i + 1], vals[i:i + 1], dele[i:i + 1])
+        # the same batch pre-resolved: every op a copy of the last op on its key
+        last = {}
+        for i in range(n):
+            last[int(keys[i])] = i
+        w = np.array([last[int(k)] for k in keys], np.int64)
+        s.call("update", keys[w], vals[w], dele[w])
+    assert_levels(lsm, s)
+    q = np.arange(key_space + 3, dtype=np.uint32)
+    val, found = lsm.lookup(q)
+    ev, ef = o1.lookup(q)
+    np.testing.assert_array_equal(found.cpu().numpy(), ef)
+    np.testing.assert_array_equal(u32(val), ev)
+    k1 = np.zeros(1, np.uint32)
+    k2 = np.full(1, key_space, np.uint32)
+    np.testing.assert_array_equal(u32(lsm.count(k1, k2)), o1.count(k1, k2))
