@@ -745,6 +745,7 @@ def run_serving(args):
                          levels=st0["levels"], device_bytes=st0["device_bytes"],
                          resident_before=st0["resident"], resident_after=st1["resident"],
                          all_ok=bool((out["status"] == 0).all()))
+        print("serving %s: %s" % (name, json.dumps(res[name])), file=sys.stderr, flush=True)
         srv.close()
         del srv
         torch.cuda.synchronize(dev)
@@ -755,7 +756,7 @@ def run_serving(args):
             "metric": SERVING_METRIC, "value": c["M_keys_per_s"], "unit": "M keys/s", "n_gpus": world,
             "steps": 1, "warmup": max(1, args.warmup), "ms_per_step": 1000 * c["wall_s"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic (seeded Poisson arrivals, kinds 40/10/35/5/10 %, sizes round(2^U[0,16]) keys; "
+            "data": "synthetic (seeded Poisson arrivals, kinds 40/10/35/5/10 %%, sizes round(2^U[0,16]) keys; "
                     "payload windows of device-resident pools of 2^26 uniform keys; preload 2^%d uniform keys)"
                     % args.preload_log2,
             "config": {"workload": "serving: %d requests at %.0f/s (%.2f s of arrivals, %d keys), b=2^%d, "
