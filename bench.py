@@ -742,6 +742,7 @@ def run_serving(args):
                          update_batches=int(out["update_batches"]), padded_ops=int(out["padded_ops"]),
                          retrieval_groups=int(out["retrieval_groups"]), cleanups=int(out["cleanups"]),
                          refused=int(out["refused"]), range_results=int(out["range_total"]),
+                         time_split=out["time_split"],
                          levels=st0["levels"], device_bytes=st0["device_bytes"],
                          resident_before=st0["resident"], resident_after=st1["resident"],
                          all_ok=bool((out["status"] == 0).all()))

@@ -498,6 +498,12 @@ typedef struct {
   uint64_t range_total;
   uint64_t update_batches, padded_ops, retrieval_groups, cleanups, refused;
   double wall_us;
+  /* where the time went: host microseconds spent admitting update groups,
+   * admitting retrieval groups, finishing range groups, completing groups,
+   * in cleanups, sleeping; device milliseconds of update and retrieval
+   * groups (from the stream reaching a group to its completion event) */
+  double host_admit_update_us, host_admit_retrieval_us, host_range_us, host_complete_us, host_cleanup_us,
+      host_sleep_us, gpu_update_ms, gpu_retrieval_ms;
 } lsm_trace_result;
 
 /* Creates the server and its dictionary.  Errors: LSM_ERR_ARG,

@@ -205,9 +205,12 @@ __global__ void __launch_bounds__(256) multi_partition(MultiArena ar) {
 // newer ranks) and run B (the next rank), ties to A.  B always sits in the
 // TMA slot area (separate key and value arrays); A is either there too (the
 // first step) or the (key, value) pair buffer X written by the step before.
-// Thread t produces outputs [E t, E t + E) after a merge-path search for its
-// first one (threads past the end idle); the outputs go to the swizzled pair
-// buffer Y, or stay in registers (kToRegs) when this is the last step.
+// Thread t produces `per` consecutive outputs from per * t after a
+// merge-path search for its first one (threads past the end idle); the
+// outputs go to the swizzled pair buffer Y, or stay in registers (kToRegs,
+// per = E) when this is the last step.  An intermediate step spreads its
+// m outputs over all threads (per = ceil(m / threads)), so the short early
+// steps of the chain cost one or two outputs per thread instead of E.
 // An exhausted run's head key becomes kSentinel, above every key, so the
 // choice of each output is a single comparison.
 constexpr uint32_t kSentinel = 0x80000000u;
@@ -217,7 +220,8 @@ __device__ __forceinline__ void merge_step(const uint32_t* __restrict__ sk, cons
                                            const uint2* __restrict__ X, uint2* __restrict__ Y, uint32_t aS,
                                            uint32_t nA, uint32_t bS, uint32_t nB, uint2 (&out)[E]) {
   const uint32_t m = nA + nB;
-  const uint32_t q0 = threadIdx.x * E;
+  const uint32_t per = kToRegs ? uint32_t(E) : (m + kThreads - 1) / kThreads;
+  const uint32_t q0 = threadIdx.x * per;
   if (q0 >= m) return;
   const uint32_t* xk = reinterpret_cast<const uint32_t*>(X);
   auto keyA = [&](uint32_t i) { return kAFromSlot ? sk[aS + i] : xk[2 * psw(i)]; };
@@ -241,7 +245,7 @@ __device__ __forceinline__ void merge_step(const uint32_t* __restrict__ sk, cons
   }
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    if (q0 + e < m) {
+    if ((kToRegs || uint32_t(e) < per) && q0 + e < m) {
       const bool take_a = ka <= kb;
       const uint2 o = take_a ? a : b;
       if (kToRegs) out[e] = o;

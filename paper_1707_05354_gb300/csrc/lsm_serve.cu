@@ -115,7 +115,7 @@ struct Slot {
   uint64_t* h_roff = nullptr;
   uint32_t *h_rk = nullptr, *h_rv = nullptr;
   uint64_t* h_total = nullptr;
-  cudaEvent_t ev_done = nullptr, ev_total = nullptr;
+  cudaEvent_t ev_done = nullptr, ev_total = nullptr, ev_start = nullptr;
 };
 
 enum Stage { kFree = 0, kRunning = 1, kRangePending = 2 };
@@ -188,6 +188,7 @@ void free_slot(Slot& s) {
     if (p) cudaFreeHost(p);
   if (s.ev_done) cudaEventDestroy(s.ev_done);
   if (s.ev_total) cudaEventDestroy(s.ev_total);
+  if (s.ev_start) cudaEventDestroy(s.ev_start);
   s = Slot{};
 }
 
@@ -228,8 +229,9 @@ cudaError_t alloc_slot(Slot& s, const lsm_server_config& c, uint32_t max_levels,
   if (e == cudaSuccess) e = halloc(&s.h_rv, R);
   if (e == cudaSuccess) e = halloc(&s.h_total, 8);
   if (e == cudaSuccess) e = cudaMemset(s.ctr, 0, 64);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreate(&s.ev_done);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_total, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreate(&s.ev_start);
   return e;
 }
 
@@ -298,10 +300,13 @@ struct Run {
       return k >= int(L);
     };
     if (full(r)) {
+      const double c0 = now_us(t0);
       LSM_TRY_S(lsm_cleanup(s->dict, s->st));
+      res->host_cleanup_us += now_us(t0) - c0;
       res->cleanups += 1;
       r = dict_r(s->dict);
     }
+    LSM_TRY(cudaEventRecord(sl.ev_start, s->st));
     if (full(r)) {
       g.refused = true;
       res->refused += g.reqs.size();
@@ -358,6 +363,7 @@ struct Run {
       pos = e;
     }
     const uint32_t nd = uint32_t(g.reqs.size());
+    LSM_TRY(cudaEventRecord(sl.ev_start, s->st));
     LSM_TRY(cudaMemcpyAsync(sl.d_start, sl.h_start, 8ull * nd, cudaMemcpyHostToDevice, s->st));
     LSM_TRY(cudaMemcpyAsync(sl.d_size, sl.h_size, 4ull * nd, cudaMemcpyHostToDevice, s->st));
     LSM_TRY(cudaMemcpyAsync(sl.d_dst, sl.h_dst, 8ull * nd, cudaMemcpyHostToDevice, s->st));
@@ -450,6 +456,12 @@ struct Run {
   // Results of a finished group to the caller's arrays; completion times.
   void complete(Group& g, double now) {
     Slot& sl = s->slots[g.slot];
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, sl.ev_start, sl.ev_done) == cudaSuccess) {
+      if (g.update) res->gpu_update_ms += ms;
+      else res->gpu_retrieval_ms += ms;
+    }
+    const double h0 = now_us(t0);
     for (uint64_t i : g.reqs) {
       res->done_us[i] = now;
       res->status[i] = g.refused ? LSM_ERR_BUDGET : LSM_OK;
@@ -494,6 +506,7 @@ struct Run {
     res->range_total += g.range_total;
     done += g.reqs.size();
     free_slots.push_back(g.slot);
+    res->host_complete_us += now_us(t0) - h0;
   }
 
   lsm_status poll(double now) {
@@ -505,7 +518,9 @@ struct Run {
         const cudaError_t e = cudaEventQuery(sl.ev_total);
         if (e == cudaErrorNotReady) break;
         LSM_TRY(e);
+        const double f0 = now_us(t0);
         LSM_TRY_S(finish_range(g));
+        res->host_range_us += now_us(t0) - f0;
       }
     }
     while (!inflight.empty()) {
@@ -545,15 +560,22 @@ struct Run {
         const int sl = free_slots.back();
         free_slots.pop_back();
         // the older front goes first
-        if (wu && (!wr || t->arrival_us[upd.front()] <= t->arrival_us[ret.front()]))
+        const double a0 = now_us(t0);
+        if (wu && (!wr || t->arrival_us[upd.front()] <= t->arrival_us[ret.front()])) {
           LSM_TRY_S(admit_updates(sl));
-        else
+          res->host_admit_update_us += now_us(t0) - a0;
+        } else {
           LSM_TRY_S(admit_retrievals(sl));
+          res->host_admit_retrieval_us += now_us(t0) - a0;
+        }
       }
       if (inflight.empty() && next < t->n && upd.empty() && ret.empty()) {
         // idle until the next arrival
         const double wait = t->arrival_us[next] - now_us(t0);
-        if (wait > 50.0) std::this_thread::sleep_for(std::chrono::microseconds(int64_t(wait - 20.0)));
+        if (wait > 50.0) {
+          std::this_thread::sleep_for(std::chrono::microseconds(int64_t(wait - 20.0)));
+          res->host_sleep_us += wait - 20.0;
+        }
       }
     }
     return LSM_OK;
@@ -691,6 +713,8 @@ lsm_status lsm_server_run(lsm_server_t* s, const lsm_trace* t, lsm_trace_result*
   DeviceGuard g(s->cfg.device);
   r->range_total = 0;
   r->update_batches = r->padded_ops = r->retrieval_groups = r->cleanups = r->refused = 0;
+  r->host_admit_update_us = r->host_admit_retrieval_us = r->host_range_us = r->host_complete_us = 0;
+  r->host_cleanup_us = r->host_sleep_us = r->gpu_update_ms = r->gpu_retrieval_ms = 0;
   Run run;
   run.s = s;
   run.t = t;

@@ -64,7 +64,11 @@ class TraceResult(ctypes.Structure):
                 ("range_cap", ctypes.c_uint64), ("range_total", ctypes.c_uint64),
                 ("update_batches", ctypes.c_uint64), ("padded_ops", ctypes.c_uint64),
                 ("retrieval_groups", ctypes.c_uint64), ("cleanups", ctypes.c_uint64), ("refused", ctypes.c_uint64),
-                ("wall_us", ctypes.c_double)]
+                ("wall_us", ctypes.c_double), ("host_admit_update_us", ctypes.c_double),
+                ("host_admit_retrieval_us", ctypes.c_double), ("host_range_us", ctypes.c_double),
+                ("host_complete_us", ctypes.c_double), ("host_cleanup_us", ctypes.c_double),
+                ("host_sleep_us", ctypes.c_double), ("gpu_update_ms", ctypes.c_double),
+                ("gpu_retrieval_ms", ctypes.c_double)]
 
 
 class ProfileEntry(ctypes.Structure):
@@ -662,5 +666,8 @@ class Server:
         lsm_server_run(self.h, tr, res)
         out.update(range_total=res.range_total, update_batches=res.update_batches, padded_ops=res.padded_ops,
                    retrieval_groups=res.retrieval_groups, cleanups=res.cleanups, refused=res.refused,
-                   wall_us=res.wall_us)
+                   wall_us=res.wall_us,
+                   time_split={k: getattr(res, k) for k in (
+                       "host_admit_update_us", "host_admit_retrieval_us", "host_range_us", "host_complete_us",
+                       "host_cleanup_us", "host_sleep_us", "gpu_update_ms", "gpu_retrieval_ms")})
         return out
