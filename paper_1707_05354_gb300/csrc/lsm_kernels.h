@@ -262,17 +262,19 @@ cudaError_t resolve_last_launch(const uint32_t* sk, const uint32_t* sv, uint32_t
                                 const uint32_t* vals, const uint8_t* del, uint32_t* out_k, uint32_t* out_v,
                                 uint8_t* out_d, cudaStream_t st);
 
-// Gathers windows of device-resident payload arrays: for request j,
-// dst[dst_off[j] + t] = src[start[j] + t], t < size[j] (up to two arrays at
-// once; src_b / dst_b may be null).
+// Gathers windows of device-resident payload arrays: request j (of nreq,
+// dst_off ascending) fills dst[dst_off[j] + t] = src[start[j] + t] for the
+// positions up to the next request's offset (or `total`); up to two arrays
+// at once (src_b / dst_b may be null).
 cudaError_t gather_windows_launch(const uint32_t* src_a, const uint32_t* src_b, const uint64_t* start,
-                                  const uint32_t* size, const uint64_t* dst_off, uint32_t nreq, uint32_t* dst_a,
+                                  const uint64_t* dst_off, uint32_t nreq, uint64_t total, uint32_t* dst_a,
                                   uint32_t* dst_b, cudaStream_t st);
 
-// Gathers whole update requests into a batch: keys from pool_k, values from
-// pool_v (0 for a delete request), the request's delete flag per op.
+// Gathers whole update requests into a batch the same way: keys from pool_k,
+// values from pool_v (0 for a delete request), the request's delete flag
+// per op.
 cudaError_t gather_update_launch(const uint32_t* pool_k, const uint32_t* pool_v, const uint64_t* start,
-                                 const uint32_t* size, const uint64_t* dst_off, const uint8_t* is_del, uint32_t nreq,
+                                 const uint64_t* dst_off, const uint8_t* is_del, uint32_t nreq, uint64_t total,
                                  uint32_t* out_k, uint32_t* out_v, uint8_t* out_d, cudaStream_t st);
 
 // ----------------------------------------------------------------- query ---

@@ -102,12 +102,10 @@ struct Slot {
   uint32_t *rk = nullptr, *rv = nullptr;
   uint32_t* ctr = nullptr;
   uint64_t* d_start = nullptr;
-  uint32_t* d_size = nullptr;
   uint64_t* d_dst = nullptr;
   uint8_t* d_flag = nullptr;
   // pinned host mirrors
   uint64_t* h_start = nullptr;
-  uint32_t* h_size = nullptr;
   uint64_t* h_dst = nullptr;
   uint8_t* h_flag = nullptr;
   uint32_t *h_val = nullptr, *h_cnt = nullptr;
@@ -164,7 +162,7 @@ cudaError_t halloc(T** p, uint64_t count) {
 uint64_t slot_bytes(const lsm_server_config& c, uint32_t max_levels, uint32_t max_req) {
   const uint64_t b = rup(c.b, 32) + 32, G = rup(c.group_keys, 32) + 32;
   return b * 9 + G * (4 + 4 + 1) + G * 12 + G * (4 + 4 + 4 + 8ull * max_levels) + (G + 1) * 8 +
-         (G / 2048 + 2) * 8 + uint64_t(c.range_cap) * 8 + uint64_t(max_req) * (8 + 4 + 8 + 1) + 64;
+         (G / 2048 + 2) * 8 + uint64_t(c.range_cap) * 8 + uint64_t(max_req) * (8 + 8 + 1) + 64;
 }
 
 // Device bytes of a dictionary with L levels of batch size b, as lsm_create
@@ -179,10 +177,10 @@ uint64_t dict_bytes(uint32_t b, uint32_t L) {
 
 void free_slot(Slot& s) {
   void* d[] = {s.uk, s.uv, s.ud, s.q,  s.val, s.found, s.c1, s.c2, s.cnt, s.r1, s.r2, s.rcnt, s.bounds,
-               s.roff, s.lb, s.rk, s.rv, s.ctr, s.d_start, s.d_size, s.d_dst, s.d_flag};
+               s.roff, s.lb, s.rk, s.rv, s.ctr, s.d_start, s.d_dst, s.d_flag};
   for (void* p : d)
     if (p) cudaFree(p);
-  void* h[] = {s.h_start, s.h_size, s.h_dst, s.h_flag, s.h_val, s.h_cnt, s.h_found, s.h_roff, s.h_rk, s.h_rv,
+  void* h[] = {s.h_start, s.h_dst, s.h_flag, s.h_val, s.h_cnt, s.h_found, s.h_roff, s.h_rk, s.h_rv,
                s.h_total};
   for (void* p : h)
     if (p) cudaFreeHost(p);
@@ -214,11 +212,9 @@ cudaError_t alloc_slot(Slot& s, const lsm_server_config& c, uint32_t max_levels,
   if (e == cudaSuccess) e = dalloc(&s.rv, R);
   if (e == cudaSuccess) e = dalloc(&s.ctr, 16);
   if (e == cudaSuccess) e = dalloc(&s.d_start, max_req);
-  if (e == cudaSuccess) e = dalloc(&s.d_size, max_req);
   if (e == cudaSuccess) e = dalloc(&s.d_dst, max_req);
   if (e == cudaSuccess) e = dalloc(&s.d_flag, max_req);
   if (e == cudaSuccess) e = halloc(&s.h_start, max_req);
-  if (e == cudaSuccess) e = halloc(&s.h_size, max_req);
   if (e == cudaSuccess) e = halloc(&s.h_dst, max_req);
   if (e == cudaSuccess) e = halloc(&s.h_flag, max_req);
   if (e == cudaSuccess) e = halloc(&s.h_val, G);
@@ -267,7 +263,6 @@ struct Run {
       const uint64_t i = reqs[j];
       const uint32_t d = first + uint32_t(j - a);
       sl.h_start[d] = t->start[i];
-      sl.h_size[d] = t->size[i];
       sl.h_dst[d] = keys;
       sl.h_flag[d] = t->kind[i] == LSM_REQ_DELETE ? 1 : 0;
       keys += t->size[i];
@@ -315,11 +310,10 @@ struct Run {
       const uint64_t n = describe(sl, g.reqs, 0, g.reqs.size(), 0);
       const uint32_t nd = uint32_t(g.reqs.size());
       LSM_TRY(cudaMemcpyAsync(sl.d_start, sl.h_start, 8ull * nd, cudaMemcpyHostToDevice, s->st));
-      LSM_TRY(cudaMemcpyAsync(sl.d_size, sl.h_size, 4ull * nd, cudaMemcpyHostToDevice, s->st));
       LSM_TRY(cudaMemcpyAsync(sl.d_dst, sl.h_dst, 8ull * nd, cudaMemcpyHostToDevice, s->st));
       LSM_TRY(cudaMemcpyAsync(sl.d_flag, sl.h_flag, nd, cudaMemcpyHostToDevice, s->st));
-      LSM_TRY(gather_update_launch(s->pool_a, s->pool_b, sl.d_start, sl.d_size, sl.d_dst, sl.d_flag, nd, sl.uk,
-                                   sl.uv, sl.ud, s->st));
+      LSM_TRY(gather_update_launch(s->pool_a, s->pool_b, sl.d_start, sl.d_dst, sl.d_flag, nd, n, sl.uk, sl.uv,
+                                   sl.ud, s->st));
       LSM_TRY_S(dict_update_ordered(s->dict, sl.uk, sl.uv, sl.ud, n, s->st, false));
       LSM_TRY(dict_record_applied(s->dict, sl.ev_done, s->st));
       res->update_batches += 1;
@@ -365,14 +359,13 @@ struct Run {
     const uint32_t nd = uint32_t(g.reqs.size());
     LSM_TRY(cudaEventRecord(sl.ev_start, s->st));
     LSM_TRY(cudaMemcpyAsync(sl.d_start, sl.h_start, 8ull * nd, cudaMemcpyHostToDevice, s->st));
-    LSM_TRY(cudaMemcpyAsync(sl.d_size, sl.h_size, 4ull * nd, cudaMemcpyHostToDevice, s->st));
     LSM_TRY(cudaMemcpyAsync(sl.d_dst, sl.h_dst, 8ull * nd, cudaMemcpyHostToDevice, s->st));
     LSM_TRY(dict_join(s->dict, s->st));
     g.ls = dict_levels(s->dict);
     const LevelSet& ls = g.ls;
     if (g.look.count) {
       const uint32_t f = g.look.first;
-      LSM_TRY(gather_windows_launch(s->pool_a, nullptr, sl.d_start + f, sl.d_size + f, sl.d_dst + f, g.look.count,
+      LSM_TRY(gather_windows_launch(s->pool_a, nullptr, sl.d_start + f, sl.d_dst + f, g.look.count, g.look.keys,
                                     sl.q, nullptr, s->st));
       if (ls.count) {
         LSM_TRY(lookup_launch(ls, sl.q, g.look.keys, sl.val, sl.found, s->st));
@@ -385,8 +378,8 @@ struct Run {
     }
     if (g.count.count) {
       const uint32_t f = g.count.first;
-      LSM_TRY(gather_windows_launch(s->pool_a, s->pool_c, sl.d_start + f, sl.d_size + f, sl.d_dst + f,
-                                    g.count.count, sl.c1, sl.c2, s->st));
+      LSM_TRY(gather_windows_launch(s->pool_a, s->pool_c, sl.d_start + f, sl.d_dst + f, g.count.count,
+                                    g.count.keys, sl.c1, sl.c2, s->st));
       if (ls.count)
         LSM_TRY(count_launch(ls, sl.c1, sl.c2, g.count.keys, sl.cnt, nullptr, s->st));
       else
@@ -396,8 +389,8 @@ struct Run {
     if (g.range.count) {
       const uint32_t f = g.range.first;
       const uint64_t nr = g.range.keys;
-      LSM_TRY(gather_windows_launch(s->pool_a, s->pool_c, sl.d_start + f, sl.d_size + f, sl.d_dst + f,
-                                    g.range.count, sl.r1, sl.r2, s->st));
+      LSM_TRY(gather_windows_launch(s->pool_a, s->pool_c, sl.d_start + f, sl.d_dst + f, g.range.count,
+                                    g.range.keys, sl.r1, sl.r2, s->st));
       if (ls.count) {
         LSM_TRY(count_launch(ls, sl.r1, sl.r2, nr, sl.rcnt, sl.bounds, s->st));
         LSM_TRY(scan_launch(sl.rcnt, nr, sl.roff, sl.lb, sl.ctr, dict_status_word(s->dict), s->st));

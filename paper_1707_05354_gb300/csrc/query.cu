@@ -41,6 +41,21 @@ __device__ __forceinline__ uint32_t level_lower_bound(const LevelSet& ls, int l,
   return lower_bound_kv(ls.keys[l], fence_at(f, fs, n, bin), fence_at(f, fs, n, bin + 1), target);
 }
 
+// Window [lower_bound(t1), lower_bound(t2)) of level l, t1 <= t2.  A narrow
+// interval usually has both bounds in one prefix-index bin: the bin's two
+// entries are then loaded once and the second search starts at the first
+// bound.
+__device__ __forceinline__ void level_window(const LevelSet& ls, int l, uint32_t t1, uint32_t t2, uint32_t& lo,
+                                             uint32_t& hi) {
+  const uint32_t* f = ls.fence[l];
+  const int fs = ls.fshift[l];
+  const uint32_t n = ls.n[l], b1 = fence_bin(t1, fs), b2 = fence_bin(t2, fs);
+  const uint32_t e1 = fence_at(f, fs, n, b1 + 1);
+  lo = lower_bound_kv(ls.keys[l], fence_at(f, fs, n, b1), e1, t1);
+  if (b2 == b1) hi = lower_bound_kv(ls.keys[l], lo, e1, t2);
+  else hi = lower_bound_kv(ls.keys[l], fence_at(f, fs, n, b2), fence_at(f, fs, n, b2 + 1), t2);
+}
+
 // Lookup of one key over the levels (newest first).
 __device__ __forceinline__ void lookup_one(const LevelSet& ls, uint32_t key, uint32_t& val, uint8_t& found) {
   val = 0;
@@ -192,10 +207,7 @@ __global__ void __launch_bounds__(kThreads) count_kernel(LevelSet ls, const uint
 #pragma unroll
     for (int l = 0; l < L; ++l) {
       lo[l] = hi[l] = 0;
-      if (l < ls.count && !empty) {
-        lo[l] = level_lower_bound(ls, l, a << 1);
-        hi[l] = level_lower_bound(ls, l, (z + 1u) << 1);
-      }
+      if (l < ls.count && !empty) level_window(ls, l, a << 1, (z + 1u) << 1, lo[l], hi[l]);
     }
     out_count[i] = merge_windows<false, L>(ls, lo, hi, nullptr, nullptr, 0);
     if (bounds) {

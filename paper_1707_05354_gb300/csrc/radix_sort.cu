@@ -65,6 +65,13 @@ struct Loader {
     v = (is_del || bad) ? 0u : __ldg(vals + s);
   }
 
+  // Leading positions of the reversed padded batch that are padding (copies
+  // of op n_in - 1); 0 outside the batch modes.
+  __device__ __forceinline__ uint32_t npad() const {
+    if (mode == kSortPairs || mode == kSortQueries) return 0u;
+    return uint64_t(n) > n_in ? uint32_t(uint64_t(n) - n_in) : 0u;
+  }
+
   // Key variable only (the histogram needs no values).
   __device__ __forceinline__ uint32_t load_key(uint32_t p, bool& bad) const {
     bad = false;
@@ -270,15 +277,22 @@ __global__ void __launch_bounds__(kThreads, LSM_SORT_MINB) sort_pass(Loader ld, 
 // ---------------------------------------------------------------------------
 constexpr int kBucketThreads = 512;
 constexpr int kBucketWarps = kBucketThreads / 32;
-constexpr int kBucketIPT = 11;
-constexpr uint32_t kBucketCap = kBucketThreads * kBucketIPT;  // 5632
+constexpr int kBucketIPT = 10;
+constexpr uint32_t kBucketCap = kBucketThreads * kBucketIPT;  // 5120
+constexpr uint32_t kSubBins = 4096;      // counting pass of the bucket fast path
+constexpr uint32_t kSubBinMax = 48;      // larger sub-bins take the pass-by-pass path
 constexpr int kMsdIPT = int(kMsdTile) / kThreads;              // 16
 static_assert(kMsdIPT * kThreads == int(kMsdTile), "tile");
 
+// The padding of a short batch (copies of its last op, the leading
+// positions of the reversed sequence) is neither counted per tile nor
+// scattered: it is one run of equal elements, added to its bucket's total
+// here and written by that bucket's sort at its sorted place.
 __global__ void __launch_bounds__(kThreads) msd_count(Loader ld, uint32_t* __restrict__ tilecnt,
                                                       uint32_t* __restrict__ ctl, uint32_t* status) {
   __shared__ uint32_t s_h[kRadix];
   const uint32_t tid = threadIdx.x, tile = blockIdx.x;
+  const uint32_t npad = ld.npad();
   s_h[tid] = 0;
   __syncthreads();
   uint32_t kv[kMsdIPT];
@@ -287,16 +301,22 @@ __global__ void __launch_bounds__(kThreads) msd_count(Loader ld, uint32_t* __res
   for (int j = 0; j < kMsdIPT; ++j) {
     const uint32_t p = tile * kMsdTile + j * kThreads + tid;
     bool bad = false;
-    kv[j] = p < ld.n ? ld.load_key(p, bad) : 0u;
+    kv[j] = (p < ld.n && p >= npad) ? ld.load_key(p, bad) : 0u;
     bad_any |= bad;
   }
 #pragma unroll
-  for (int j = 0; j < kMsdIPT; ++j)
-    if (tile * kMsdTile + j * kThreads + tid < ld.n) atomicAdd(&s_h[kv[j] >> 24], 1u);
+  for (int j = 0; j < kMsdIPT; ++j) {
+    const uint32_t p = tile * kMsdTile + j * kThreads + tid;
+    if (p < ld.n && p >= npad) atomicAdd(&s_h[kv[j] >> 24], 1u);
+  }
   const int any_bad = __syncthreads_or(bad_any);
   const uint32_t c = s_h[tid];
   tilecnt[tile * kRadix + tid] = c;
   if (c) atomicAdd(ctl + 3 * kRadix + tid, c);
+  if (tile == 0 && tid == 0 && npad) {
+    bool bad;
+    atomicAdd(ctl + 3 * kRadix + (ld.load_key(0, bad) >> 24), npad);
+  }
   if (any_bad && tid == 0 && status) *reinterpret_cast<volatile uint32_t*>(status) = kErrBadKey;
 }
 
@@ -331,7 +351,8 @@ __global__ void __launch_bounds__(kThreads) msd_offsets(const uint32_t* __restri
 template <int NT, int IPT>
 __device__ __forceinline__ void rank_block(const uint32_t (&kv)[IPT], uint32_t m, uint32_t base, int shift,
                                            uint32_t (&rank)[IPT], uint32_t (*s_whist)[kRadix],
-                                           uint32_t* s_excl, uint32_t* s_scan, uint32_t* digit_total) {
+                                           uint32_t* s_excl, uint32_t* s_scan, uint32_t* digit_total,
+                                           uint32_t lo = 0) {
   constexpr int NW = NT / 32;
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   for (uint32_t i = lane; i < kRadix; i += 32) s_whist[warp][i] = 0;
@@ -340,7 +361,7 @@ __device__ __forceinline__ void rank_block(const uint32_t (&kv)[IPT], uint32_t m
 #pragma unroll
   for (int j = 0; j < IPT; ++j) {
     const uint32_t p = base + j * 32 + lane;
-    const uint32_t d = (p < m) ? ((kv[j] >> shift) & 255u) : kNoDigit;
+    const uint32_t d = (p < m && p >= lo) ? ((kv[j] >> shift) & 255u) : kNoDigit;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const uint32_t before = __popc(peers & lt);
     const uint32_t cnt = (d != kNoDigit) ? s_whist[warp][d] : 0u;
@@ -376,25 +397,27 @@ __global__ void __launch_bounds__(kThreads) msd_scatter(Loader ld, const uint32_
   __shared__ uint32_t s_whist[kWarps][kRadix];
   __shared__ uint32_t s_excl[kRadix], s_gbase[kRadix], s_scan[kWarps];
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5, tile = blockIdx.x;
-  const uint32_t n = ld.n;
-  const uint32_t base = tile * kMsdTile + warp * (32 * kMsdIPT);
+  const uint32_t n = ld.n, npad = ld.npad();
+  const uint32_t t0 = tile * kMsdTile;
+  if (t0 + kMsdTile <= npad) return;  // whole CTA: padding only
+  const uint32_t base = t0 + warp * (32 * kMsdIPT);
   uint32_t kv[kMsdIPT], v[kMsdIPT], rank[kMsdIPT];
 #pragma unroll
   for (int j = 0; j < kMsdIPT; ++j) {
     const uint32_t p = base + j * 32 + lane;
     kv[j] = 0;
     v[j] = 0;
-    if (p < n) {
+    if (p < n && p >= npad) {
       bool bad;
       ld.load(p, kv[j], v[j], bad);
     }
   }
   s_gbase[tid] = tileoff[tile * kRadix + tid];
-  rank_block<kThreads, kMsdIPT>(kv, n, base, 24, rank, s_whist, s_excl, s_scan, nullptr);
+  rank_block<kThreads, kMsdIPT>(kv, n, base, 24, rank, s_whist, s_excl, s_scan, nullptr, npad);
 #pragma unroll
   for (int j = 0; j < kMsdIPT; ++j) {
     const uint32_t p = base + j * 32 + lane;
-    if (p < n) {
+    if (p < n && p >= npad) {
       const uint32_t d = kv[j] >> 24;
       const uint32_t pos = s_excl[d] + s_whist[warp][d] + rank[j];
       s_keys[pos] = kv[j];
@@ -402,8 +425,8 @@ __global__ void __launch_bounds__(kThreads) msd_scatter(Loader ld, const uint32_
     }
   }
   __syncthreads();
-  const uint32_t t0 = tile * kMsdTile;
-  const uint32_t tile_n = (n - t0) < kMsdTile ? (n - t0) : kMsdTile;
+  const uint32_t lo_t = t0 > npad ? t0 : npad, hi_t = (n - t0) < kMsdTile ? n : t0 + kMsdTile;
+  const uint32_t tile_n = hi_t > lo_t ? hi_t - lo_t : 0u;  // real elements of the tile
   for (uint32_t i = tid; i < tile_n; i += kThreads) {
     const uint32_t k = s_keys[i];
     const uint32_t d = k >> 24;
@@ -433,26 +456,150 @@ __device__ __forceinline__ void bucket_fence(const uint32_t* a, uint32_t m, uint
     fence[bin0 + i] = start + lower_bound_bin(a, m, bin0 + i, fshift);
 }
 
-// One bucket, one CTA of kBucketThreads: sorts tmp[start, start + m) by bits
-// 0 .. 8 npass - 1 of the key variable (stable 8-bit passes) into
-// out[start, start + m), and writes the prefix-index entries of the bucket's
-// bins [bin0, bin0 + nbins) when fence is given.  Up to kBucketCap elements
-// are sorted in shared memory (bsm: 4 kBucketCap words); a larger bucket
-// (heavy duplicate keys) is sorted in chunks through global memory, still
-// stably.
+// Writes the sorted run a/av[0, m) (shared memory) to out[start ..) with
+// the padding run inserted before the first element >= pad_kv, and the
+// prefix-index entries of bins [bin0, bin0 + nbins) of the result.
+__device__ __forceinline__ void bucket_write(const uint32_t* a, const uint32_t* av, uint32_t m, uint32_t* out_k,
+                                             uint32_t* out_v, uint32_t start, uint32_t pad, uint32_t pad_kv,
+                                             uint32_t pad_v, uint32_t* fence, int fshift, uint32_t bin0,
+                                             uint32_t nbins) {
+  uint32_t L = m;
+  if (pad) {
+    uint32_t lo = 0, hi = m;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (a[mid] < pad_kv) lo = mid + 1; else hi = mid;
+    }
+    L = lo;
+  }
+  for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+    const uint32_t dst = start + i + (i >= L ? pad : 0u);
+    out_k[dst] = a[i];
+    out_v[dst] = av[i];
+  }
+  for (uint32_t j = threadIdx.x; j < pad; j += blockDim.x) {
+    out_k[start + L + j] = pad_kv;
+    out_v[start + L + j] = pad_v;
+  }
+  if (fence) {
+    const uint32_t pad_bin = pad ? fence_bin(pad_kv, fshift) : 0xFFFFFFFFu;
+    for (uint32_t i = threadIdx.x; i < nbins; i += blockDim.x) {
+      const uint32_t bin = bin0 + i;
+      fence[bin] = start + lower_bound_bin(a, m, bin, fshift) + (bin > pad_bin ? pad : 0u);
+    }
+  }
+}
+
+// One bucket, one CTA of kBucketThreads: sorts tmp[start, start + m) stably
+// by the low `rest` bits of the key variable (the bits above are the
+// bucket's and equal) into out[start, start + m), and writes the
+// prefix-index entries of the bucket's bins [bin0, bin0 + nbins) when fence
+// is given.
+//   Fast path (bucket in shared memory, no sub-bin above kSubBinMax): one
+//   counting pass on the top 12 of the `rest` bits places every element in
+//   its sub-bin (about one element each for spread keys), at an arbitrary
+//   slot; each thread then insertion-sorts whole sub-bins by (key variable,
+//   index in the bucket), which is the stable order.
+//   Otherwise: ceil(rest / 8) stable 8-bit passes in shared memory, or, for
+//   a bucket above kBucketCap (heavy duplicate keys), the same passes in
+//   chunks through global memory.
+// A run of `pad` copies of (pad_kv, pad_v) (a short batch's padding, which
+// comes first among equal key variables in the stable order) is written at
+// its sorted place: the output holds m + pad elements.
+// bsm holds 4 kBucketCap words plus kBucketCap 16-bit indexes.
 __device__ __forceinline__ void bucket_body(uint32_t* tmp_k, uint32_t* tmp_v, uint32_t* out_k, uint32_t* out_v,
-                                            uint32_t start, uint32_t m, int npass, uint32_t* __restrict__ fence,
+                                            uint32_t start, uint32_t m, int rest, uint32_t* __restrict__ fence,
                                             int fshift, uint32_t bin0, uint32_t nbins, uint32_t* bsm,
-                                            uint32_t* s_scan) {
+                                            uint32_t* s_scan, uint32_t pad, uint32_t pad_kv, uint32_t pad_v) {
   __shared__ uint32_t s_whist[kBucketWarps][kRadix];
   __shared__ uint32_t s_excl[kRadix], s_run[kRadix], s_tot[kRadix];
+  __shared__ uint32_t s_max;
   uint32_t* ak = bsm;
   uint32_t* av = bsm + kBucketCap;
   uint32_t* bk = bsm + 2 * kBucketCap;
   uint32_t* bv = bsm + 3 * kBucketCap;
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint32_t wbase = warp * (32 * kBucketIPT);
+  const int npass = (rest + 7) / 8;
   uint32_t kv[kBucketIPT], v[kBucketIPT], rank[kBucketIPT];
+  static_assert(kSubBins == kBucketWarps * kRadix, "the counters reuse the per-warp histograms");
+
+  if (m <= kBucketCap && rest >= 12) {
+    uint32_t* cnt = &s_whist[0][0];
+    uint16_t* bi = reinterpret_cast<uint16_t*>(bsm + 4 * kBucketCap);
+    const int sh = rest - 12;
+    for (uint32_t i = tid; i < kSubBins; i += kBucketThreads) cnt[i] = 0u;
+    if (tid == 0) s_max = 0u;
+    __syncthreads();
+    uint32_t slot[kBucketIPT];
+#pragma unroll
+    for (int j = 0; j < kBucketIPT; ++j) {
+      const uint32_t i = tid + j * kBucketThreads;
+      if (i < m) {
+        const uint32_t k = tmp_k[start + i];
+        ak[i] = k;
+        av[i] = tmp_v[start + i];
+        slot[j] = atomicAdd(&cnt[(k >> sh) & (kSubBins - 1)], 1u);
+      }
+    }
+    __syncthreads();
+    // sub-bin starts: thread t owns counters [8 t, 8 t + 8)
+    constexpr int kPer = int(kSubBins) / kBucketThreads;
+    uint32_t c[kPer], sum = 0, mx = 0;
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+      c[e] = cnt[tid * kPer + e];
+      sum += c[e];
+      mx = max(mx, c[e]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0 && mx > kSubBinMax) atomicMax(&s_max, mx);
+    uint32_t all;
+    uint32_t run = block_excl_scan<kBucketThreads>(sum, s_scan, all);
+    if (s_max <= kSubBinMax) {  // uniform: s_max settled before the scan's barriers
+#pragma unroll
+      for (int e = 0; e < kPer; ++e) {
+        cnt[tid * kPer + e] = run;
+        run += c[e];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < kBucketIPT; ++j) {
+        const uint32_t i = tid + j * kBucketThreads;
+        if (i < m) {
+          const uint32_t k = ak[i];
+          const uint32_t pos = cnt[(k >> sh) & (kSubBins - 1)] + slot[j];
+          bk[pos] = k;
+          bv[pos] = av[i];
+          bi[pos] = uint16_t(i);
+        }
+      }
+      __syncthreads();
+      // every sub-bin sorted by (key variable, index): the stable order
+      for (uint32_t b = tid; b < kSubBins; b += kBucketThreads) {
+        const uint32_t s0 = cnt[b], s1 = b + 1 < kSubBins ? cnt[b + 1] : m;
+        for (uint32_t x = s0 + 1; x < s1; ++x) {
+          const uint32_t k = bk[x], vv = bv[x];
+          const uint16_t ix = bi[x];
+          uint32_t y = x;
+          while (y > s0 && (bk[y - 1] > k || (bk[y - 1] == k && bi[y - 1] > ix))) {
+            bk[y] = bk[y - 1];
+            bv[y] = bv[y - 1];
+            bi[y] = bi[y - 1];
+            --y;
+          }
+          bk[y] = k;
+          bv[y] = vv;
+          bi[y] = ix;
+        }
+      }
+      __syncthreads();
+      bucket_write(bk, bv, m, out_k, out_v, start, pad, pad_kv, pad_v, fence, fshift, bin0, nbins);
+      return;
+    }
+    __syncthreads();  // skewed bucket: the pass-by-pass path below reloads it
+  }
 
   if (m <= kBucketCap) {
     for (uint32_t i = tid; i < m; i += kBucketThreads) {
@@ -485,11 +632,7 @@ __device__ __forceinline__ void bucket_body(uint32_t* tmp_k, uint32_t* tmp_v, ui
       t = sk; sk = dk; dk = t;
       t = sv; sv = dv; dv = t;
     }
-    for (uint32_t i = tid; i < m; i += kBucketThreads) {
-      out_k[start + i] = sk[i];
-      out_v[start + i] = sv[i];
-    }
-    if (fence) bucket_fence(sk, m, start, bin0, nbins, fence, fshift);
+    bucket_write(sk, sv, m, out_k, out_v, start, pad, pad_kv, pad_v, fence, fshift, bin0, nbins);
     return;
   }
   // Chunked: npass stable passes over [start, start + m) through global
@@ -545,10 +688,45 @@ __device__ __forceinline__ void bucket_body(uint32_t* tmp_k, uint32_t* tmp_v, ui
     }
     __syncthreads();
   }
-  if (fence) bucket_fence(out_k + start, m, start, bin0, nbins, fence, fshift);
+  if (pad) {
+    // open a gap of `pad` before the first element >= pad_kv: move the tail
+    // up, a block at a time from the end (each block read before written)
+    __shared__ uint32_t s_L;
+    if (tid == 0) {
+      uint32_t lo = 0, hi = m;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (out_k[start + mid] < pad_kv) lo = mid + 1; else hi = mid;
+      }
+      s_L = lo;
+    }
+    __syncthreads();
+    const uint32_t L = s_L;
+    for (uint32_t e = m; e > L;) {
+      const uint32_t c = (e - L) < kBucketThreads ? (e - L) : kBucketThreads;
+      uint32_t k = 0, x = 0;
+      if (tid < c) {
+        k = out_k[start + e - c + tid];
+        x = out_v[start + e - c + tid];
+      }
+      __syncthreads();
+      if (tid < c) {
+        out_k[start + e - c + tid + pad] = k;
+        out_v[start + e - c + tid + pad] = x;
+      }
+      __syncthreads();
+      e -= c;
+    }
+    for (uint32_t j = tid; j < pad; j += kBucketThreads) {
+      out_k[start + L + j] = pad_kv;
+      out_v[start + L + j] = pad_v;
+    }
+    __syncthreads();
+  }
+  if (fence) bucket_fence(out_k + start, m + pad, start, bin0, nbins, fence, fshift);
 }
 
-__global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort(uint32_t* __restrict__ tmp_k,
+__global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort(Loader ld, uint32_t* __restrict__ tmp_k,
                                                               uint32_t* __restrict__ tmp_v,
                                                               uint32_t* __restrict__ out_k,
                                                               uint32_t* __restrict__ out_v,
@@ -562,9 +740,17 @@ __global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort(uint32_t* __res
   if (d == 0)
     for (uint32_t i = tid; i < uint32_t(kSortCtlWords); i += kBucketThreads) next_ctl[i] = 0u;
   const uint32_t start = bucket_start<kBucketThreads>(ctl, d, s_scan);
-  const uint32_t m = ctl[3 * kRadix + d];
+  uint32_t m = ctl[3 * kRadix + d];
+  // a short batch's padding: one run in the bucket of its key variable
+  uint32_t pad = ld.npad(), pad_kv = 0, pad_v = 0;
+  if (pad) {
+    bool bad;
+    ld.load(0, pad_kv, pad_v, bad);
+    if ((pad_kv >> 24) == d) m -= pad; else pad = 0;
+  }
   const uint32_t per = fence ? 1u << (24 - fshift) : 0u;  // bins per bucket
-  bucket_body(tmp_k, tmp_v, out_k, out_v, start, m, 3, fence, fshift, d * per, per, bsm, s_scan);
+  bucket_body(tmp_k, tmp_v, out_k, out_v, start, m, 24, fence, fshift, d * per, per, bsm, s_scan, pad, pad_kv,
+              pad_v);
   // the bucket sort writes every entry: the populated range is all bins
   if (fence && d == kRadix - 1 && tid == 0) {
     fence[fence_bins(fshift)] = n;
@@ -747,10 +933,9 @@ __global__ void __launch_bounds__(kBucketThreads, 2) mseg_bucket(MultiArena ar) 
   }
   const int fs = d.fshift0;
   const int rest = 32 - int(d.msd_bits);              // bits below the bucket bits
-  const int npass = (rest + 7) / 8;
   const uint32_t per = 1u << (rest - fs);             // bins per bucket
-  bucket_body(ar.tkeys + d.boff, ar.tvals + d.boff, ok, ov, start, m, npass, of, fs, bucket * per, per, bsm,
-              s_scan);
+  bucket_body(ar.tkeys + d.boff, ar.tvals + d.boff, ok, ov, start, m, rest, of, fs, bucket * per, per, bsm,
+              s_scan, 0u, 0u, 0u);
   if (bucket == (1u << d.msd_bits) - 1 && threadIdx.x == 0) {
     const uint32_t nb = fence_bins(fs);
     of[nb] = d.b;
@@ -761,7 +946,7 @@ __global__ void __launch_bounds__(kBucketThreads, 2) mseg_bucket(MultiArena ar) 
 
 }  // namespace
 
-constexpr size_t kBucketSmem = 4 * size_t(kBucketCap) * sizeof(uint32_t);
+constexpr size_t kBucketSmem = 4 * size_t(kBucketCap) * sizeof(uint32_t) + size_t(kBucketCap) * sizeof(uint16_t);
 
 cudaError_t bucket_sort_launch(const SortArgs& a, SortWorkspace& ws, cudaStream_t st, uint32_t* status,
                                cudaEvent_t ev) {
@@ -789,7 +974,7 @@ cudaError_t bucket_sort_launch(const SortArgs& a, SortWorkspace& ws, cudaStream_
   msd_scatter<<<ntiles, kThreads, 0, st>>>(ld, tileoff, a.tmp_keys, a.tmp_vals);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   count_launches(1);
-  bucket_sort<<<kRadix, kBucketThreads, kBucketSmem, st>>>(a.tmp_keys, a.tmp_vals, a.out_keys, a.out_vals,
+  bucket_sort<<<kRadix, kBucketThreads, kBucketSmem, st>>>(ld, a.tmp_keys, a.tmp_vals, a.out_keys, a.out_vals,
                                                           ctl, a.n, a.fence, a.fshift, next);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   ws.flip ^= 1;

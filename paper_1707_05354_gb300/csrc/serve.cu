@@ -38,54 +38,63 @@ __global__ void __launch_bounds__(256) resolve_last(const uint32_t* __restrict__
   }
 }
 
-// One CTA per request window.
+// Request j of the n descriptors owns output positions [dst_off[j],
+// dst_off[j] + size[j]); dst_off ascending.  Largest j with dst_off[j] <= g.
+__device__ __forceinline__ uint32_t owner(const uint64_t* __restrict__ dst_off, uint32_t n, uint64_t g) {
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(dst_off + mid) <= g) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// One thread per output element (requests are found by bisection of the
+// output offsets), so a few large windows still spread over the GPU.
 __global__ void __launch_bounds__(256) gather_windows(const uint32_t* __restrict__ src_a,
                                                       const uint32_t* __restrict__ src_b,
                                                       const uint64_t* __restrict__ start,
-                                                      const uint32_t* __restrict__ size,
                                                       const uint64_t* __restrict__ dst_off, uint32_t nreq,
-                                                      uint32_t* __restrict__ dst_a, uint32_t* __restrict__ dst_b) {
-  for (uint32_t j = blockIdx.x; j < nreq; j += gridDim.x) {
-    const uint64_t s = __ldg(start + j), d = __ldg(dst_off + j);
-    const uint32_t m = __ldg(size + j);
-    for (uint32_t t = threadIdx.x; t < m; t += 256u) {
-      dst_a[d + t] = __ldg(src_a + s + t);
-      if (src_b) dst_b[d + t] = __ldg(src_b + s + t);
-    }
+                                                      uint64_t total, uint32_t* __restrict__ dst_a,
+                                                      uint32_t* __restrict__ dst_b) {
+  for (uint64_t g = blockIdx.x * 256ull + threadIdx.x; g < total; g += uint64_t(gridDim.x) * 256ull) {
+    const uint32_t j = owner(dst_off, nreq, g);
+    const uint64_t s = __ldg(start + j) + (g - __ldg(dst_off + j));
+    dst_a[g] = __ldg(src_a + s);
+    if (src_b) dst_b[g] = __ldg(src_b + s);
   }
 }
 
-// One CTA per update request: its keys, its values (0 for a delete) and
-// its delete flag, at its offset in the batch.
+// Update requests into a batch: keys from pool_k, values from pool_v (0 for
+// a delete request), the request's delete flag per op.
 __global__ void __launch_bounds__(256) gather_update(const uint32_t* __restrict__ pool_k,
                                                      const uint32_t* __restrict__ pool_v,
                                                      const uint64_t* __restrict__ start,
-                                                     const uint32_t* __restrict__ size,
                                                      const uint64_t* __restrict__ dst_off,
                                                      const uint8_t* __restrict__ is_del, uint32_t nreq,
-                                                     uint32_t* __restrict__ out_k, uint32_t* __restrict__ out_v,
-                                                     uint8_t* __restrict__ out_d) {
-  for (uint32_t j = blockIdx.x; j < nreq; j += gridDim.x) {
-    const uint64_t s = __ldg(start + j), d = __ldg(dst_off + j);
-    const uint32_t m = __ldg(size + j);
+                                                     uint64_t total, uint32_t* __restrict__ out_k,
+                                                     uint32_t* __restrict__ out_v, uint8_t* __restrict__ out_d) {
+  for (uint64_t g = blockIdx.x * 256ull + threadIdx.x; g < total; g += uint64_t(gridDim.x) * 256ull) {
+    const uint32_t j = owner(dst_off, nreq, g);
+    const uint64_t s = __ldg(start + j) + (g - __ldg(dst_off + j));
     const uint8_t del = __ldg(is_del + j);
-    for (uint32_t t = threadIdx.x; t < m; t += 256u) {
-      out_k[d + t] = __ldg(pool_k + s + t);
-      out_v[d + t] = del ? 0u : __ldg(pool_v + s + t);
-      out_d[d + t] = del;
-    }
+    out_k[g] = __ldg(pool_k + s);
+    out_v[g] = del ? 0u : __ldg(pool_v + s);
+    out_d[g] = del;
   }
 }
 
 }  // namespace
 
 cudaError_t gather_update_launch(const uint32_t* pool_k, const uint32_t* pool_v, const uint64_t* start,
-                                 const uint32_t* size, const uint64_t* dst_off, const uint8_t* is_del, uint32_t nreq,
+                                 const uint64_t* dst_off, const uint8_t* is_del, uint32_t nreq, uint64_t total,
                                  uint32_t* out_k, uint32_t* out_v, uint8_t* out_d, cudaStream_t st) {
-  if (nreq == 0) return cudaSuccess;
-  const uint32_t blocks = nreq < 152 * 16 ? nreq : 152 * 16;
+  if (nreq == 0 || total == 0) return cudaSuccess;
+  uint64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
   count_launches(1);
-  gather_update<<<blocks, 256, 0, st>>>(pool_k, pool_v, start, size, dst_off, is_del, nreq, out_k, out_v, out_d);
+  gather_update<<<unsigned(blocks), 256, 0, st>>>(pool_k, pool_v, start, dst_off, is_del, nreq, total, out_k, out_v,
+                                                  out_d);
   return cudaGetLastError();
 }
 
@@ -101,12 +110,13 @@ cudaError_t resolve_last_launch(const uint32_t* sk, const uint32_t* sv, uint32_t
 }
 
 cudaError_t gather_windows_launch(const uint32_t* src_a, const uint32_t* src_b, const uint64_t* start,
-                                  const uint32_t* size, const uint64_t* dst_off, uint32_t nreq, uint32_t* dst_a,
+                                  const uint64_t* dst_off, uint32_t nreq, uint64_t total, uint32_t* dst_a,
                                   uint32_t* dst_b, cudaStream_t st) {
-  if (nreq == 0) return cudaSuccess;
-  const uint32_t blocks = nreq < 152 * 16 ? nreq : 152 * 16;
+  if (nreq == 0 || total == 0) return cudaSuccess;
+  uint64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
   count_launches(1);
-  gather_windows<<<blocks, 256, 0, st>>>(src_a, src_b, start, size, dst_off, nreq, dst_a, dst_b);
+  gather_windows<<<unsigned(blocks), 256, 0, st>>>(src_a, src_b, start, dst_off, nreq, total, dst_a, dst_b);
   return cudaGetLastError();
 }
 

@@ -107,6 +107,36 @@ def test_sort_pairs_matches_stable_sort(g, n):
     np.testing.assert_array_equal(u32(vo), vals[order])
 
 
+@pytest.mark.parametrize("dist", ["dup4", "sub_bin_skew", "one_bucket_spread"])
+def test_sort_pairs_key_distributions(g, dist):
+    """Stability and order for the bucket sort's paths: keys that repeat
+    about 4 times each (ties inside the counting pass's sub-bins), buckets
+    whose keys crowd a few sub-bins (the pass-by-pass path), and every key in
+    one top-byte bucket of at most 5120 elements spread over its low bits."""
+    n = 1 << 20
+    rng = np.random.default_rng(7)
+    if dist == "dup4":
+        keys = (rng.integers(0, 1 << 18, size=n).astype(np.uint64) * np.uint64(16411) % np.uint64(1 << 32))
+        keys = keys.astype(np.uint32)
+    elif dist == "sub_bin_skew":
+        # random top byte and low 12 bits, few distinct values in bits 12..23
+        top = rng.integers(0, 256, size=n).astype(np.uint32) << np.uint32(24)
+        mid = (rng.integers(0, 3, size=n).astype(np.uint32) * np.uint32(1111)) << np.uint32(12)
+        keys = top | mid | rng.integers(0, 4096, size=n).astype(np.uint32)
+    else:
+        n = 5000
+        keys = (np.uint32(0x5A) << np.uint32(24)) | rng.integers(0, 1 << 24, size=n).astype(np.uint32)
+    lsm = g.LSM(n, n)
+    vals = np.arange(n, dtype=np.uint32)
+    kd, vd = g.as_device_u32(keys, 0), g.as_device_u32(vals, 0)
+    ko, vo = torch.empty_like(kd), torch.empty_like(vd)
+    g.lsm_sort_pairs(lsm.h, kd.data_ptr(), vd.data_ptr(), ko.data_ptr(), vo.data_ptr(), n,
+                     torch.cuda.current_stream().cuda_stream)
+    order = np.argsort(keys, kind="stable")
+    np.testing.assert_array_equal(u32(ko), keys[order])
+    np.testing.assert_array_equal(u32(vo), vals[order])
+
+
 # ------------------------------------------------------ configuration tiny --
 def test_tiny_configuration_bit_exact(g):
     cfg = workload.tiny()
@@ -338,3 +368,46 @@ def test_ordered_update_batches(g, b, key_space, nb):
     k1 = np.zeros(1, np.uint32)
     k2 = np.full(1, key_space, np.uint32)
     np.testing.assert_array_equal(u32(lsm.count(k1, k2)), o1.count(k1, k2))
+
+
+@pytest.mark.parametrize("case", ["few", "one_bucket_chunked", "almost_full", "pad_key_smallest"])
+def test_short_batch_padding(g, case):
+    """A short batch is padded with copies of its last op (one run of equal
+    key variables, placed before the real elements of that key variable):
+    the bucket sort writes the run at its place without sorting it.  Cases:
+    a handful of ops; a bucket of real elements too large for shared memory
+    (the run is opened inside the chunked path's output); b - 1 ops; the
+    padded key smaller than every other key."""
+    b = 1 << 16
+    rng = np.random.default_rng(len(case))
+    lsm = g.LSM(b, 8 * b)
+    s = oracle.StructuralOracle(b)
+    o1 = oracle.MapOracle(b)
+    seen = []
+    for t in range(5):
+        if case == "few":
+            n = 5
+            keys = rng.integers(0, 1 << 31, size=n).astype(np.uint32) % np.uint32(0x7FFFFFFE)
+        elif case == "one_bucket_chunked":
+            n = 6000
+            keys = (np.uint32(0x21) << np.uint32(23)) | rng.integers(0, 1 << 12, size=n).astype(np.uint32)
+        elif case == "almost_full":
+            n = b - 1
+            keys = rng.integers(0, 0x7FFFFFFE, size=n).astype(np.uint32)
+        else:
+            n = 300
+            keys = rng.integers(1000, 0x7FFFFFFE, size=n).astype(np.uint32)
+            keys[-1] = np.uint32(t)     # the padded op has the smallest key
+        vals = rng.integers(0, 1 << 32, size=n, dtype=np.uint64).astype(np.uint32)
+        dele = (rng.random(n) < 0.3).astype(np.uint8)
+        lsm.update(keys, vals, dele)
+        s.call("update", keys, vals, dele)
+        o1.call("update", keys, vals, dele)
+        seen.append(keys)
+        assert_levels(lsm, s)
+    q = np.concatenate(seen + [rng.integers(0, 0x7FFFFFFE, size=1000).astype(np.uint32)])
+    val, found = lsm.lookup(q)
+    ev, ef = o1.lookup(q)
+    np.testing.assert_array_equal(found.cpu().numpy(), ef)
+    np.testing.assert_array_equal(u32(val), ev)
+    assert lsm.device_errors() == 0
