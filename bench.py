@@ -57,6 +57,8 @@ def parse_args():
     p.add_argument("--rate", type=float, default=3.0e5, help="serving: arrivals per second")
     p.add_argument("--flush-us", type=float, default=1000.0, help="serving: longest wait of a partial batch")
     p.add_argument("--preload-log2", type=int, default=28, help="serving: dictionary size before the stream")
+    p.add_argument("--preload-batches", type=int, default=0,
+                   help="serving: preload this many batches of b instead of 2^preload-log2 keys")
     p.add_argument("--budget-gb", type=float, default=64.0, help="serving: HBM admission budget (GiB)")
     p.add_argument("--instances", type=int, default=256)
     p.add_argument("--rounds", type=int, default=32)
@@ -707,12 +709,19 @@ def run_serving(args):
     wk, wa, ws, wz = workload.serving_trace(seed=workload.SERVING_SEED + 1, n_req=max(1000, args.requests // 100),
                                             rate=args.rate, pool_n=pool_n)
     keys_total = int(size.astype(np.int64).sum())
-    # preload: uniform keys drawn on the device (setup, not timed)
-    gen = torch.Generator(device=dev)
-    gen.manual_seed(workload.SERVING_SEED)
-    npre = 1 << args.preload_log2
-    pre_k = torch.randint(0, (1 << 31) - 1, (npre,), device=dev, dtype=torch.int64, generator=gen).to(torch.int32)
-    pre_v = torch.randint(0, 1 << 31, (npre,), device=dev, dtype=torch.int64, generator=gen).to(torch.int32)
+    # preload: uniform keys drawn on the device (setup, not timed), in chunks
+    npre = args.preload_batches * b if args.preload_batches else 1 << args.preload_log2
+
+    def preload(srv):
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(workload.SERVING_SEED)
+        done_ = 0
+        while done_ < npre:
+            m = min(1 << 26, npre - done_)
+            k = torch.randint(0, (1 << 31) - 1, (m,), device=dev, dtype=torch.int64, generator=gen).to(torch.int32)
+            v = torch.randint(0, 1 << 31, (m,), device=dev, dtype=torch.int64, generator=gen).to(torch.int32)
+            srv.preload(k, v)
+            done_ += m
     budget = int(args.budget_gb * (1 << 30))
     res = {}
     clocks = None
@@ -721,7 +730,7 @@ def run_serving(args):
         srv = G.Server(b, budget, flush_us=args.flush_us, group_keys=1 << 20, slots=3, range_cap=1 << 25,
                        policy=policy, device=local)
         srv.set_pool(pa, pb, pc)
-        srv.preload(pre_k, pre_v)
+        preload(srv)
         for _ in range(max(1, args.warmup)):
             srv.run(wk, wa, ws, wz)       # warm-up: a short trace of the same mix
         st0 = srv.stats()
@@ -758,8 +767,8 @@ def run_serving(args):
             "steps": 1, "warmup": max(1, args.warmup), "ms_per_step": 1000 * c["wall_s"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic (seeded Poisson arrivals, kinds 40/10/35/5/10 %%, sizes round(2^U[0,16]) keys; "
-                    "payload windows of device-resident pools of 2^26 uniform keys; preload 2^%d uniform keys)"
-                    % args.preload_log2,
+                    "payload windows of device-resident pools of 2^26 uniform keys; preload %d uniform keys)"
+                    % npre,
             "config": {"workload": "serving: %d requests at %.0f/s (%.2f s of arrivals, %d keys), b=2^%d, "
                                    "%.0f GiB HBM budget, flush %.0f us, 3 slots"
                                    % (len(kind), args.rate, span_s, keys_total, args.b_log2, args.budget_gb,

@@ -515,11 +515,13 @@ void lsm_server_destroy(lsm_server_t* s);
  * while the server runs): d_a = keys of updates and lookups and the lower
  * bounds of count/range intervals, d_b = insert values, d_c = upper bounds.
  * Every key of d_a must be < 2^31 - 1 (checked here once, so that update
- * batches need no per-batch check): else LSM_ERR_KEY_RANGE. */
+ * batches need no per-batch check): else LSM_ERR_KEY_RANGE.  Waits for all
+ * device work first, so the pools may be written on any stream. */
 lsm_status lsm_server_set_pool(lsm_server_t* s, const uint32_t* d_a, const uint32_t* d_b, const uint32_t* d_c,
                                uint64_t n);
 
-/* Inserts n pairs into the dictionary before a run (synchronous). */
+/* Inserts n pairs into the dictionary before a run (synchronous; waits for
+ * all device work first, so the pairs may come from any stream). */
 lsm_status lsm_server_preload(lsm_server_t* s, const uint32_t* d_keys, const uint32_t* d_vals, uint64_t n);
 
 /* Replays the trace in real time (blocking until every request completed). */

@@ -135,6 +135,8 @@ __device__ __forceinline__ uint32_t corank_lane(bool act, const uint32_t* a, con
 
 __global__ void __launch_bounds__(256) fold_partition(FoldSources src, uint64_t total, uint32_t ntiles,
                                                       uint32_t tile, uint32_t* __restrict__ part) {
+  pdl_trigger();
+  pdl_wait();
   const uint32_t t = (blockIdx.x * 256u + threadIdx.x) >> 5;
   if (t > ntiles) return;  // whole warp leaves together
   const uint32_t lane = lane_id();
@@ -534,6 +536,8 @@ __global__ void __launch_bounds__(kThreads) fold_merge(FoldSources src, uint64_t
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ MergeShared sh;
   __shared__ uint32_t s_tile;
+  pdl_trigger();
+  pdl_wait();
   if (threadIdx.x == 0) {
     s_tile = kCleanup ? atomicAdd(tile_ctr, 1u) : blockIdx.x;
     mbar_init(&s_bar, 1);
@@ -725,8 +729,8 @@ cudaError_t fold_partition_launch(const FoldArgs& a, cudaStream_t st) {
   if (ntiles == 0) return cudaSuccess;
   const uint64_t pblocks = ((ntiles + 1) * 32 + 255) / 256;
   count_launches(1);
-  fold_partition<<<unsigned(pblocks), 256, 0, st>>>(a.src, a.total, uint32_t(ntiles), kFoldTile, a.part);
-  return cudaGetLastError();
+  return launch_pdl(fold_partition, dim3(unsigned(pblocks)), dim3(256), 0, st, a.src, a.total, uint32_t(ntiles),
+                    uint32_t(kFoldTile), a.part);
 }
 
 cudaError_t fold_merge_launch(const FoldArgs& a, cudaStream_t st) {
@@ -752,9 +756,10 @@ cudaError_t fold_merge_launch(const FoldArgs& a, cudaStream_t st) {
                                                               a.out_count, uint32_t(ntiles));
   } else {
     count_launches(1);
-    fold_merge<false><<<unsigned(ntiles), kThreads, smem, st>>>(a.src, a.total, a.part, a.out_keys, a.out_vals,
-                                                               a.out_fence, a.out_fshift, a.status, nullptr,
-                                                               nullptr, nullptr, uint32_t(ntiles));
+    return launch_pdl(fold_merge<false>, dim3(unsigned(ntiles)), dim3(kThreads), smem, st, a.src, a.total,
+                      static_cast<const uint32_t*>(a.part), a.out_keys, a.out_vals, a.out_fence, a.out_fshift,
+                      a.status, static_cast<uint64_t*>(nullptr), static_cast<uint32_t*>(nullptr),
+                      static_cast<uint64_t*>(nullptr), uint32_t(ntiles));
   }
   return cudaGetLastError();
 }

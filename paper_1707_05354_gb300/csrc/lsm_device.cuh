@@ -10,6 +10,15 @@ namespace gpulsm {
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// launch_pdl may be scheduled while the kernel before it in the stream is
+// still running; pdl_wait() blocks until that kernel has completed and its
+// writes are visible (a no-op for a kernel launched without the attribute).
+// pdl_trigger() lets the next kernel's blocks be scheduled once every block
+// of this grid has executed it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

@@ -7,6 +7,25 @@
 
 namespace gpulsm {
 
+// Launches `kernel` with programmatic stream serialization: its blocks may be
+// scheduled while the previous kernel in the stream finishes; the kernel
+// itself calls pdl_wait() before touching anything that kernel wrote.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Number of kernels this library has launched (all handles); read through
 // LSM_OPT_KERNEL_LAUNCHES.  Incremented by every launcher below.
 void count_launches(uint64_t n);
@@ -299,17 +318,22 @@ cudaError_t lookup_sorted_launch(const LevelSet& ls, const uint32_t* sq, const u
                                  uint64_t nq, uint32_t* val, uint8_t* found, cudaStream_t st);
 
 // Count per query; when `bounds` is not null also stores, per query and
-// level, the window [lo, hi) (2 * count words per query).
+// level, the window [lo, hi) (2 * count words per query).  With `perm`, the
+// queries come sorted by k1 (k1 = sorted lower bounds, perm = their
+// positions; k2 stays in query order) and results go to position perm[i].
 cudaError_t count_launch(const LevelSet& ls, const uint32_t* k1, const uint32_t* k2,
-                         uint64_t nq, uint32_t* count, uint32_t* bounds, cudaStream_t st);
+                         uint64_t nq, uint32_t* count, uint32_t* bounds, cudaStream_t st,
+                         const uint32_t* perm = nullptr);
 
 // Exclusive scan of n u32 into n + 1 u64 (out[n] = total).
 cudaError_t scan_launch(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* lookback,
                         uint32_t* tile_ctr, uint32_t* status, cudaStream_t st);
 inline uint64_t scan_tiles(uint64_t n) { return (n + 2047) / 2048; }
 
+// Range output from the windows of count_launch; with `perm`, thread i
+// serves query perm[i] (neighbouring threads, neighbouring windows).
 cudaError_t range_emit_launch(const LevelSet& ls, uint64_t nq, const uint32_t* bounds,
                               const uint64_t* offsets, uint32_t* keys, uint32_t* vals,
-                              cudaStream_t st);
+                              cudaStream_t st, const uint32_t* perm = nullptr);
 
 }  // namespace gpulsm

@@ -114,7 +114,19 @@ struct Slot {
   uint32_t *h_rk = nullptr, *h_rv = nullptr;
   uint64_t* h_total = nullptr;
   cudaEvent_t ev_done = nullptr, ev_total = nullptr, ev_start = nullptr;
+  // sorting the queries of a large group (by key, with their positions):
+  // set A for lookups and counts, set B for ranges (its positions are read
+  // again by the emit)
+  SortWorkspace sws{};
+  uint32_t *sort_ctl = nullptr, *sort_tilecnt = nullptr;
+  uint32_t* sa[4] = {};  // sorted keys, positions, two scratch arrays
+  uint32_t* sb[4] = {};
 };
+
+// Groups of at least this many keys of one kind are processed in key order
+// (a sort first): neighbouring threads then search neighbouring parts of
+// every level, which matters once the levels span many gigabytes.
+constexpr uint64_t kSortQueriesFrom = 1u << 15;
 
 enum Stage { kFree = 0, kRunning = 1, kRangePending = 2 };
 
@@ -128,6 +140,7 @@ struct Group {
   uint64_t range_total = 0;
   LevelSet ls{};               // the state the range counts saw
   bool refused = false;
+  bool range_sorted = false;   // the range intervals were processed in key order
   // range output larger than the slot's buffer: a buffer of its own
   uint32_t *big_k = nullptr, *big_v = nullptr, *h_big_k = nullptr, *h_big_v = nullptr;
 };
@@ -162,7 +175,8 @@ cudaError_t halloc(T** p, uint64_t count) {
 uint64_t slot_bytes(const lsm_server_config& c, uint32_t max_levels, uint32_t max_req) {
   const uint64_t b = rup(c.b, 32) + 32, G = rup(c.group_keys, 32) + 32;
   return b * 9 + G * (4 + 4 + 1) + G * 12 + G * (4 + 4 + 4 + 8ull * max_levels) + (G + 1) * 8 +
-         (G / 2048 + 2) * 8 + uint64_t(c.range_cap) * 8 + uint64_t(max_req) * (8 + 8 + 1) + 64;
+         (G / 2048 + 2) * 8 + uint64_t(c.range_cap) * 8 + uint64_t(max_req) * (8 + 8 + 1) + 8 * 4 * G +
+         4ull * kMsdTileWords + 64;
 }
 
 // Device bytes of a dictionary with L levels of batch size b, as lsm_create
@@ -187,6 +201,12 @@ void free_slot(Slot& s) {
   if (s.ev_done) cudaEventDestroy(s.ev_done);
   if (s.ev_total) cudaEventDestroy(s.ev_total);
   if (s.ev_start) cudaEventDestroy(s.ev_start);
+  if (s.sort_ctl) cudaFree(s.sort_ctl);
+  if (s.sort_tilecnt) cudaFree(s.sort_tilecnt);
+  for (int i = 0; i < 4; ++i) {
+    if (s.sa[i]) cudaFree(s.sa[i]);
+    if (s.sb[i]) cudaFree(s.sb[i]);
+  }
   s = Slot{};
 }
 
@@ -228,6 +248,16 @@ cudaError_t alloc_slot(Slot& s, const lsm_server_config& c, uint32_t max_levels,
   if (e == cudaSuccess) e = cudaEventCreate(&s.ev_done);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_total, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreate(&s.ev_start);
+  if (e == cudaSuccess) e = dalloc(&s.sort_ctl, 2 * kSortCtlWords);
+  if (e == cudaSuccess) e = cudaMemset(s.sort_ctl, 0, 4ull * 2 * kSortCtlWords);
+  if (e == cudaSuccess) e = dalloc(&s.sort_tilecnt, kMsdTileWords);
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+    e = dalloc(&s.sa[i], G);
+    if (e == cudaSuccess) e = dalloc(&s.sb[i], G);
+  }
+  s.sws.ctl = s.sort_ctl;
+  s.sws.flip = 0;
+  s.sws.tilecnt = s.sort_tilecnt;
   return e;
 }
 
@@ -367,7 +397,12 @@ struct Run {
       const uint32_t f = g.look.first;
       LSM_TRY(gather_windows_launch(s->pool_a, nullptr, sl.d_start + f, sl.d_dst + f, g.look.count, g.look.keys,
                                     sl.q, nullptr, s->st));
-      if (ls.count) {
+      lsm_status err = LSM_OK;
+      if (ls.count && sort_queries(sl, sl.sa, sl.q, g.look.keys, err)) {
+        LSM_TRY(lookup_sorted_launch(ls, sl.sa[0], sl.sa[1], g.look.keys, sl.val, sl.found, s->st));
+      } else if (err != LSM_OK) {
+        return err;
+      } else if (ls.count) {
         LSM_TRY(lookup_launch(ls, sl.q, g.look.keys, sl.val, sl.found, s->st));
       } else {
         LSM_TRY(cudaMemsetAsync(sl.val, 0, 4 * g.look.keys, s->st));
@@ -380,7 +415,12 @@ struct Run {
       const uint32_t f = g.count.first;
       LSM_TRY(gather_windows_launch(s->pool_a, s->pool_c, sl.d_start + f, sl.d_dst + f, g.count.count,
                                     g.count.keys, sl.c1, sl.c2, s->st));
-      if (ls.count)
+      lsm_status err = LSM_OK;
+      if (ls.count && sort_queries(sl, sl.sa, sl.c1, g.count.keys, err))
+        LSM_TRY(count_launch(ls, sl.sa[0], sl.c2, g.count.keys, sl.cnt, nullptr, s->st, sl.sa[1]));
+      else if (err != LSM_OK)
+        return err;
+      else if (ls.count)
         LSM_TRY(count_launch(ls, sl.c1, sl.c2, g.count.keys, sl.cnt, nullptr, s->st));
       else
         LSM_TRY(cudaMemsetAsync(sl.cnt, 0, 4 * g.count.keys, s->st));
@@ -392,7 +432,13 @@ struct Run {
       LSM_TRY(gather_windows_launch(s->pool_a, s->pool_c, sl.d_start + f, sl.d_dst + f, g.range.count,
                                     g.range.keys, sl.r1, sl.r2, s->st));
       if (ls.count) {
-        LSM_TRY(count_launch(ls, sl.r1, sl.r2, nr, sl.rcnt, sl.bounds, s->st));
+        lsm_status err = LSM_OK;
+        g.range_sorted = sort_queries(sl, sl.sb, sl.r1, nr, err);
+        if (err != LSM_OK) return err;
+        if (g.range_sorted)
+          LSM_TRY(count_launch(ls, sl.sb[0], sl.r2, nr, sl.rcnt, sl.bounds, s->st, sl.sb[1]));
+        else
+          LSM_TRY(count_launch(ls, sl.r1, sl.r2, nr, sl.rcnt, sl.bounds, s->st));
         LSM_TRY(scan_launch(sl.rcnt, nr, sl.roff, sl.lb, sl.ctr, dict_status_word(s->dict), s->st));
       } else {
         LSM_TRY(cudaMemsetAsync(sl.roff, 0, 8 * (nr + 1), s->st));
@@ -408,6 +454,24 @@ struct Run {
     res->retrieval_groups += 1;
     inflight.push_back(std::move(g));
     return LSM_OK;
+  }
+
+  // Sorts n query keys with their positions into set[0] (keys) / set[1]
+  // (positions), when the group is large enough to profit.
+  bool sort_queries(Slot& sl, uint32_t* const* set, const uint32_t* keys, uint64_t n, lsm_status& err) {
+    if (n < kSortQueriesFrom || n > kMsdMaxN) return false;
+    SortArgs a{};
+    a.mode = kSortQueries;
+    a.in_keys = keys;
+    a.n_in = n;
+    a.n = uint32_t(n);
+    a.out_keys = set[0];
+    a.out_vals = set[1];
+    a.tmp_keys = set[2];
+    a.tmp_vals = set[3];
+    sl.sws.sticky = dict_status_word(s->dict);
+    err = cuda_status(sort_launch(a, sl.sws, s->st, nullptr, nullptr));
+    return err == LSM_OK;
   }
 
   // Second step of a range group: the emit (the state has not changed since
@@ -429,7 +493,8 @@ struct Run {
       hk = g.h_big_k;
       hv = g.h_big_v;
     }
-    if (total && g.ls.count) LSM_TRY(range_emit_launch(g.ls, nr, sl.bounds, sl.roff, dk, dv, s->st));
+    if (total && g.ls.count)
+      LSM_TRY(range_emit_launch(g.ls, nr, sl.bounds, sl.roff, dk, dv, s->st, g.range_sorted ? sl.sb[1] : nullptr));
     LSM_TRY(cudaMemcpyAsync(sl.h_roff, sl.roff, 8 * (nr + 1), cudaMemcpyDeviceToHost, s->st));
     if (total) {
       LSM_TRY(cudaMemcpyAsync(hk, dk, 4 * total, cudaMemcpyDeviceToHost, s->st));
@@ -668,6 +733,7 @@ lsm_status lsm_server_set_pool(lsm_server_t* s, const uint32_t* d_a, const uint3
                                uint64_t n) {
   if (!s || !d_a || !d_b || !d_c || n == 0) return LSM_ERR_ARG;
   DeviceGuard g(s->cfg.device);
+  LSM_TRY(cudaDeviceSynchronize());  // the pools were written on other streams
   // update keys come from pool a: check them once here, so that batches need
   // no per-batch key check
   uint32_t* flag = nullptr;
@@ -690,6 +756,7 @@ lsm_status lsm_server_set_pool(lsm_server_t* s, const uint32_t* d_a, const uint3
 lsm_status lsm_server_preload(lsm_server_t* s, const uint32_t* d_keys, const uint32_t* d_vals, uint64_t n) {
   if (!s) return LSM_ERR_ARG;
   DeviceGuard g(s->cfg.device);
+  LSM_TRY(cudaDeviceSynchronize());  // the pairs were written on other streams
   LSM_TRY_S(lsm_insert_batch(s->dict, d_keys, d_vals, n, s->st));
   LSM_TRY(cudaDeviceSynchronize());
   return LSM_OK;

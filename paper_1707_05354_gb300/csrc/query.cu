@@ -10,10 +10,10 @@
 //         one bin of about one 32-byte sector, and a short binary search
 //         finishes inside it.
 //         lookup_direct takes the queries in input order (one thread each);
-//         lookup_sorted takes queries sorted by key: the first and last lane
-//         of a warp bound the warp's window in each level and every lane then
-//         searches only that window, which its neighbours share in cache
-//         (the "bulk" alternative of §IV-B).
+//         lookup_sorted takes them sorted by key (the "bulk" alternative of
+//         §IV-B): the same search, but neighbouring threads read
+//         neighbouring parts of each level, which keeps page and sector
+//         reuse high when the levels span many gigabytes.
 // COUNT   per query and level the window [lower_bound(k1), upper_bound(k2))
 //         on the original key; the windows of all levels are then merged on
 //         the key, newer level first among equal keys, and a key counts when
@@ -90,57 +90,23 @@ __global__ void __launch_bounds__(kThreads) lookup_direct(LevelSet ls, const uin
   }
 }
 
-// Queries sorted by key; results scattered back to positions idx[i].
+// Queries sorted by key: the same per-query search as lookup_direct, in key
+// order, so neighbouring threads read neighbouring parts of every level and
+// prefix index (few pages and sectors per warp); results scattered back to
+// positions idx[i].
 __global__ void __launch_bounds__(kThreads) lookup_sorted(LevelSet ls, const uint32_t* __restrict__ sq,
                                                           const uint32_t* __restrict__ idx, uint64_t nq,
                                                           uint32_t* __restrict__ out_v,
                                                           uint8_t* __restrict__ out_f) {
-  const uint32_t lane = lane_id();
-  const uint64_t warps = uint64_t(gridDim.x) * (kThreads / 32);
-  for (uint64_t w = (blockIdx.x * uint64_t(kThreads) + threadIdx.x) >> 5; w * 32 < nq; w += warps) {
-    const uint64_t i = w * 32 + lane;
-    const bool act = i < nq;
-    const uint32_t key = act ? __ldg(sq + i) : 0xFFFFFFFFu;
-    // the warp's smallest and largest valid query (queries are sorted and
-    // out-of-domain keys sort last)
-    const uint32_t nact = __popc(__ballot_sync(0xffffffffu, act && key <= kMaxUserKey));
-    uint32_t val = 0;
-    uint8_t found = 0;
-    bool done = !(act && key <= kMaxUserKey);
-    if (nact) {
-      const uint32_t kfirst = __shfl_sync(0xffffffffu, key, 0);
-      const uint32_t klast = __shfl_sync(0xffffffffu, key, nact - 1);
-      for (int l = 0; l < ls.count; ++l) {
-        if (__all_sync(0xffffffffu, done)) break;
-        // Lanes 0 and 1 find where the warp's smallest and largest key would
-        // start; every lane's answer lies in [wlo, whi] (lower bounds are
-        // monotone in the key), so each lane searches [wlo, whi + 1).
-        uint32_t edge = 0;
-        if (lane < 2) edge = level_lower_bound(ls, l, (lane == 0 ? kfirst : klast) << 1);
-        const uint32_t wlo = __shfl_sync(0xffffffffu, edge, 0);
-        uint32_t whi = __shfl_sync(0xffffffffu, edge, 1);
-        whi = whi < ls.n[l] ? whi + 1 : ls.n[l];
-        if (!done) {
-          const uint32_t pos = lower_bound_kv(ls.keys[l], wlo, whi, key << 1);
-          if (pos < ls.n[l]) {
-            const uint32_t kv = __ldg(ls.keys[l] + pos);
-            if (key_of(kv) == key) {
-              done = true;
-              if (kv & 1u) {
-                found = 1;
-                val = __ldg(ls.vals[l] + pos);
-              }
-            }
-          }
-        }
-      }
-    }
-    if (act) {
-      const uint32_t o = __ldg(idx + i);
-      if (o < nq) {  // a permutation of [0, nq) unless the sort gave up on a wait
-        out_v[o] = val;
-        out_f[o] = found;
-      }
+  for (uint64_t i = blockIdx.x * uint64_t(kThreads) + threadIdx.x; i < nq;
+       i += uint64_t(gridDim.x) * kThreads) {
+    uint32_t v;
+    uint8_t f;
+    lookup_one(ls, __ldg(sq + i), v, f);
+    const uint32_t o = __ldg(idx + i);
+    if (o < nq) {  // a permutation of [0, nq) unless the sort gave up on a wait
+      out_v[o] = v;
+      out_f[o] = f;
     }
   }
 }
@@ -192,14 +158,21 @@ __device__ __forceinline__ uint32_t merge_windows(const LevelSet& ls, const uint
   return c;
 }
 
+// With `perm` (queries sorted by k1: k1 holds the sorted lower bounds and
+// perm their positions), thread i serves query perm[i] and stores its count
+// and windows at that position; neighbouring threads then search
+// neighbouring parts of every level.
 template <int L>
 __global__ void __launch_bounds__(kThreads) count_kernel(LevelSet ls, const uint32_t* __restrict__ k1,
                                                          const uint32_t* __restrict__ k2, uint64_t nq,
                                                          uint32_t* __restrict__ out_count,
-                                                         uint32_t* __restrict__ bounds) {
-  for (uint64_t i = blockIdx.x * uint64_t(kThreads) + threadIdx.x; i < nq;
-       i += uint64_t(gridDim.x) * kThreads) {
-    const uint32_t a = __ldg(k1 + i);
+                                                         uint32_t* __restrict__ bounds,
+                                                         const uint32_t* __restrict__ perm) {
+  for (uint64_t i0 = blockIdx.x * uint64_t(kThreads) + threadIdx.x; i0 < nq;
+       i0 += uint64_t(gridDim.x) * kThreads) {
+    const uint64_t i = perm ? __ldg(perm + i0) : i0;
+    if (i >= nq) continue;  // a permutation of [0, nq) unless its sort gave up on a wait
+    const uint32_t a = __ldg(k1 + i0);
     uint32_t z = __ldg(k2 + i);
     if (z > kMaxUserKey) z = kMaxUserKey;
     uint32_t lo[L], hi[L];
@@ -227,9 +200,12 @@ __global__ void __launch_bounds__(kThreads) range_emit(LevelSet ls, uint64_t nq,
                                                        const uint32_t* __restrict__ bounds,
                                                        const uint64_t* __restrict__ offsets,
                                                        uint32_t* __restrict__ keys,
-                                                       uint32_t* __restrict__ vals) {
-  for (uint64_t i = blockIdx.x * uint64_t(kThreads) + threadIdx.x; i < nq;
-       i += uint64_t(gridDim.x) * kThreads) {
+                                                       uint32_t* __restrict__ vals,
+                                                       const uint32_t* __restrict__ perm) {
+  for (uint64_t i0 = blockIdx.x * uint64_t(kThreads) + threadIdx.x; i0 < nq;
+       i0 += uint64_t(gridDim.x) * kThreads) {
+    const uint64_t i = perm ? __ldg(perm + i0) : i0;
+    if (i >= nq) continue;
     uint32_t lo[L], hi[L];
     const uint32_t* b = bounds + i * 2 * ls.count;
 #pragma unroll
@@ -369,16 +345,16 @@ cudaError_t lookup_sorted_launch(const LevelSet& ls, const uint32_t* sq, const u
 }
 
 cudaError_t count_launch(const LevelSet& ls, const uint32_t* k1, const uint32_t* k2, uint64_t nq,
-                         uint32_t* count, uint32_t* bounds, cudaStream_t st) {
+                         uint32_t* count, uint32_t* bounds, cudaStream_t st, const uint32_t* perm) {
   if (nq == 0) return cudaSuccess;
   const unsigned grid = persistent_grid(nq, kThreads, 152 * 8);
   count_launches(1);
-  if (ls.count <= 1) count_kernel<1><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds);
-  else if (ls.count <= 2) count_kernel<2><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds);
-  else if (ls.count <= 4) count_kernel<4><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds);
-  else if (ls.count <= 8) count_kernel<8><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds);
-  else if (ls.count <= 16) count_kernel<16><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds);
-  else count_kernel<kMaxLevels><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds);
+  if (ls.count <= 1) count_kernel<1><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds, perm);
+  else if (ls.count <= 2) count_kernel<2><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds, perm);
+  else if (ls.count <= 4) count_kernel<4><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds, perm);
+  else if (ls.count <= 8) count_kernel<8><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds, perm);
+  else if (ls.count <= 16) count_kernel<16><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds, perm);
+  else count_kernel<kMaxLevels><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds, perm);
   return cudaGetLastError();
 }
 
@@ -395,16 +371,16 @@ cudaError_t scan_launch(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t*
 }
 
 cudaError_t range_emit_launch(const LevelSet& ls, uint64_t nq, const uint32_t* bounds, const uint64_t* offsets,
-                              uint32_t* keys, uint32_t* vals, cudaStream_t st) {
+                              uint32_t* keys, uint32_t* vals, cudaStream_t st, const uint32_t* perm) {
   if (nq == 0) return cudaSuccess;
   const unsigned grid = persistent_grid(nq, kThreads, 152 * 8);
   count_launches(1);
-  if (ls.count <= 1) range_emit<1><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals);
-  else if (ls.count <= 2) range_emit<2><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals);
-  else if (ls.count <= 4) range_emit<4><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals);
-  else if (ls.count <= 8) range_emit<8><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals);
-  else if (ls.count <= 16) range_emit<16><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals);
-  else range_emit<kMaxLevels><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals);
+  if (ls.count <= 1) range_emit<1><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals, perm);
+  else if (ls.count <= 2) range_emit<2><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals, perm);
+  else if (ls.count <= 4) range_emit<4><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals, perm);
+  else if (ls.count <= 8) range_emit<8><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals, perm);
+  else if (ls.count <= 16) range_emit<16><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals, perm);
+  else range_emit<kMaxLevels><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals, perm);
   return cudaGetLastError();
 }
 

@@ -281,38 +281,48 @@ constexpr int kBucketIPT = 10;
 constexpr uint32_t kBucketCap = kBucketThreads * kBucketIPT;  // 5120
 constexpr uint32_t kSubBins = 4096;      // counting pass of the bucket fast path
 constexpr uint32_t kSubBinMax = 48;      // larger sub-bins take the pass-by-pass path
-constexpr int kMsdIPT = int(kMsdTile) / kThreads;              // 16
-static_assert(kMsdIPT * kThreads == int(kMsdTile), "tile");
+
+// The count and the scatter run 512 threads of 8 elements per
+// 4096-element tile: many warps to keep loads in flight, and a short
+// ranking chain per warp in the scatter.
+constexpr int kScatterThreads = 512;
+constexpr int kScatterWarps = kScatterThreads / 32;
+constexpr int kScatterIPT = int(kMsdTile) / kScatterThreads;  // 8
+static_assert(kScatterIPT * kScatterThreads == int(kMsdTile), "tile");
 
 // The padding of a short batch (copies of its last op, the leading
 // positions of the reversed sequence) is neither counted per tile nor
 // scattered: it is one run of equal elements, added to its bucket's total
 // here and written by that bucket's sort at its sorted place.
-__global__ void __launch_bounds__(kThreads) msd_count(Loader ld, uint32_t* __restrict__ tilecnt,
+__global__ void __launch_bounds__(kScatterThreads) msd_count(Loader ld, uint32_t* __restrict__ tilecnt,
                                                       uint32_t* __restrict__ ctl, uint32_t* status) {
   __shared__ uint32_t s_h[kRadix];
+  pdl_trigger();
+  pdl_wait();
   const uint32_t tid = threadIdx.x, tile = blockIdx.x;
   const uint32_t npad = ld.npad();
-  s_h[tid] = 0;
+  if (tid < kRadix) s_h[tid] = 0;
   __syncthreads();
-  uint32_t kv[kMsdIPT];
+  uint32_t kv[kScatterIPT];
   bool bad_any = false;
 #pragma unroll
-  for (int j = 0; j < kMsdIPT; ++j) {
-    const uint32_t p = tile * kMsdTile + j * kThreads + tid;
+  for (int j = 0; j < kScatterIPT; ++j) {
+    const uint32_t p = tile * kMsdTile + j * kScatterThreads + tid;
     bool bad = false;
     kv[j] = (p < ld.n && p >= npad) ? ld.load_key(p, bad) : 0u;
     bad_any |= bad;
   }
 #pragma unroll
-  for (int j = 0; j < kMsdIPT; ++j) {
-    const uint32_t p = tile * kMsdTile + j * kThreads + tid;
+  for (int j = 0; j < kScatterIPT; ++j) {
+    const uint32_t p = tile * kMsdTile + j * kScatterThreads + tid;
     if (p < ld.n && p >= npad) atomicAdd(&s_h[kv[j] >> 24], 1u);
   }
   const int any_bad = __syncthreads_or(bad_any);
-  const uint32_t c = s_h[tid];
-  tilecnt[tile * kRadix + tid] = c;
-  if (c) atomicAdd(ctl + 3 * kRadix + tid, c);
+  if (tid < kRadix) {
+    const uint32_t c = s_h[tid];
+    tilecnt[tile * kRadix + tid] = c;
+    if (c) atomicAdd(ctl + 3 * kRadix + tid, c);
+  }
   if (tile == 0 && tid == 0 && npad) {
     bool bad;
     atomicAdd(ctl + 3 * kRadix + (ld.load_key(0, bad) >> 24), npad);
@@ -336,6 +346,8 @@ __global__ void __launch_bounds__(kThreads) msd_offsets(const uint32_t* __restri
                                                         const uint32_t* __restrict__ ctl,
                                                         uint32_t* __restrict__ tileoff) {
   __shared__ uint32_t s_scan[kWarps];
+  pdl_trigger();
+  pdl_wait();
   const uint32_t d = blockIdx.x, t = threadIdx.x;
   const uint32_t base = bucket_start<kThreads>(ctl, d, s_scan);
   const uint32_t c = t < ntiles ? tilecnt[t * kRadix + d] : 0u;
@@ -389,21 +401,23 @@ __device__ __forceinline__ void rank_block(const uint32_t (&kv)[IPT], uint32_t m
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads) msd_scatter(Loader ld, const uint32_t* __restrict__ tileoff,
+__global__ void __launch_bounds__(kScatterThreads) msd_scatter(Loader ld, const uint32_t* __restrict__ tileoff,
                                                         uint32_t* __restrict__ out_k,
                                                         uint32_t* __restrict__ out_v) {
   __shared__ __align__(16) uint32_t s_keys[kMsdTile];
   __shared__ __align__(16) uint32_t s_vals[kMsdTile];
-  __shared__ uint32_t s_whist[kWarps][kRadix];
-  __shared__ uint32_t s_excl[kRadix], s_gbase[kRadix], s_scan[kWarps];
+  __shared__ uint32_t s_whist[kScatterWarps][kRadix];
+  __shared__ uint32_t s_excl[kRadix], s_gbase[kRadix], s_scan[kScatterWarps];
+  pdl_trigger();
+  pdl_wait();
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5, tile = blockIdx.x;
   const uint32_t n = ld.n, npad = ld.npad();
   const uint32_t t0 = tile * kMsdTile;
   if (t0 + kMsdTile <= npad) return;  // whole CTA: padding only
-  const uint32_t base = t0 + warp * (32 * kMsdIPT);
-  uint32_t kv[kMsdIPT], v[kMsdIPT], rank[kMsdIPT];
+  const uint32_t base = t0 + warp * (32 * kScatterIPT);
+  uint32_t kv[kScatterIPT], v[kScatterIPT], rank[kScatterIPT];
 #pragma unroll
-  for (int j = 0; j < kMsdIPT; ++j) {
+  for (int j = 0; j < kScatterIPT; ++j) {
     const uint32_t p = base + j * 32 + lane;
     kv[j] = 0;
     v[j] = 0;
@@ -412,10 +426,10 @@ __global__ void __launch_bounds__(kThreads) msd_scatter(Loader ld, const uint32_
       ld.load(p, kv[j], v[j], bad);
     }
   }
-  s_gbase[tid] = tileoff[tile * kRadix + tid];
-  rank_block<kThreads, kMsdIPT>(kv, n, base, 24, rank, s_whist, s_excl, s_scan, nullptr, npad);
+  if (tid < kRadix) s_gbase[tid] = tileoff[tile * kRadix + tid];
+  rank_block<kScatterThreads, kScatterIPT>(kv, n, base, 24, rank, s_whist, s_excl, s_scan, nullptr, npad);
 #pragma unroll
-  for (int j = 0; j < kMsdIPT; ++j) {
+  for (int j = 0; j < kScatterIPT; ++j) {
     const uint32_t p = base + j * 32 + lane;
     if (p < n && p >= npad) {
       const uint32_t d = kv[j] >> 24;
@@ -427,7 +441,7 @@ __global__ void __launch_bounds__(kThreads) msd_scatter(Loader ld, const uint32_
   __syncthreads();
   const uint32_t lo_t = t0 > npad ? t0 : npad, hi_t = (n - t0) < kMsdTile ? n : t0 + kMsdTile;
   const uint32_t tile_n = hi_t > lo_t ? hi_t - lo_t : 0u;  // real elements of the tile
-  for (uint32_t i = tid; i < tile_n; i += kThreads) {
+  for (uint32_t i = tid; i < tile_n; i += kScatterThreads) {
     const uint32_t k = s_keys[i];
     const uint32_t d = k >> 24;
     const uint32_t dst = s_gbase[d] + (i - s_excl[d]);
@@ -735,6 +749,8 @@ __global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort(Loader ld, uint
                                                               uint32_t* __restrict__ next_ctl) {
   extern __shared__ __align__(16) uint32_t bsm[];
   __shared__ uint32_t s_scan[kBucketWarps];
+  pdl_trigger();
+  pdl_wait();
   const uint32_t tid = threadIdx.x, d = blockIdx.x;
   // the control block of the next sort starts zeroed (it is idle now)
   if (d == 0)
@@ -964,19 +980,22 @@ cudaError_t bucket_sort_launch(const SortArgs& a, SortWorkspace& ws, cudaStream_
   uint32_t* next = ws.ctl + (ws.flip ^ 1) * kSortCtlWords;
   Loader ld{a.mode, a.in_keys, a.in_vals, a.in_del, a.n_in, a.n};
   count_launches(1);
-  msd_count<<<ntiles, kThreads, 0, st>>>(ld, tilecnt, ctl, status);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_pdl(msd_count, dim3(ntiles), dim3(kScatterThreads), 0, st, ld, tilecnt, ctl, status)) !=
+      cudaSuccess)
+    return e;
   if (status && (e = cudaEventRecord(ev, st)) != cudaSuccess) return e;
   count_launches(1);
-  msd_offsets<<<kRadix, kThreads, 0, st>>>(tilecnt, ntiles, ctl, tileoff);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_pdl(msd_offsets, dim3(kRadix), dim3(kThreads), 0, st, tilecnt, ntiles, ctl, tileoff)) !=
+      cudaSuccess)
+    return e;
   count_launches(1);
-  msd_scatter<<<ntiles, kThreads, 0, st>>>(ld, tileoff, a.tmp_keys, a.tmp_vals);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_pdl(msd_scatter, dim3(ntiles), dim3(kScatterThreads), 0, st, ld, tileoff, a.tmp_keys,
+                      a.tmp_vals)) != cudaSuccess)
+    return e;
   count_launches(1);
-  bucket_sort<<<kRadix, kBucketThreads, kBucketSmem, st>>>(ld, a.tmp_keys, a.tmp_vals, a.out_keys, a.out_vals,
-                                                          ctl, a.n, a.fence, a.fshift, next);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_pdl(bucket_sort, dim3(kRadix), dim3(kBucketThreads), kBucketSmem, st, ld, a.tmp_keys, a.tmp_vals,
+                      a.out_keys, a.out_vals, ctl, a.n, a.fence, a.fshift, next)) != cudaSuccess)
+    return e;
   ws.flip ^= 1;
   return cudaSuccess;
 }

@@ -5,6 +5,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -39,3 +41,16 @@ def test_host_only_calls_without_gpu(lsm_lib):
 def test_built_for_sm_103a():
     from paper_1707_05354_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def test_library_resolves_its_own_symbols(lsm_lib):
+    """Every internal (gpulsm::) function the library calls is defined in it:
+    a declaration left without a definition would only fail when loaded."""
+    import shutil
+    import subprocess
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    out = subprocess.run([nm, "-D", "-C", "--undefined-only", lsm_lib.LIB_PATH], capture_output=True, text=True)
+    missing = [ln for ln in out.stdout.splitlines() if "gpulsm::" in ln]
+    assert not missing, missing

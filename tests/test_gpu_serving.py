@@ -90,9 +90,9 @@ def real_time_order_holds(out, arrival):
     return bool(ok.all())
 
 
-def small_setup(seed, n_req, key_space, rate):
+def small_setup(seed, n_req, key_space, rate, size_hi_log2=8.0):
     pools = workload.serving_pools(seed=seed, n=1 << 15, key_space=key_space, width=64)
-    trace = workload.serving_trace(seed=seed, n_req=n_req, rate=rate, pool_n=1 << 15, size_hi_log2=8.0)
+    trace = workload.serving_trace(seed=seed, n_req=n_req, rate=rate, pool_n=1 << 15, size_hi_log2=size_hi_log2)
     g_ = workload.rng(seed, 3, 99)
     pre = (workload.u32(g_, 4096, 0, key_space), workload.u32(g_, 4096))
     return pools, trace, pre
@@ -113,6 +113,23 @@ def test_serving_linearisable(g, policy, slots):
     assert real_time_order_holds(out, trace[1])
     # groups really coalesced requests
     assert out["update_batches"] + out["retrieval_groups"] < len(trace[0])
+
+
+def test_serving_large_groups_sorted(g):
+    """Requests that arrive almost at once form retrieval groups of tens of
+    thousands of keys, which the server processes in key order (sorted
+    lookups, counts and ranges with their positions)."""
+    b = 1 << 15
+    pools, trace, pre = small_setup(1707053577, 3000, 1 << 14, 1.0e7, size_hi_log2=12.0)
+    srv = g.Server(b, 1 << 31, flush_us=2000.0, group_keys=1 << 17, slots=2, range_cap=1 << 21)
+    srv.set_pool(*pools)
+    srv.preload(*pre)
+    out = srv.run(*trace, keep_results=True)
+    assert (out["status"] == g.LSM_OK).all()
+    sizes = trace[3].astype(np.int64)
+    assert out["retrieval_groups"] < 200 and sizes[trace[0] >= 2].sum() > (1 << 17)
+    replay_and_check(g, b, pools, pre, trace, out)
+    assert real_time_order_holds(out, trace[1])
 
 
 def test_serving_budget_cleanup_and_refusal(g):
