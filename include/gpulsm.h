@@ -180,6 +180,19 @@ lsm_status lsm_range(lsm_t* h, const uint32_t* d_k1, const uint32_t* d_k2, uint6
 lsm_status lsm_cleanup(lsm_t* h, void* stream);
 
 /*
+ * lsm_bulk_build - fill an EMPTY dictionary (r = 0) with n (key, value)
+ * pairs at once: the same query results as lsm_insert_batch of the pairs (the
+ * last occurrence of a key wins), laid out as a cleanup leaves the levels
+ * (the live pairs sorted, filling the set bits of r = ceil(n'/b), placebos
+ * after them).  One stable sort of all n pairs (the paper's bulk build, §V)
+ * and the cleanup's compaction; needs temporary device memory of about
+ * 18 bytes per pair.  Synchronises.
+ * Errors: LSM_ERR_ARG (not empty), LSM_ERR_FULL (n > capacity),
+ * LSM_ERR_KEY_RANGE, LSM_ERR_OOM, LSM_ERR_CUDA.
+ */
+lsm_status lsm_bulk_build(lsm_t* h, const uint32_t* d_keys, const uint32_t* d_vals, uint64_t n, void* stream);
+
+/*
  * lsm_stats - host-side state: r = resident batches, resident = r * b
  * elements, b = batch size, levels = number of allocated levels.  Any output
  * pointer may be NULL.  Does not touch the device.
@@ -504,6 +517,9 @@ typedef struct {
    * groups (from the stream reaching a group to its completion event) */
   double host_admit_update_us, host_admit_retrieval_us, host_range_us, host_complete_us, host_cleanup_us,
       host_sleep_us, gpu_update_ms, gpu_retrieval_ms;
+  /* device milliseconds of the retrieval groups' phases: payload gathers and
+   * sorts, lookups, counts, range counts with their scan, range emits */
+  double gpu_prep_ms, gpu_lookup_ms, gpu_count_ms, gpu_range_ms, gpu_emit_ms;
 } lsm_trace_result;
 
 /* Creates the server and its dictionary.  Errors: LSM_ERR_ARG,

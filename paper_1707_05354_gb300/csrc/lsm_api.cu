@@ -607,13 +607,12 @@ lsm_status lsm_range(lsm_t* h, const uint32_t* d_k1, const uint32_t* d_k2, uint6
   return cuda_status(range_emit_launch(ls, nq, bounds, d_offsets, d_keys, d_vals, st));
 }
 
-lsm_status lsm_cleanup(lsm_t* h, void* stream) {
-  if (!h) return LSM_ERR_ARG;
-  if (h->r == 0) return LSM_OK;
-  DeviceGuard g(h->device);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  LSM_TRY(join_side(h, st));
-  const uint64_t total = h->r * h->b;
+// Rebuild of the levels from sorted sources (rank order: newest first): the
+// fold keeps the first element of every key when it is regular and compacts
+// the survivors; the n' live pairs then fill the set bits of r' = ceil(n'/b)
+// in ascending level order, with placebo tombstones after the last one
+// (§IV-E).  Synchronises with `st` (the host must learn n').
+static lsm_status rebuild(lsm_t* h, const FoldSources& src, uint64_t total, cudaStream_t st) {
   if (h->clean_cap < total) {
     if (h->d_ck) cudaFree(h->d_ck);
     if (h->d_cv) cudaFree(h->d_cv);
@@ -627,16 +626,8 @@ lsm_status lsm_cleanup(lsm_t* h, void* stream) {
     LSM_TRY(dalloc(&h->d_clb, fold_tiles(cap) + 1));
     h->clean_cap = cap;
   }
-  const LevelSet ls = full_levels(h);
   FoldArgs f{};
-  f.src.count = ls.count;
-  for (int i = 0; i < ls.count; ++i) {
-    f.src.keys[i] = ls.keys[i];
-    f.src.vals[i] = ls.vals[i];
-    f.src.fence[i] = ls.fence[i];
-    f.src.fshift[i] = ls.fshift[i];
-    f.src.n[i] = ls.n[i];
-  }
+  f.src = src;
   f.total = total;
   f.out_keys = h->d_ck;
   f.out_vals = h->d_cv;
@@ -679,6 +670,93 @@ lsm_status lsm_cleanup(lsm_t* h, void* stream) {
   }
   h->r = r2;
   return LSM_OK;
+}
+
+lsm_status lsm_cleanup(lsm_t* h, void* stream) {
+  if (!h) return LSM_ERR_ARG;
+  if (h->r == 0) return LSM_OK;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  LSM_TRY(join_side(h, st));
+  const LevelSet ls = full_levels(h);
+  FoldSources src{};
+  src.count = ls.count;
+  for (int i = 0; i < ls.count; ++i) {
+    src.keys[i] = ls.keys[i];
+    src.vals[i] = ls.vals[i];
+    src.fence[i] = ls.fence[i];
+    src.fshift[i] = ls.fshift[i];
+    src.n[i] = ls.n[i];
+  }
+  return rebuild(h, src, h->r * h->b, st);
+}
+
+lsm_status lsm_bulk_build(lsm_t* h, const uint32_t* d_keys, const uint32_t* d_vals, uint64_t n, void* stream) {
+  if (!h || (n && (!d_keys || !d_vals))) return LSM_ERR_ARG;
+  if (h->r != 0) return LSM_ERR_ARG;
+  if (n == 0) return LSM_OK;
+  if (n > h->capacity || n > 0xFFFFFFFFull) return LSM_ERR_FULL;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  LSM_TRY(join_side(h, st));
+  // one stable sort of the whole reversed input (the last occurrence of a key
+  // first), with its prefix index, into temporary buffers
+  const uint64_t npad = round_up(n, kLevelAlign) + kSlack;
+  const uint64_t tiles = (n + kSortTile - 1) / kSortTile;
+  const int fs = fence_shift_for(n);
+  uint32_t *buf = nullptr, *ctl = nullptr, *tilecnt = nullptr;
+  uint64_t* lookback = nullptr;
+  lsm_status result = LSM_OK;
+  cudaError_t e = dalloc(&buf, 4 * npad + fence_words(fs));
+  if (e == cudaSuccess) e = dalloc(&ctl, 2 * kSortCtlWords);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, 4ull * 2 * kSortCtlWords, st);
+  if (e == cudaSuccess) e = dalloc(&tilecnt, kMsdTileWords);
+  if (e == cudaSuccess) e = dalloc(&lookback, uint64_t(kSortPasses) * tiles * 256);
+  if (e == cudaSuccess) e = cudaMemsetAsync(lookback, 0, 8ull * kSortPasses * tiles * 256, st);
+  if (e == cudaSuccess) {
+    SortWorkspace ws{};
+    ws.ctl = ctl;
+    ws.flip = 0;
+    ws.lookback = lookback;
+    ws.max_tiles = uint32_t(tiles);
+    ws.epoch = 0;
+    ws.sticky = h->d_misc + kMiscSticky;
+    ws.tilecnt = tilecnt;
+    SortArgs a{};
+    a.mode = kSortInsert;
+    a.in_keys = d_keys;
+    a.in_vals = d_vals;
+    a.n_in = n;
+    a.n = uint32_t(n);
+    a.out_keys = buf;
+    a.out_vals = buf + npad;
+    a.tmp_keys = buf + 2 * npad;
+    a.tmp_vals = buf + 3 * npad;
+    a.fence = buf + 4 * npad;
+    a.fshift = fs;
+    *reinterpret_cast<volatile uint32_t*>(h->h_status) = 0u;
+    e = sort_launch(a, ws, st, h->d_status_map, h->ev);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && (*reinterpret_cast<volatile uint32_t*>(h->h_status) & kErrBadKey)) {
+      result = LSM_ERR_KEY_RANGE;
+    } else if (e == cudaSuccess) {
+      FoldSources src{};
+      src.count = 1;
+      src.keys[0] = a.out_keys;
+      src.vals[0] = a.out_vals;
+      src.fence[0] = a.fence;
+      src.fshift[0] = fs;
+      src.n[0] = uint32_t(n);
+      result = rebuild(h, src, n, st);
+    }
+  }
+  cudaStreamSynchronize(st);
+  if (buf) cudaFree(buf);
+  if (ctl) cudaFree(ctl);
+  if (tilecnt) cudaFree(tilecnt);
+  if (lookback) cudaFree(lookback);
+  if (e != cudaSuccess) return cuda_status(e);
+  return result;
 }
 
 lsm_status lsm_stats(const lsm_t* h, uint64_t* r, uint64_t* resident, uint32_t* b, uint32_t* levels) {

@@ -114,6 +114,7 @@ struct Slot {
   uint32_t *h_rk = nullptr, *h_rv = nullptr;
   uint64_t* h_total = nullptr;
   cudaEvent_t ev_done = nullptr, ev_total = nullptr, ev_start = nullptr;
+  cudaEvent_t ev_ph[6] = {};  // retrieval phases: after gathers+sorts ... before the emit
   // sorting the queries of a large group (by key, with their positions):
   // set A for lookups and counts, set B for ranges (its positions are read
   // again by the emit)
@@ -201,6 +202,8 @@ void free_slot(Slot& s) {
   if (s.ev_done) cudaEventDestroy(s.ev_done);
   if (s.ev_total) cudaEventDestroy(s.ev_total);
   if (s.ev_start) cudaEventDestroy(s.ev_start);
+  for (cudaEvent_t e : s.ev_ph)
+    if (e) cudaEventDestroy(e);
   if (s.sort_ctl) cudaFree(s.sort_ctl);
   if (s.sort_tilecnt) cudaFree(s.sort_tilecnt);
   for (int i = 0; i < 4; ++i) {
@@ -248,6 +251,7 @@ cudaError_t alloc_slot(Slot& s, const lsm_server_config& c, uint32_t max_levels,
   if (e == cudaSuccess) e = cudaEventCreate(&s.ev_done);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_total, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreate(&s.ev_start);
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreate(&s.ev_ph[i]);
   if (e == cudaSuccess) e = dalloc(&s.sort_ctl, 2 * kSortCtlWords);
   if (e == cudaSuccess) e = cudaMemset(s.sort_ctl, 0, 4ull * 2 * kSortCtlWords);
   if (e == cudaSuccess) e = dalloc(&s.sort_tilecnt, kMsdTileWords);
@@ -393,6 +397,7 @@ struct Run {
     LSM_TRY(dict_join(s->dict, s->st));
     g.ls = dict_levels(s->dict);
     const LevelSet& ls = g.ls;
+    LSM_TRY(cudaEventRecord(sl.ev_ph[0], s->st));
     if (g.look.count) {
       const uint32_t f = g.look.first;
       LSM_TRY(gather_windows_launch(s->pool_a, nullptr, sl.d_start + f, sl.d_dst + f, g.look.count, g.look.keys,
@@ -411,6 +416,7 @@ struct Run {
       LSM_TRY(cudaMemcpyAsync(sl.h_val, sl.val, 4 * g.look.keys, cudaMemcpyDeviceToHost, s->st));
       LSM_TRY(cudaMemcpyAsync(sl.h_found, sl.found, g.look.keys, cudaMemcpyDeviceToHost, s->st));
     }
+    LSM_TRY(cudaEventRecord(sl.ev_ph[1], s->st));
     if (g.count.count) {
       const uint32_t f = g.count.first;
       LSM_TRY(gather_windows_launch(s->pool_a, s->pool_c, sl.d_start + f, sl.d_dst + f, g.count.count,
@@ -426,6 +432,7 @@ struct Run {
         LSM_TRY(cudaMemsetAsync(sl.cnt, 0, 4 * g.count.keys, s->st));
       LSM_TRY(cudaMemcpyAsync(sl.h_cnt, sl.cnt, 4 * g.count.keys, cudaMemcpyDeviceToHost, s->st));
     }
+    LSM_TRY(cudaEventRecord(sl.ev_ph[2], s->st));
     if (g.range.count) {
       const uint32_t f = g.range.first;
       const uint64_t nr = g.range.keys;
@@ -443,11 +450,13 @@ struct Run {
       } else {
         LSM_TRY(cudaMemsetAsync(sl.roff, 0, 8 * (nr + 1), s->st));
       }
+      LSM_TRY(cudaEventRecord(sl.ev_ph[3], s->st));
       LSM_TRY(cudaMemcpyAsync(sl.h_total, sl.roff + nr, 8, cudaMemcpyDeviceToHost, s->st));
       LSM_TRY(cudaEventRecord(sl.ev_total, s->st));
       g.stage = kRangePending;
       pending_ranges += 1;
     } else {
+      LSM_TRY(cudaEventRecord(sl.ev_ph[3], s->st));
       LSM_TRY(cudaEventRecord(sl.ev_done, s->st));
       g.stage = kRunning;
     }
@@ -493,8 +502,10 @@ struct Run {
       hk = g.h_big_k;
       hv = g.h_big_v;
     }
+    LSM_TRY(cudaEventRecord(sl.ev_ph[4], s->st));
     if (total && g.ls.count)
       LSM_TRY(range_emit_launch(g.ls, nr, sl.bounds, sl.roff, dk, dv, s->st, g.range_sorted ? sl.sb[1] : nullptr));
+    LSM_TRY(cudaEventRecord(sl.ev_ph[5], s->st));
     LSM_TRY(cudaMemcpyAsync(sl.h_roff, sl.roff, 8 * (nr + 1), cudaMemcpyDeviceToHost, s->st));
     if (total) {
       LSM_TRY(cudaMemcpyAsync(hk, dk, 4 * total, cudaMemcpyDeviceToHost, s->st));
@@ -518,6 +529,18 @@ struct Run {
     if (cudaEventElapsedTime(&ms, sl.ev_start, sl.ev_done) == cudaSuccess) {
       if (g.update) res->gpu_update_ms += ms;
       else res->gpu_retrieval_ms += ms;
+    }
+    if (!g.update) {
+      // the phases (the lookups include their gathers and sort, and so on)
+      auto el = [&](cudaEvent_t a, cudaEvent_t b) {
+        float x = 0.f;
+        return cudaEventElapsedTime(&x, a, b) == cudaSuccess ? double(x) : 0.0;
+      };
+      res->gpu_prep_ms += el(sl.ev_start, sl.ev_ph[0]);
+      res->gpu_lookup_ms += el(sl.ev_ph[0], sl.ev_ph[1]);
+      res->gpu_count_ms += el(sl.ev_ph[1], sl.ev_ph[2]);
+      res->gpu_range_ms += el(sl.ev_ph[2], sl.ev_ph[3]);
+      if (g.range.count) res->gpu_emit_ms += el(sl.ev_ph[4], sl.ev_ph[5]);
     }
     const double h0 = now_us(t0);
     for (uint64_t i : g.reqs) {
@@ -775,6 +798,7 @@ lsm_status lsm_server_run(lsm_server_t* s, const lsm_trace* t, lsm_trace_result*
   r->update_batches = r->padded_ops = r->retrieval_groups = r->cleanups = r->refused = 0;
   r->host_admit_update_us = r->host_admit_retrieval_us = r->host_range_us = r->host_complete_us = 0;
   r->host_cleanup_us = r->host_sleep_us = r->gpu_update_ms = r->gpu_retrieval_ms = 0;
+  r->gpu_prep_ms = r->gpu_lookup_ms = r->gpu_count_ms = r->gpu_range_ms = r->gpu_emit_ms = 0;
   Run run;
   run.s = s;
   run.t = t;

@@ -114,7 +114,10 @@ __global__ void __launch_bounds__(kThreads) lookup_sorted(LevelSet ls, const uin
 // Per-query multi-way merge of the level windows on the key, newer level
 // first among equal keys; visits the newest element of every key once.  L is
 // a compile-time bound on the number of full levels (loops fully unrolled, so
-// the cursors stay in registers); levels l >= ls.count are empty.
+// the cursors stay in registers); levels l >= ls.count are empty.  Once a
+// key's newest element is taken, every level skips the whole run of that key
+// (a binary search when the run is longer than one element), so keys stored
+// many times (stale versions, a short batch's padding) cost O(L log run).
 template <bool kEmit, int L>
 __device__ __forceinline__ uint32_t merge_windows(const LevelSet& ls, const uint32_t (&lo)[L],
                                                   const uint32_t (&hi)[L], uint32_t* out_k, uint32_t* out_v,
@@ -125,7 +128,7 @@ __device__ __forceinline__ uint32_t merge_windows(const LevelSet& ls, const uint
     cur[l] = lo[l];
     head[l] = (l < ls.count && cur[l] < hi[l]) ? key_of(__ldg(ls.keys[l] + cur[l])) : 0xFFFFFFFFu;
   }
-  uint32_t c = 0, last = 0xFFFFFFFFu;
+  uint32_t c = 0;
   while (true) {
     uint32_t bk = 0xFFFFFFFFu, p = 0;
     int best = -1;
@@ -137,23 +140,24 @@ __device__ __forceinline__ uint32_t merge_windows(const LevelSet& ls, const uint
         p = cur[l];
       }
     if (best < 0) break;
-    if (bk != last) {
-      last = bk;
-      const uint32_t kv = __ldg(ls.keys[best] + p);
-      if (kv & 1u) {
-        if (kEmit && c < room) {
-          out_k[c] = bk;
-          out_v[c] = __ldg(ls.vals[best] + p);
-        }
-        ++c;
+    const uint32_t kv = __ldg(ls.keys[best] + p);
+    if (kv & 1u) {
+      if (kEmit && c < room) {
+        out_k[c] = bk;
+        out_v[c] = __ldg(ls.vals[best] + p);
       }
+      ++c;
     }
 #pragma unroll
-    for (int l = 0; l < L; ++l)
-      if (l == best) {
-        cur[l] = p + 1;
-        head[l] = p + 1 < hi[l] ? key_of(__ldg(ls.keys[l] + p + 1)) : 0xFFFFFFFFu;
+    for (int l = 0; l < L; ++l) {
+      if (head[l] == bk) {  // past every element of key bk in level l
+        const uint32_t* a = ls.keys[l];
+        uint32_t q = cur[l] + 1;
+        if (q < hi[l] && key_of(__ldg(a + q)) == bk) q = upper_bound_key(a, q + 1, hi[l], bk);
+        cur[l] = q;
+        head[l] = q < hi[l] ? key_of(__ldg(a + q)) : 0xFFFFFFFFu;
       }
+    }
   }
   return c;
 }

@@ -68,7 +68,9 @@ class TraceResult(ctypes.Structure):
                 ("host_admit_retrieval_us", ctypes.c_double), ("host_range_us", ctypes.c_double),
                 ("host_complete_us", ctypes.c_double), ("host_cleanup_us", ctypes.c_double),
                 ("host_sleep_us", ctypes.c_double), ("gpu_update_ms", ctypes.c_double),
-                ("gpu_retrieval_ms", ctypes.c_double)]
+                ("gpu_retrieval_ms", ctypes.c_double), ("gpu_prep_ms", ctypes.c_double),
+                ("gpu_lookup_ms", ctypes.c_double), ("gpu_count_ms", ctypes.c_double),
+                ("gpu_range_ms", ctypes.c_double), ("gpu_emit_ms", ctypes.c_double)]
 
 
 class ProfileEntry(ctypes.Structure):
@@ -88,6 +90,7 @@ _SIGS = {
     "lsm_count": ([_vp, _vp, _vp, _u64, _vp, _vp], _i32),
     "lsm_range": ([_vp, _vp, _vp, _u64, _vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp], _i32),
     "lsm_cleanup": ([_vp, _vp], _i32),
+    "lsm_bulk_build": ([_vp, _vp, _vp, _u64, _vp], _i32),
     "lsm_stats": ([_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u32),
                    ctypes.POINTER(_u32)], _i32),
     "lsm_level_offset": ([_vp, _u32, ctypes.POINTER(_u64), ctypes.POINTER(_u64)], _i32),
@@ -194,6 +197,10 @@ def lsm_range(h, d_k1, d_k2, nq, d_offsets, d_keys, d_vals, capacity, stream=Non
 
 def lsm_cleanup(h, stream=None):
     return _check(_lib.lsm_cleanup(h, stream), "lsm_cleanup")
+
+
+def lsm_bulk_build(h, d_keys, d_vals, n, stream=None):
+    return _check(_lib.lsm_bulk_build(h, d_keys, d_vals, n, stream), "lsm_bulk_build")
 
 
 def lsm_stats(h):
@@ -461,6 +468,10 @@ class LSM:
     def cleanup(self):
         lsm_cleanup(self.h, _stream(self.device))
 
+    def bulk_build(self, keys, vals):
+        k, v = as_device_u32(keys, self.device), as_device_u32(vals, self.device)
+        lsm_bulk_build(self.h, _ptr(k), _ptr(v), k.numel(), _stream(self.device))
+
     # queries -------------------------------------------------------------
     def lookup(self, q):
         torch = _torch()
@@ -669,5 +680,6 @@ class Server:
                    wall_us=res.wall_us,
                    time_split={k: getattr(res, k) for k in (
                        "host_admit_update_us", "host_admit_retrieval_us", "host_range_us", "host_complete_us",
-                       "host_cleanup_us", "host_sleep_us", "gpu_update_ms", "gpu_retrieval_ms")})
+                       "host_cleanup_us", "host_sleep_us", "gpu_update_ms", "gpu_retrieval_ms", "gpu_prep_ms",
+                       "gpu_lookup_ms", "gpu_count_ms", "gpu_range_ms", "gpu_emit_ms")})
         return out

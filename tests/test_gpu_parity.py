@@ -410,4 +410,44 @@ def test_short_batch_padding(g, case):
     ev, ef = o1.lookup(q)
     np.testing.assert_array_equal(found.cpu().numpy(), ef)
     np.testing.assert_array_equal(u32(val), ev)
+    # count / range windows over the long runs of padded copies
+    k1 = np.concatenate([q[:2000] - np.minimum(q[:2000], 3), np.zeros(2, np.uint32)])
+    k2 = np.concatenate([q[:2000] + 3, np.full(2, 0x7FFFFFFE, np.uint32)])
+    np.testing.assert_array_equal(u32(lsm.count(k1, k2)), o1.count(k1, k2))
+    off, rk, rv = lsm.range(k1, k2)
+    eo, ek, evv = o1.range(k1, k2)
+    np.testing.assert_array_equal(off.cpu().numpy().astype(np.uint64), eo)
+    np.testing.assert_array_equal(u32(rk), ek)
+    np.testing.assert_array_equal(u32(rv), evv)
+    assert lsm.device_errors() == 0
+
+
+@pytest.mark.parametrize("b,n,key_space", [(1024, 1, 100), (1024, 5000, 3000), (1000, 77777, 1 << 20),
+                                           (1 << 16, (3 << 20) + 5, 1 << 21)])
+def test_bulk_build(g, b, n, key_space):
+    """lsm_bulk_build equals inserting the pairs and cleaning up: the same
+    level layout as the oracle's insert + cleanup (sorted live pairs over the
+    set bits of ceil(n'/b), placebos after them) and the same answers; the
+    largest case sorts more than 2^20 pairs (the pass-by-pass sort)."""
+    rng = np.random.default_rng(n)
+    keys = rng.integers(0, key_space, size=n).astype(np.uint32)
+    vals = rng.integers(0, 1 << 32, size=n, dtype=np.uint64).astype(np.uint32)
+    lsm = g.LSM(b, n + 2 * b)
+    lsm.bulk_build(keys, vals)
+    s = oracle.StructuralOracle(b)
+    s.call("insert", keys, vals)
+    s.cleanup()
+    assert_levels(lsm, s)
+    o1 = oracle.MapOracle(b)
+    o1.call("insert", keys, vals)
+    q = np.concatenate([keys[:4096], rng.integers(0, key_space + 10, size=4096).astype(np.uint32)])
+    val, found = lsm.lookup(q)
+    ev, ef = o1.lookup(q)
+    np.testing.assert_array_equal(found.cpu().numpy(), ef)
+    np.testing.assert_array_equal(u32(val), ev)
+    k1 = rng.integers(0, key_space, size=2048).astype(np.uint32)
+    k2 = (k1 + rng.integers(0, 64, size=2048)).astype(np.uint32)
+    np.testing.assert_array_equal(u32(lsm.count(k1, k2)), o1.count(k1, k2))
+    with pytest.raises(g.LSMError):
+        lsm.bulk_build(keys[:10], vals[:10])   # only into an empty dictionary
     assert lsm.device_errors() == 0
