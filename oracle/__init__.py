@@ -70,6 +70,7 @@ def _load():
     lib.o1_lookup.argtypes = [vp, vp, u64, vp, vp]
     lib.o1_count.argtypes = [vp, vp, vp, u64, vp]
     lib.o1_range.argtypes = [vp, vp, vp, u64, vp, vp, vp]
+    lib.o1_neighbor.argtypes = [vp, vp, u64, ctypes.c_int, vp, vp, vp]
     lib.s_new.argtypes = [ctypes.c_uint32]
     lib.s_new.restype = vp
     lib.s_free.argtypes = [vp]
@@ -167,6 +168,16 @@ class MapOracle:
         out = np.empty(len(k1), np.uint32)
         self._lib.o1_count(self._h, _p(k1), _p(k2), len(k1), _p(out))
         return out
+
+    def neighbor(self, q, successor=True):
+        """(key, value, found) of the successor (smallest live key >= q) or
+        predecessor (largest live key <= q) of every query."""
+        q = _u32(q)
+        key = np.empty(len(q), np.uint32)
+        val = np.empty(len(q), np.uint32)
+        found = np.empty(len(q), np.uint8)
+        self._lib.o1_neighbor(self._h, _p(q), len(q), 1 if successor else 0, _p(key), _p(val), _p(found))
+        return key, val, found
 
     def range(self, k1, k2):
         k1, k2 = _u32(k1), _u32(k2)

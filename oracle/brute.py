@@ -67,3 +67,18 @@ def count_by_enumeration(batches, k1, k2):
     """Count by testing every key in [k1, k2] one by one (small widths only)."""
     k2 = min(k2, MAX_USER_KEY)
     return sum(1 for k in range(k1, k2 + 1) if state_of(batches, k)[0])
+
+
+def neighbor(batches, q, successor=True):
+    """(key, value) of the live key nearest to q on one side (inclusive), or
+    None: every key the log mentions on that side, tested one by one."""
+    keys = set()
+    for batch in batches:
+        for k, _, _ in batch:
+            if (k >= q) if successor else (k <= min(q, MAX_USER_KEY)):
+                keys.add(k)
+    for k in (sorted(keys) if successor else sorted(keys, reverse=True)):
+        found, v = state_of(batches, k)
+        if found:
+            return k, v
+    return None

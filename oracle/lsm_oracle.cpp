@@ -219,6 +219,36 @@ void o1_count(void* h, const uint32_t* k1, const uint32_t* k2, uint64_t nq,
   }
 }
 
+// Order-based neighbour queries that §II-A's footnote names beside the
+// three retrievals (successor and predecessor of a key), read inclusively:
+// successor(q) = the live pair with the smallest key >= q, predecessor(q) =
+// the one with the largest key <= q (keys above 2^31 - 2 are never live).
+// found[i] = 0 and key = value = 0 when there is none.
+void o1_neighbor(void* h, const uint32_t* q, uint64_t nq, int successor, uint32_t* key, uint32_t* val,
+                 uint8_t* found) {
+  const auto& m = static_cast<O1*>(h)->m;
+  for (uint64_t i = 0; i < nq; ++i) {
+    key[i] = val[i] = 0;
+    found[i] = 0;
+    if (successor) {
+      auto it = m.lower_bound(q[i]);
+      if (it != m.end()) {
+        key[i] = it->first;
+        val[i] = it->second;
+        found[i] = 1;
+      }
+    } else {
+      auto it = m.upper_bound(std::min(q[i], kMaxUserKey));
+      if (it != m.begin()) {
+        --it;
+        key[i] = it->first;
+        val[i] = it->second;
+        found[i] = 1;
+      }
+    }
+  }
+}
+
 // §I-B range, as CSR: offsets[nq + 1] (first call with keys == nullptr only
 // fills offsets), then keys/vals of each query in ascending key order.
 void o1_range(void* h, const uint32_t* k1, const uint32_t* k2, uint64_t nq,

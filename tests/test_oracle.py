@@ -157,6 +157,20 @@ def test_map_oracle_vs_brute_force(b):
             ref = brute.range_query(log, int(k1[i]), int(k2[i]))
             got = list(zip(rk[off[i]:off[i + 1]].tolist(), rv[off[i]:off[i + 1]].tolist()))
             assert got == ref
+        # successor / predecessor: the nearest live key on each side, checked
+        # by testing every key the log mentions (and the closed form on an
+        # enumerated key range)
+        qn = np.concatenate([np.arange(19, dtype=np.uint32), np.array([0x7FFFFFFF, 0xFFFFFFFF], np.uint32)])
+        for succ in (True, False):
+            nk, nv, nf = o1.neighbor(qn, successor=succ)
+            for i, qq in enumerate(qn.tolist()):
+                ref = brute.neighbor(log, qq, successor=succ)
+                assert (ref is not None) == bool(nf[i])
+                if ref is not None:
+                    assert (int(nk[i]), int(nv[i])) == ref
+                    live = [k for k in range(18) if brute.state_of(log, k)[0]]
+                    side = [k for k in live if (k >= qq if succ else k <= qq)]
+                    assert int(nk[i]) == (min(side) if succ else max(side))
 
 
 @pytest.mark.parametrize("b", [1, 2, 3, 5, 8])
