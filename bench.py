@@ -55,6 +55,7 @@ def parse_args():
                         "serving: a Poisson stream of mixed requests through the serving engine")
     p.add_argument("--requests", type=int, default=10 ** 6, help="serving: requests in the trace")
     p.add_argument("--rate", type=float, default=3.0e5, help="serving: arrivals per second")
+    p.add_argument("--rate2", type=float, default=6.0e5, help="serving: a second, heavier load point (0: none)")
     p.add_argument("--flush-us", type=float, default=1000.0, help="serving: longest wait of a partial batch")
     p.add_argument("--preload-log2", type=int, default=28, help="serving: dictionary size before the stream")
     p.add_argument("--preload-batches", type=int, default=0,
@@ -705,7 +706,9 @@ def run_serving(args):
     b = 1 << args.b_log2
     pool_n = 1 << 26
     pa, pb, pc = workload.serving_pools(n=pool_n)
-    kind, arrival, start, size = workload.serving_trace(n_req=args.requests, rate=args.rate, pool_n=pool_n)
+    traces = {r: workload.serving_trace(n_req=args.requests, rate=r, pool_n=pool_n)
+              for r in [args.rate] + ([args.rate2] if args.rate2 else [])}
+    kind, arrival, start, size = traces[args.rate]
     wk, wa, ws, wz = workload.serving_trace(seed=workload.SERVING_SEED + 1, n_req=max(1000, args.requests // 100),
                                             rate=args.rate, pool_n=pool_n)
     keys_total = int(size.astype(np.int64).sum())
@@ -722,43 +725,50 @@ def run_serving(args):
             v = torch.randint(0, 1 << 31, (m,), device=dev, dtype=torch.int64, generator=gen).to(torch.int32)
             srv.preload(k, v)
             done_ += m
+
     budget = int(args.budget_gb * (1 << 30))
-    res = {}
+    results = {}
     clocks = None
     launches = 0
-    for name, policy in (("continuous", G.SERVE_CONTINUOUS), ("fixed", G.SERVE_FIXED)):
-        srv = G.Server(b, budget, flush_us=args.flush_us, group_keys=1 << 20, slots=3, range_cap=1 << 25,
-                       policy=policy, device=local)
-        srv.set_pool(pa, pb, pc)
-        preload(srv)
-        for _ in range(max(1, args.warmup)):
-            srv.run(wk, wa, ws, wz)       # warm-up: a short trace of the same mix
-        st0 = srv.stats()
-        sampler = ClockSampler(local) if name == "continuous" else None
-        if sampler:
-            sampler.start()
-            time.sleep(0.3)
-        l0 = G.kernel_launches()
-        out = srv.run(kind, arrival, start, size)
-        if name == "continuous":
-            launches = G.kernel_launches() - l0
-        if sampler:
-            clocks = sampler.stop()
-        st1 = srv.stats()
-        wall_s = out["wall_us"] / 1e6
-        res[name] = dict(latency=latency_stats(out, arrival), requests_per_s=len(kind) / wall_s,
-                         M_keys_per_s=keys_total / wall_s / 1e6, wall_s=wall_s,
-                         update_batches=int(out["update_batches"]), padded_ops=int(out["padded_ops"]),
-                         retrieval_groups=int(out["retrieval_groups"]), cleanups=int(out["cleanups"]),
-                         refused=int(out["refused"]), range_results=int(out["range_total"]),
-                         time_split=out["time_split"],
-                         levels=st0["levels"], device_bytes=st0["device_bytes"],
-                         resident_before=st0["resident"], resident_after=st1["resident"],
-                         all_ok=bool((out["status"] == 0).all()))
-        print("serving %s: %s" % (name, json.dumps(res[name])), file=sys.stderr, flush=True)
-        srv.close()
-        del srv
-        torch.cuda.synchronize(dev)
+    for rate, (t_kind, t_arr, t_start, t_size) in traces.items():
+        res = {}
+        t_keys = int(t_size.astype(np.int64).sum())
+        for name, policy in (("continuous", G.SERVE_CONTINUOUS), ("fixed", G.SERVE_FIXED)):
+            srv = G.Server(b, budget, flush_us=args.flush_us, group_keys=1 << 20, slots=3, range_cap=1 << 25,
+                           policy=policy, device=local)
+            srv.set_pool(pa, pb, pc)
+            preload(srv)
+            for _ in range(max(1, args.warmup)):
+                srv.run(wk, wa, ws, wz)       # warm-up: a short trace of the same mix
+            st0 = srv.stats()
+            first = rate == args.rate and name == "continuous"
+            sampler = ClockSampler(local) if first else None
+            if sampler:
+                sampler.start()
+                time.sleep(0.3)
+            l0 = G.kernel_launches()
+            out = srv.run(t_kind, t_arr, t_start, t_size)
+            if first:
+                launches = G.kernel_launches() - l0
+                clocks = sampler.stop()
+            st1 = srv.stats()
+            wall_s = out["wall_us"] / 1e6
+            res[name] = dict(latency=latency_stats(out, t_arr), requests_per_s=len(t_kind) / wall_s,
+                             M_keys_per_s=t_keys / wall_s / 1e6, wall_s=wall_s,
+                             arrivals_s=float(t_arr[-1]) / 1e6,
+                             update_batches=int(out["update_batches"]), padded_ops=int(out["padded_ops"]),
+                             retrieval_groups=int(out["retrieval_groups"]), cleanups=int(out["cleanups"]),
+                             refused=int(out["refused"]), range_results=int(out["range_total"]),
+                             time_split=out["time_split"],
+                             levels=st0["levels"], device_bytes=st0["device_bytes"],
+                             resident_before=st0["resident"], resident_after=st1["resident"],
+                             all_ok=bool((out["status"] == 0).all()))
+            print("serving %s at %.0f/s: %s" % (name, rate, json.dumps(res[name])), file=sys.stderr, flush=True)
+            srv.close()
+            del srv
+            torch.cuda.synchronize(dev)
+        results[rate] = res
+    res = results[args.rate]
     c = res["continuous"]
     span_s = float(arrival[-1]) / 1e6
     if rank == 0:
@@ -781,6 +791,8 @@ def run_serving(args):
             "vs_fixed": {"p50_ratio": res["fixed"]["latency"]["p50_ms"] / max(1e-9, c["latency"]["p50_ms"]),
                          "p99_ratio": res["fixed"]["latency"]["p99_ms"] / max(1e-9, c["latency"]["p99_ms"]),
                          "throughput_ratio": c["M_keys_per_s"] / max(1e-9, res["fixed"]["M_keys_per_s"])},
+            "heavier_load": ({"rate_per_s": args.rate2, "continuous": results[args.rate2]["continuous"],
+                              "fixed_batching": results[args.rate2]["fixed"]} if args.rate2 else None),
             "roofline": None, "cpu_baseline": None,
             "e2e": {"value": c["M_keys_per_s"], "unit": "M keys/s", "h2d_bytes_per_step": 21 * len(kind),
                     "d2h_bytes_per_step": None,

@@ -152,6 +152,19 @@ lsm_status lsm_count(lsm_t* h, const uint32_t* d_k1, const uint32_t* d_k2, uint6
                      uint32_t* d_count, void* stream);
 
 /*
+ * lsm_successor / lsm_predecessor - the order-based queries the paper's
+ * problem statement names beside lookup, count and range (§II-A footnote),
+ * read inclusively: the live pair with the smallest key >= q (successor) or
+ * the largest key <= q (predecessor).  d_key/d_val/d_found receive nq
+ * results; found = 0 (and key = value = 0) when there is none.  Keys above
+ * 2^31 - 2 are never live.  Asynchronous.
+ */
+lsm_status lsm_successor(lsm_t* h, const uint32_t* d_q, uint64_t nq, uint32_t* d_key, uint32_t* d_val,
+                         uint8_t* d_found, void* stream);
+lsm_status lsm_predecessor(lsm_t* h, const uint32_t* d_q, uint64_t nq, uint32_t* d_key, uint32_t* d_val,
+                           uint8_t* d_found, void* stream);
+
+/*
  * lsm_range - every live (key, value) with k1[i] <= key <= k2[i] (§III-E,
  * §IV-D, Fig. 2(d)), as compressed rows:
  *   d_offsets  nq + 1 device uint64: query i owns output slots

@@ -559,6 +559,33 @@ lsm_status lsm_lookup(lsm_t* h, const uint32_t* d_q, uint64_t nq, uint32_t* d_va
   return cuda_status(lookup_sorted_launch(ls, sk, sv, nq, d_val, d_found, st));
 }
 
+static lsm_status neighbor_call(lsm_t* h, const uint32_t* d_q, uint64_t nq, bool successor, uint32_t* d_key,
+                                uint32_t* d_val, uint8_t* d_found, void* stream) {
+  if (!h || (nq && (!d_q || !d_key || !d_val || !d_found))) return LSM_ERR_ARG;
+  if (nq == 0) return LSM_OK;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  LSM_TRY(join_side(h, st));
+  const LevelSet ls = full_levels(h);
+  if (ls.count == 0) {
+    LSM_TRY(cudaMemsetAsync(d_key, 0, sizeof(uint32_t) * nq, st));
+    LSM_TRY(cudaMemsetAsync(d_val, 0, sizeof(uint32_t) * nq, st));
+    LSM_TRY(cudaMemsetAsync(d_found, 0, nq, st));
+    return LSM_OK;
+  }
+  return cuda_status(neighbor_launch(ls, d_q, nq, successor, d_key, d_val, d_found, st));
+}
+
+lsm_status lsm_successor(lsm_t* h, const uint32_t* d_q, uint64_t nq, uint32_t* d_key, uint32_t* d_val,
+                         uint8_t* d_found, void* stream) {
+  return neighbor_call(h, d_q, nq, true, d_key, d_val, d_found, stream);
+}
+
+lsm_status lsm_predecessor(lsm_t* h, const uint32_t* d_q, uint64_t nq, uint32_t* d_key, uint32_t* d_val,
+                           uint8_t* d_found, void* stream) {
+  return neighbor_call(h, d_q, nq, false, d_key, d_val, d_found, stream);
+}
+
 lsm_status lsm_count(lsm_t* h, const uint32_t* d_k1, const uint32_t* d_k2, uint64_t nq, uint32_t* d_count,
                      void* stream) {
   if (!h || (nq && (!d_k1 || !d_k2 || !d_count))) return LSM_ERR_ARG;

@@ -325,6 +325,11 @@ cudaError_t count_launch(const LevelSet& ls, const uint32_t* k1, const uint32_t*
                          uint64_t nq, uint32_t* count, uint32_t* bounds, cudaStream_t st,
                          const uint32_t* perm = nullptr);
 
+// Successor (smallest live key >= q) or predecessor (largest live key <= q)
+// of every query: key, value and found flag (0 / 0 / 0 when none).
+cudaError_t neighbor_launch(const LevelSet& ls, const uint32_t* q, uint64_t nq, bool successor, uint32_t* key,
+                            uint32_t* val, uint8_t* found, cudaStream_t st);
+
 // Exclusive scan of n u32 into n + 1 u64 (out[n] = total).
 cudaError_t scan_launch(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* lookback,
                         uint32_t* tile_ctr, uint32_t* status, cudaStream_t st);

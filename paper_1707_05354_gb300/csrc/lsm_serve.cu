@@ -283,11 +283,13 @@ struct Run {
   int pending_ranges = 0;         // range groups awaiting their totals (no update admitted meanwhile)
   uint64_t range_pos = 0;         // next free entry of the caller's range output
 
-  bool want_updates(double now) const {
-    if (upd.empty() || pending_ranges > 0) return false;
+  // The update queue is ready for a group (ignoring range groups in flight).
+  bool updates_ready(double now) const {
+    if (upd.empty()) return false;
     if (upd_ops >= s->cfg.b || next >= t->n) return true;
     return now - t->arrival_us[upd.front()] >= s->cfg.flush_us;
   }
+  bool want_updates(double now) const { return pending_ranges == 0 && updates_ready(now); }
 
   // Writes the descriptors of requests [a, b) of `reqs` into the slot's
   // pinned arrays from index `first`; returns the keys.
@@ -636,7 +638,11 @@ struct Run {
       LSM_TRY_S(poll(now));
       while (!free_slots.empty()) {
         const bool wu = want_updates(now);
-        const bool wr = !ret.empty();
+        bool wr = !ret.empty();
+        // a ready update group held back only by range groups in flight goes
+        // before retrievals that arrived after it (else a steady stream of
+        // range groups would keep the barrier up and starve the updates)
+        if (!wu && wr && updates_ready(now) && t->arrival_us[upd.front()] <= t->arrival_us[ret.front()]) wr = false;
         if (!wu && !wr) break;
         const int sl = free_slots.back();
         free_slots.pop_back();

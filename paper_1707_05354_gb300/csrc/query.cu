@@ -222,6 +222,96 @@ __global__ void __launch_bounds__(kThreads) range_emit(LevelSet ls, uint64_t nq,
   }
 }
 
+// SUCCESSOR / PREDECESSOR (the order-based queries the problem statement's
+// footnote names beside the three retrievals, read inclusively): the live
+// pair with the smallest key >= q, or the largest key <= q.  Each level's
+// cursor starts at q's position; the levels are merged on the key from q
+// outwards (ascending for the successor, descending for the predecessor),
+// newest level first among equal keys; the first key whose newest element is
+// regular is the answer, every other key is skipped in all levels at once.
+// Within a level a key's newest element is the first of its run, so the
+// descending merge looks up each run's start.
+template <int L, bool kSucc>
+__global__ void __launch_bounds__(kThreads) neighbor_kernel(LevelSet ls, const uint32_t* __restrict__ q,
+                                                            uint64_t nq, uint32_t* __restrict__ out_k,
+                                                            uint32_t* __restrict__ out_v,
+                                                            uint8_t* __restrict__ out_f) {
+  for (uint64_t i = blockIdx.x * uint64_t(kThreads) + threadIdx.x; i < nq; i += uint64_t(gridDim.x) * kThreads) {
+    const uint32_t key = __ldg(q + i);
+    uint32_t rk = 0, rv = 0;
+    uint8_t rf = 0;
+    uint32_t cur[L], head[L];
+    bool live[L];  // the level still has a candidate on the search side
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      cur[l] = 0;
+      head[l] = 0;
+      live[l] = false;
+      if (l < ls.count) {
+        if (kSucc) {
+          if (key <= kMaxUserKey) {
+            cur[l] = level_lower_bound(ls, l, key << 1);
+            live[l] = cur[l] < ls.n[l];
+          }
+        } else {
+          const uint32_t kq = key < kMaxUserKey ? key : kMaxUserKey;
+          const uint32_t e = level_lower_bound(ls, l, (kq + 1u) << 1);  // first key > kq
+          live[l] = e > 0;
+          cur[l] = live[l] ? e - 1 : 0u;
+        }
+        if (live[l]) head[l] = key_of(__ldg(ls.keys[l] + cur[l]));
+      }
+    }
+    while (true) {
+      int best = -1;
+      uint32_t bk = 0;
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        if (!live[l]) continue;
+        const bool better = best < 0 || (kSucc ? head[l] < bk : head[l] > bk);  // strict: newest level wins ties
+        if (better) {
+          bk = head[l];
+          best = l;
+        }
+      }
+      if (best < 0) break;
+      // newest element of key bk: the run start in the newest level holding it
+      uint32_t p = cur[best];
+      if (!kSucc) p = lower_bound_kv(ls.keys[best], 0, cur[best] + 1, bk << 1);
+      const uint32_t kv = __ldg(ls.keys[best] + p);
+      if (kv & 1u) {
+        rk = bk;
+        rv = __ldg(ls.vals[best] + p);
+        rf = 1;
+        break;
+      }
+      // skip key bk in every level
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        if (!live[l] || head[l] != bk) continue;
+        const uint32_t* a = ls.keys[l];
+        if (kSucc) {
+          uint32_t nx = cur[l] + 1;
+          if (nx < ls.n[l] && key_of(__ldg(a + nx)) == bk) nx = upper_bound_key(a, nx + 1, ls.n[l], bk);
+          cur[l] = nx;
+          live[l] = nx < ls.n[l];
+          if (live[l]) head[l] = key_of(__ldg(a + nx));
+        } else {
+          const uint32_t st = lower_bound_kv(a, 0, cur[l] + 1, bk << 1);  // run start of bk
+          live[l] = st > 0;
+          if (live[l]) {
+            cur[l] = st - 1;
+            head[l] = key_of(__ldg(a + cur[l]));
+          }
+        }
+      }
+    }
+    out_k[i] = rk;
+    out_v[i] = rv;
+    out_f[i] = rf;
+  }
+}
+
 constexpr int kScanIPT = 8;
 constexpr int kScanTile = kThreads * kScanIPT;  // 2048
 constexpr uint64_t kLbAgg = 1ull << 62, kLbIncl = 2ull << 62, kLbMask = (1ull << 62) - 1;
@@ -394,6 +484,25 @@ cudaError_t multi_lookup_launch(const MultiArena& ar, const uint32_t* q, const u
   if (nq == 0) return cudaSuccess;
   count_launches(1);
   multi_lookup<<<persistent_grid(nq, kThreads, 152 * 8), kThreads, 0, st>>>(ar, q, qoff, nq, val, found);
+  return cudaGetLastError();
+}
+
+
+cudaError_t neighbor_launch(const LevelSet& ls, const uint32_t* q, uint64_t nq, bool successor, uint32_t* key,
+                            uint32_t* val, uint8_t* found, cudaStream_t st) {
+  if (nq == 0) return cudaSuccess;
+  const unsigned grid = persistent_grid(nq, kThreads, 152 * 8);
+  count_launches(1);
+#define LSM_NB(LL)                                                                                   \
+  (successor ? (neighbor_kernel<LL, true><<<grid, kThreads, 0, st>>>(ls, q, nq, key, val, found), 0) \
+             : (neighbor_kernel<LL, false><<<grid, kThreads, 0, st>>>(ls, q, nq, key, val, found), 0))
+  if (ls.count <= 1) LSM_NB(1);
+  else if (ls.count <= 2) LSM_NB(2);
+  else if (ls.count <= 4) LSM_NB(4);
+  else if (ls.count <= 8) LSM_NB(8);
+  else if (ls.count <= 16) LSM_NB(16);
+  else LSM_NB(kMaxLevels);
+#undef LSM_NB
   return cudaGetLastError();
 }
 

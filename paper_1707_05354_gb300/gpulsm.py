@@ -88,6 +88,8 @@ _SIGS = {
     "lsm_update_batch_ordered": ([_vp, _vp, _vp, _vp, _u64, _vp], _i32),
     "lsm_lookup": ([_vp, _vp, _u64, _vp, _vp, _vp], _i32),
     "lsm_count": ([_vp, _vp, _vp, _u64, _vp, _vp], _i32),
+    "lsm_successor": ([_vp, _vp, _u64, _vp, _vp, _vp, _vp], _i32),
+    "lsm_predecessor": ([_vp, _vp, _u64, _vp, _vp, _vp, _vp], _i32),
     "lsm_range": ([_vp, _vp, _vp, _u64, _vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp], _i32),
     "lsm_cleanup": ([_vp, _vp], _i32),
     "lsm_bulk_build": ([_vp, _vp, _vp, _u64, _vp], _i32),
@@ -180,6 +182,14 @@ def lsm_update_batch_ordered(h, d_keys, d_vals, d_is_delete, n, stream=None):
 
 def lsm_lookup(h, d_q, nq, d_val, d_found, stream=None):
     return _check(_lib.lsm_lookup(h, d_q, nq, d_val, d_found, stream), "lsm_lookup")
+
+
+def lsm_successor(h, d_q, nq, d_key, d_val, d_found, stream=None):
+    return _check(_lib.lsm_successor(h, d_q, nq, d_key, d_val, d_found, stream), "lsm_successor")
+
+
+def lsm_predecessor(h, d_q, nq, d_key, d_val, d_found, stream=None):
+    return _check(_lib.lsm_predecessor(h, d_q, nq, d_key, d_val, d_found, stream), "lsm_predecessor")
 
 
 def lsm_count(h, d_k1, d_k2, nq, d_count, stream=None):
@@ -481,6 +491,18 @@ class LSM:
         found = torch.empty(n, dtype=torch.uint8, device=self.device)
         lsm_lookup(self.h, _ptr(qd), n, _ptr(val), _ptr(found), _stream(self.device))
         return val, found
+
+    def neighbor(self, q, successor=True):
+        """(key, value, found) of each query's successor or predecessor."""
+        torch = _torch()
+        qd = as_device_u32(q, self.device)
+        n = qd.numel()
+        key = torch.empty(n, dtype=torch.int32, device=self.device)
+        val = torch.empty(n, dtype=torch.int32, device=self.device)
+        found = torch.empty(n, dtype=torch.uint8, device=self.device)
+        fn = lsm_successor if successor else lsm_predecessor
+        fn(self.h, _ptr(qd), n, _ptr(key), _ptr(val), _ptr(found), _stream(self.device))
+        return key, val, found
 
     def count(self, k1, k2):
         torch = _torch()

@@ -451,3 +451,33 @@ def test_bulk_build(g, b, n, key_space):
     with pytest.raises(g.LSMError):
         lsm.bulk_build(keys[:10], vals[:10])   # only into an empty dictionary
     assert lsm.device_errors() == 0
+
+
+@pytest.mark.parametrize("b,key_space,ncalls,cleanup", [(1, 12, 30, False), (7, 40, 25, False),
+                                                        (64, 500, 30, True), (1000, 5000, 20, False)])
+def test_successor_predecessor(g, b, key_space, ncalls, cleanup):
+    """Order-based neighbour queries against the ordered-map oracle, on logs
+    with deletes and overwrites (several versions of a key across levels,
+    deleted keys to skip), after a cleanup (placebos at the end), and at the
+    edges of the key domain."""
+    rng = np.random.default_rng(b * 7 + key_space)
+    lsm = g.LSM(b, (ncalls + 2) * b)
+    o1 = oracle.MapOracle(b)
+    for _ in range(ncalls):
+        n = int(rng.integers(1, b + 1))
+        keys = rng.integers(0, key_space, size=n).astype(np.uint32)
+        vals = rng.integers(0, 1 << 32, size=n, dtype=np.uint64).astype(np.uint32)
+        dele = (rng.random(n) < 0.35).astype(np.uint8)
+        lsm.update(keys, vals, dele)
+        o1.call("update", keys, vals, dele)
+    if cleanup:
+        lsm.cleanup()
+    q = np.concatenate([np.arange(key_space + 2, dtype=np.uint32),
+                        np.array([0, 0x7FFFFFFE, 0x7FFFFFFF, 0xFFFFFFFF], np.uint32)])
+    for succ in (True, False):
+        k, v, f = lsm.neighbor(q, successor=succ)
+        ek, ev, ef = o1.neighbor(q, successor=succ)
+        np.testing.assert_array_equal(f.cpu().numpy(), ef)
+        np.testing.assert_array_equal(u32(k), ek)
+        np.testing.assert_array_equal(u32(v), ev)
+    assert lsm.device_errors() == 0
