@@ -50,10 +50,12 @@ def parse_args():
     p.add_argument("--lookup-mode", type=int, default=0, help="0 auto, 1 direct, 2 sorted")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="paper", choices=["paper", "batched", "serving"],
+    p.add_argument("--workload", default="paper", choices=["paper", "batched", "serving", "sweep"],
                    help="paper: b=2^20 plain dictionary (default); batched: 256 dictionaries per round; "
                         "serving: a Poisson stream of mixed requests through the serving engine")
     p.add_argument("--requests", type=int, default=10 ** 6, help="serving: requests in the trace")
+    p.add_argument("--sweep-b", default="16,18,20,22,24", help="sweep: log2 of the batch sizes")
+    p.add_argument("--sweep-total-log2", type=int, default=28, help="sweep: updates per point")
     p.add_argument("--rate", type=float, default=3.0e5, help="serving: arrivals per second")
     p.add_argument("--rate2", type=float, default=6.0e5, help="serving: a second, heavier load point (0: none)")
     p.add_argument("--flush-us", type=float, default=1000.0, help="serving: longest wait of a partial batch")
@@ -804,12 +806,166 @@ def run_serving(args):
     return 0
 
 
+# ------------------------------------------------------------------ sweep --
+SWEEP_METRIC = "M updates/s over the update/delete sweep (b = 2^16 .. 2^24, ~2^28 updates per point)"
+
+
+def sweep_batches_on_device(torch, dev, b, nb, frac, dist, seed):
+    """The sweep recipe drawn on the device (inputs of a timing run): keys
+    uniform in [0, 2^30) or Zipf(1.1) over ranks 1 .. 2^30 (inverse transform
+    of the continuous power law, ranks mapped to keys by rank * 0x9E3779B1 mod
+    2^30); batch 0 all inserts, later batches round(frac * b) deletes of keys
+    drawn uniformly from the earlier inserts, shuffled among the inserts."""
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    space = 1 << 30
+    keys = torch.empty(nb * b, dtype=torch.int64, device=dev)
+    dele = torch.zeros(nb * b, dtype=torch.uint8, device=dev)
+    vals = torch.randint(0, 1 << 31, (nb * b,), device=dev, dtype=torch.int64, generator=gen).to(torch.int32)
+    inserted = torch.empty(nb * b, dtype=torch.int64, device=dev)
+    n_ins_total = 0
+    for t in range(nb):
+        n_del = 0 if t == 0 else int(round(b * frac))
+        n_ins = b - n_del
+        if dist == "zipf":
+            u = torch.rand(n_ins, device=dev, dtype=torch.float64, generator=gen)
+            a = 1.0 - 1.1
+            rank = torch.floor(((float(space) ** a - 1.0) * u + 1.0) ** (1.0 / a)).clamp_(1, space).to(torch.int64)
+            ins = (rank * 0x9E3779B1) % space
+        else:
+            ins = torch.randint(0, space, (n_ins,), device=dev, dtype=torch.int64, generator=gen)
+        if n_del:
+            idx = torch.randint(0, n_ins_total, (n_del,), device=dev, dtype=torch.int64, generator=gen)
+            batch = torch.cat([ins, inserted[idx]])
+            flags = torch.cat([torch.zeros(n_ins, dtype=torch.uint8, device=dev),
+                               torch.ones(n_del, dtype=torch.uint8, device=dev)])
+            perm = torch.randperm(b, device=dev, generator=gen)
+            batch, flags = batch[perm], flags[perm]
+        else:
+            batch, flags = ins, torch.zeros(b, dtype=torch.uint8, device=dev)
+        keys[t * b:(t + 1) * b] = batch
+        dele[t * b:(t + 1) * b] = flags
+        inserted[n_ins_total:n_ins_total + n_ins] = ins
+        n_ins_total += n_ins
+    return keys.to(torch.int32), vals, dele
+
+
+def run_sweep(args):
+    import torch
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1707_05354_gb300 import gpulsm as G
+    st = torch.cuda.current_stream(dev)
+    sp = st.cuda_stream
+    total = 1 << args.sweep_total_log2
+    nq = 1 << 22
+    points = []
+    for bl in [int(x) for x in args.sweep_b.split(",")]:
+        b = 1 << bl
+        nb = total // b
+        for dist in ("uniform", "zipf"):
+            for frac in (0.0, 0.25, 0.5):
+                keys, vals, dele = sweep_batches_on_device(torch, dev, b, nb, frac, dist,
+                                                           1707053503 + bl * 10 + int(frac * 4))
+                h = G.lsm_create(b, total, local)
+                kp, vp, dp = keys.data_ptr(), vals.data_ptr(), dele.data_ptr()
+
+                def updates():
+                    G.lsm_reset(h)
+                    for t in range(nb):
+                        G.lsm_update_batch(h, kp + 4 * t * b, vp + 4 * t * b, dp + t * b, b, sp)
+                    G.lsm_stream_wait(h, sp)
+
+                updates()  # warm-up pass
+                a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize(dev)
+                a.record(st)
+                updates()
+                z.record(st)
+                z.synchronize()
+                upd_s = a.elapsed_time(z) / 1000.0
+                # live keys (for the query widths): counts over 2^16 slices of the key space
+                lo = torch.arange(1 << 16, device=dev, dtype=torch.int64) << 14
+                hi = (lo + (1 << 14) - 1).to(torch.int32)
+                lo = lo.to(torch.int32)
+                cnt = torch.empty(1 << 16, dtype=torch.int32, device=dev)
+                G.lsm_count(h, lo.data_ptr(), hi.data_ptr(), 1 << 16, cnt.data_ptr(), sp)
+                n_live = max(1, int(cnt.to(torch.int64).sum().item()))
+                ranges = {}
+                gen = torch.Generator(device=dev)
+                gen.manual_seed(bl)
+                for L in (8, 64, 512):
+                    w = max(1, int(round(L * (1 << 30) / n_live)))
+                    k1 = torch.randint(0, (1 << 30) - w, (nq,), device=dev, dtype=torch.int64, generator=gen)
+                    k2 = (k1 + w - 1).to(torch.int32)
+                    k1 = k1.to(torch.int32)
+                    off = torch.empty(nq + 1, dtype=torch.int64, device=dev)
+                    capq = int(1.3 * L * nq) + (1 << 20)
+                    rk = torch.empty(capq, dtype=torch.int32, device=dev)
+                    rv = torch.empty(capq, dtype=torch.int32, device=dev)
+                    c = torch.empty(nq, dtype=torch.int32, device=dev)
+                    for rep in range(2):
+                        torch.cuda.synchronize(dev)
+                        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                        e0.record(st)
+                        G.lsm_count(h, k1.data_ptr(), k2.data_ptr(), nq, c.data_ptr(), sp)
+                        e1.record(st)
+                        s_, tot = G.lsm_range(h, k1.data_ptr(), k2.data_ptr(), nq, off.data_ptr(), rk.data_ptr(),
+                                              rv.data_ptr(), capq, sp)
+                        e2.record(st)
+                        e2.synchronize()
+                    ranges[str(L)] = {"width": w, "count_M_per_s": nq / (e0.elapsed_time(e1) / 1000) / 1e6,
+                                      "range_M_per_s": nq / (e1.elapsed_time(e2) / 1000) / 1e6,
+                                      "results": int(tot), "status": int(s_)}
+                resident = G.lsm_stats(h)["resident"]
+                torch.cuda.synchronize(dev)
+                c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                c0.record(st)
+                G.lsm_cleanup(h, sp)
+                c1.record(st)
+                c1.synchronize()
+                clean_ms = c0.elapsed_time(c1)
+                r_after = G.lsm_stats(h)["r"]
+                errs = G.lsm_get_option(h, G.LSM_OPT_DEVICE_ERROR)
+                G.lsm_destroy(h)
+                m = nb.bit_length() - 1
+                pt = {"b_log2": bl, "dist": dist, "delete_frac": frac, "batches": nb,
+                      "M_updates_per_s": nb * b / upd_s / 1e6, "update_ms": 1000 * upd_s,
+                      "algorithmic_B_per_update": 8 * m + 16,
+                      "hbm_frac": (8 * m + 16) * nb * b / upd_s / 1e9 / float(measured_peaks()[0]["hbm_gbs"]),
+                      "live_keys": n_live, "ranges": ranges, "cleanup_ms": clean_ms,
+                      "cleanup_G_elements_per_s": resident / (clean_ms / 1000) / 1e9, "r_after_cleanup": r_after,
+                      "device_errors": errs}
+                points.append(pt)
+                print("sweep point: %s" % json.dumps(pt), file=sys.stderr, flush=True)
+                del keys, vals, dele
+                torch.cuda.empty_cache()
+    rates = [p["M_updates_per_s"] for p in points]
+    geo = float(np.exp(np.mean(np.log(rates))))
+    if rank == 0:
+        line = {"metric": SWEEP_METRIC, "value": geo, "unit": "M updates/s (geometric mean over points)",
+                "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": sum(p["update_ms"] for p in points),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                "data": "synthetic, drawn on the device (uniform keys over 2^30 or Zipf(1.1) by inverse transform; "
+                        "deletes of earlier inserted keys)",
+                "config": {"workload": "update/delete sweep: b = 2^%s, 2^%d updates per point, delete fraction "
+                                       "0/25/50%%, uniform or Zipf(1.1) keys; 2^22 count and range queries at "
+                                       "expected sizes 8/64/512; cleanup" % (args.sweep_b, args.sweep_total_log2),
+                           "l2": "inputs larger than L2", "parallelism": "single GPU"},
+                "points": points, "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":

@@ -153,9 +153,13 @@ __device__ __forceinline__ uint32_t merge_windows(const LevelSet& ls, const uint
       if (head[l] == bk) {  // past every element of key bk in level l
         const uint32_t* a = ls.keys[l];
         uint32_t q = cur[l] + 1;
-        if (q < hi[l] && key_of(__ldg(a + q)) == bk) q = upper_bound_key(a, q + 1, hi[l], bk);
+        uint32_t nk = q < hi[l] ? key_of(__ldg(a + q)) : 0xFFFFFFFFu;
+        if (nk == bk) {
+          q = upper_bound_key(a, q + 1, hi[l], bk);
+          nk = q < hi[l] ? key_of(__ldg(a + q)) : 0xFFFFFFFFu;
+        }
         cur[l] = q;
-        head[l] = q < hi[l] ? key_of(__ldg(a + q)) : 0xFFFFFFFFu;
+        head[l] = nk;
       }
     }
   }
