@@ -44,9 +44,7 @@ struct lsm_t {
   int l0_buf = -1;           // the buffer holding level 0, or -1 (level 0 in the level array)
   int last_buf = 0;          // buffer of the latest batch
   cudaStream_t side = nullptr;           // folds
-  cudaStream_t sortst = nullptr;         // batch sorts, at the highest stream priority
-  cudaEvent_t ev_in = nullptr;           // caller's stream, where a batch's inputs are ready
-  cudaEvent_t ev_sorted = nullptr;       // sort stream, after a batch's sort
+  cudaEvent_t ev_sorted = nullptr;       // caller's stream, after a batch's sort
   cudaEvent_t ev_side = nullptr;         // internal stream, after its latest work
   cudaEvent_t ev_free[3] = {};           // internal stream, after the fold that read buffer j
   bool side_pending = false;
@@ -136,8 +134,6 @@ void free_all(lsm_t* h) {
   for (void* p : dptrs)
     if (p) cudaFree(p);
   if (h->side) cudaStreamDestroy(h->side);
-  if (h->sortst) cudaStreamDestroy(h->sortst);
-  if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_sorted) cudaEventDestroy(h->ev_sorted);
   if (h->ev_side) cudaEventDestroy(h->ev_side);
   for (cudaEvent_t e : h->ev_free)
@@ -283,15 +279,7 @@ lsm_status apply_batch(lsm_t* h, int mode, const uint32_t* keys, const uint32_t*
   // that last read it
   int j = (h->last_buf + 1) % kBatchBufs;
   if (j == h->l0_buf) j = (j + 1) % kBatchBufs;
-  // The sort runs on the handle's high-priority stream: after the caller's
-  // work so far (its inputs) and after the fold that last read buffer j; the
-  // caller's stream then waits for it (inputs consumed, level 0 written).
-  // Its CTAs are scheduled ahead of the fold's, which keeps the chain of
-  // batch sorts -- the critical path of a run of inserts -- short.
-  cudaStream_t ss = h->sortst;
-  LSM_TRY(cudaEventRecord(h->ev_in, st));
-  LSM_TRY(cudaStreamWaitEvent(ss, h->ev_in, 0));
-  LSM_TRY(cudaStreamWaitEvent(ss, h->ev_free[j], 0));
+  LSM_TRY(cudaStreamWaitEvent(st, h->ev_free[j], 0));
   SortArgs a{};
   a.mode = mode;
   a.in_keys = keys;
@@ -306,12 +294,10 @@ lsm_status apply_batch(lsm_t* h, int mode, const uint32_t* keys, const uint32_t*
   a.fence = buf_fence(h, j);
   a.fshift = h->fshift[0];
   {
-    ProfScope ps(h, LSM_PROF_SORT, 16.0 * h->b, ss);
+    ProfScope ps(h, LSM_PROF_SORT, 16.0 * h->b, st);
     if (checked) *reinterpret_cast<volatile uint32_t*>(h->h_status) = 0u;
-    LSM_TRY(sort_launch(a, h->sws, ss, checked ? h->d_status_map : nullptr, h->ev));
+    LSM_TRY(sort_launch(a, h->sws, st, checked ? h->d_status_map : nullptr, h->ev));
   }
-  LSM_TRY(cudaEventRecord(h->ev_sorted, ss));
-  LSM_TRY(cudaStreamWaitEvent(st, h->ev_sorted, 0));
   if (checked) {
     LSM_TRY(cudaEventSynchronize(h->ev));
     if (*reinterpret_cast<volatile uint32_t*>(h->h_status) & kErrBadKey) return LSM_ERR_KEY_RANGE;
@@ -322,6 +308,7 @@ lsm_status apply_batch(lsm_t* h, int mode, const uint32_t* keys, const uint32_t*
     h->r += 1;
     return LSM_OK;
   }
+  LSM_TRY(cudaEventRecord(h->ev_sorted, st));
   cudaStream_t side = h->side;
   LSM_TRY(cudaStreamWaitEvent(side, h->ev_sorted, 0));
   FoldArgs f{};
@@ -494,12 +481,6 @@ lsm_status lsm_create(lsm_t** out, uint32_t b, uint64_t max_elements, int device
   if (e == cudaSuccess) e = cudaMemset(h->d_bk, 0, sizeof(uint32_t) * kBatchBufs * bpad);
   if (e == cudaSuccess) e = cudaMemset(h->d_bv, 0, sizeof(uint32_t) * kBatchBufs * bpad);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
-  {
-    int least = 0, greatest = 0;
-    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->sortst, cudaStreamNonBlocking, greatest);
-  }
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_sorted, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_side, cudaEventDisableTiming);
   for (int j = 0; j < kBatchBufs; ++j)
