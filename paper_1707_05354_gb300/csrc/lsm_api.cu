@@ -46,7 +46,7 @@ struct lsm_t {
   cudaStream_t side = nullptr;           // folds
   cudaEvent_t ev_sorted = nullptr;       // caller's stream, after a batch's sort
   cudaEvent_t ev_side = nullptr;         // internal stream, after its latest work
-  cudaEvent_t ev_free[3] = {};           // internal stream, after the fold that read buffer j
+  cudaEvent_t ev_free[kBatchBufs] = {};  // internal stream, after the fold that read buffer j
   bool side_pending = false;
   uint32_t* d_tk = nullptr;  // sort ping-pong (b + slack)
   uint32_t* d_tv = nullptr;
@@ -54,8 +54,8 @@ struct lsm_t {
   uint32_t* d_part = nullptr;
   uint64_t part_words = 0;
   uint32_t* d_fence = nullptr;  // prefix index per level (L tables) + the sorted batch's
-  uint64_t fence_off[kMaxLevels + 4] = {};  // L levels, then the batch buffers
-  int fshift[kMaxLevels + 4] = {};  // per level; [L ..] = the batch buffers
+  uint64_t fence_off[kMaxLevels + kBatchBufs + 1] = {};  // L levels, then the batch buffers
+  int fshift[kMaxLevels + kBatchBufs + 1] = {};  // per level; [L ..] = the batch buffers
   uint32_t* d_misc = nullptr;  // [0] sticky errors [1] key check [2] tile ctr [3] tile ctr
   uint64_t* d_u64 = nullptr;   // [0] cleanup count
   uint32_t* h_status = nullptr;  // mapped pinned word: key check of the current batch
@@ -176,8 +176,6 @@ struct ProfScope {
     h->prof_pending.push_back({group, a, b, bytes});
   }
 };
-
-constexpr int kBatchBufs = 3;
 
 uint32_t* buf_keys(const lsm_t* h, int j) { return h->d_bk + uint64_t(j) * h->bpad; }
 uint32_t* buf_vals(const lsm_t* h, int j) { return h->d_bv + uint64_t(j) * h->bpad; }

@@ -7,6 +7,12 @@
 
 namespace gpulsm {
 
+// Sorted-batch buffers of a plain dictionary.  A batch is sorted into the
+// next free buffer while earlier folds still read theirs, so the sorts of a
+// run of inserts can get ahead of the folds by up to kBatchBufs - 2 batches
+// (one buffer may hold level 0).
+constexpr int kBatchBufs = 6;
+
 // Full levels of the dictionary, newest first (the host's view of r).
 LevelSet dict_levels(lsm_t* h);
 // Makes `st` wait for the folds in flight on the handle's internal stream.

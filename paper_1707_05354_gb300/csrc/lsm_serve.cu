@@ -181,12 +181,13 @@ uint64_t slot_bytes(const lsm_server_config& c, uint32_t max_levels, uint32_t ma
 }
 
 // Device bytes of a dictionary with L levels of batch size b, as lsm_create
-// and a cleanup allocate them (levels, cleanup scratch, three sorted-batch
+// and a cleanup allocate them (levels, cleanup scratch, the sorted-batch
 // buffers, sort scratch, prefix indexes, co-rank table, query scratch).
 uint64_t dict_bytes(uint32_t b, uint32_t L) {
   const uint64_t cap = uint64_t(b) * ((1ull << L) - 1);
   const uint64_t bp = rup(b, 32) + 32;
-  return 8 * cap + 8 * cap + 8 * (cap / 2048 + 2) + 5 * 8 * bp + cap / 2 + 16 * bp + 4 * (cap / 2048 + 2) * (L + 1) +
+  return 8 * cap + 8 * cap + 8 * (cap / 2048 + 2) + (kBatchBufs + 2) * 8 * bp + cap / 2 + 16 * bp +
+         4 * (cap / 2048 + 2) * (L + 1) +
          (64ull << 20);
 }
 
