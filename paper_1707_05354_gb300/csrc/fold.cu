@@ -12,11 +12,14 @@
 //
 //   partition   one warp per output tile boundary p finds the co-rank vector
 //               (how many elements of each source precede position p).  The
-//               sources' prefix indexes (fences) give the 2^15-key bin
-//               holding the p-th element in a few probes; a bisection over
-//               the low 15 key bits inside that bin, each lane keeping a
-//               bracket in its own source, finds the key; the elements of
-//               that key are then split among the sources in rank order.
+//               sources' prefix indexes (fences) give the bin holding the
+//               p-th element: each round the 32 lanes probe 31 bins of the
+//               bracket at once.  A bin of at most 32 elements (the usual
+//               case: about 8 per source) is loaded one element per lane and
+//               ranked by (key, source rank, index); a crowded bin is
+//               bisected over its key range instead, each lane keeping a
+//               bracket in its own source, and the elements of the key found
+//               are split among the sources in rank order.
 //   merge       one tile per CTA: the TMA engine copies the k + 1 source
 //               segments into shared memory (16-byte aligned supersets); a
 //               left-deep chain of merge-path merges in shared memory (ranks
@@ -48,7 +51,8 @@ struct TileGeom {
   static constexpr uint32_t kSlotCap = (kTile + 8 * kMaxSources + 15) / 16 * 16;  // TMA slots + slack
   static constexpr size_t kSmem = 2 * size_t(kSlotCap) * sizeof(uint32_t) + 2 * size_t(kTile) * sizeof(uint2);
 };
-static_assert(TileGeom<8>::kTile == kFoldTile, "the plain fold uses 8 outputs per thread");
+constexpr int kFoldE = kFoldTile / kThreads;  // outputs per thread of the plain fold
+static_assert(TileGeom<kFoldE>::kTile == kFoldTile, "the plain fold's tile");
 
 // Slot of pair q of a merge step in shared memory: q with its low 4 bits
 // XORed by bits 4..7.  A thread writing 8 consecutive pairs (q = 8 t + e)
@@ -57,59 +61,102 @@ static_assert(TileGeom<8>::kTile == kFoldTile, "the plain fold uses 8 outputs pe
 // consecutive pairs stay a permutation of one 128-byte row.
 __device__ __forceinline__ uint32_t psw(uint32_t q) { return q ^ ((q >> 4) & 15u); }
 
-// Sum over the sources of their counts below bin P at the common shift
-// (lanes >= S contribute 0); cs = common shift - the lane's own shift.
-__device__ __forceinline__ uint64_t fence_sum(const uint32_t* f, bool act, uint32_t P, int cs, int fs,
-                                              uint32_t n) {
-  return warp_sum<uint64_t>(act ? fence_at(f, fs, n, P << cs) : 0u);
-}
-
 // This lane's co-rank at output position p < total (warp-collective; lane j
-// holds source j when act).
+// holds source j when act, the active lanes being 0 .. S-1).
 __device__ __forceinline__ uint32_t corank_lane(bool act, const uint32_t* a, const uint32_t* f, int fs,
                                                 uint32_t n, uint64_t p, uint64_t total) {
+  const uint32_t lane = lane_id();
+  const int S = __popc(__ballot_sync(0xffffffffu, act));
   // The search runs at the coarsest of the sources' prefix-index resolutions
   // (shift fc), which every source's table can answer.
   int fc = act ? fs : 0;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) fc = max(fc, __shfl_xor_sync(0xffffffffu, fc, o));
-  const int cs = fc - fs;
+  const int cs = act ? fc - fs : 0;
   const uint32_t nbins = 1u << (32 - fc);
-  // 1. The bin: largest P with C(P) <= p, C(P) = sum of fence_j[P]
-  //    (C(0) = 0 <= p < C(nbins) = total).  Start from the proportional
-  //    guess, gallop to a bracket, then bisect.
-  uint32_t lo, hi;
-  {
-    uint32_t g = uint32_t((p * nbins) / total);
-    if (g >= nbins) g = nbins - 1;
-    if (fence_sum(f, act, g, cs, fs, n) <= p) {
-      lo = g;
-      uint32_t step = 1;
-      while (true) {
-        hi = lo + step < nbins ? lo + step : nbins;
-        if (hi == nbins || fence_sum(f, act, hi, cs, fs, n) > p) break;
-        lo = hi;
-        step <<= 1;
-      }
-    } else {
-      hi = g;
-      uint32_t step = 1;
-      while (true) {
-        lo = hi > step ? hi - step : 0u;
-        if (lo == 0 || fence_sum(f, act, lo, cs, fs, n) <= p) break;
-        hi = lo;
-        step <<= 1;
-      }
-    }
-    while (hi - lo > 1) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (fence_sum(f, act, mid, cs, fs, n) <= p) lo = mid; else hi = mid;
-    }
+  uint32_t bmin = 0, bmax = 0;
+  if (act) {
+    bmin = __ldg(f + fence_bins(fs) + 2);
+    bmax = __ldg(f + fence_bins(fs) + 3);
   }
-  // 2. Smallest key x in the bin with #{key <= x} > p.  Invariant per lane:
-  //    blo = #{key <= xlo - 1}, bhi = #{key <= xhi} in this lane's source.
-  //    A bin at shift fc holds the keys [P << (fc - 1), (P + 1) << (fc - 1)).
+  // 1. The bin: largest P with C(P) <= p, C(P) = sum over the sources of
+  //    their counts below bin P (C(0) = 0 <= p < C(nbins) = total).  The
+  //    warp splits into G = 32 / S' groups of S' >= S lanes (lane j of a
+  //    group reads source j); each round the groups evaluate C at the
+  //    points that split the bracket into G parts (2 for a single group),
+  //    one table load per lane, and the bracket shrinks to the part where
+  //    C crosses p.
+  int lg = 0;
+  while ((1 << lg) < S) ++lg;
+  const uint32_t G = 32u >> lg, q = lane >> lg, j = lane & ((1u << lg) - 1u);
+  const bool jact = j < uint32_t(S);
+  const uint32_t* fj = reinterpret_cast<const uint32_t*>(
+      __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(f), int(j)));
+  const int csj = __shfl_sync(0xffffffffu, cs, int(j));
+  const uint32_t bminj = __shfl_sync(0xffffffffu, bmin, int(j)), bmaxj = __shfl_sync(0xffffffffu, bmax, int(j));
+  const uint32_t nj = __shfl_sync(0xffffffffu, n, int(j));
+  uint32_t lo = 0, hi = nbins;
+  // at most log2(nbins) <= 32 rounds; the bound only guards the loop
+  for (int round = 0; hi - lo > 1 && round < 64; ++round) {
+    const uint32_t span = hi - lo;
+    uint32_t P;
+    bool valid;
+    if (span <= G) {
+      P = lo + 1 + q;
+      valid = P < hi;
+    } else {  // probes split the bracket into max(G, 2) equal parts
+      const int parts = lg < 5 ? 5 - lg : 1;
+      P = lo + uint32_t((uint64_t(q + 1) * span) >> parts);
+      valid = q + 1 < (1u << parts);
+    }
+    uint32_t c = 0;  // C(P) <= total < 2^32
+    if (jact && valid) {
+      const uint32_t Pj = P << csj;
+      // an entry inside the populated range is always loaded, then selected
+      const uint32_t v = __ldg(fj + (Pj <= bminj ? bminj : (Pj > bmaxj ? bmaxj : Pj)));
+      c = Pj <= bminj ? 0u : (Pj > bmaxj ? nj : v);
+    }
+    for (uint32_t o = (1u << lg) >> 1; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, int(o));
+    // C is non-decreasing and the probes ascend with the group: a prefix
+    const int cnt = __popc(__ballot_sync(0xffffffffu, j == 0 && valid && c <= p));
+    const uint32_t p_lo = __shfl_sync(0xffffffffu, P, ((cnt + 31) & 31) << lg & 31);
+    const uint32_t p_hi = __shfl_sync(0xffffffffu, P, (cnt << lg) & 31);
+    const bool v_hi = __shfl_sync(0xffffffffu, valid, (cnt << lg) & 31);
+    if (cnt > 0) lo = p_lo;
+    if (uint32_t(cnt) < G && v_hi) hi = p_hi;
+  }
+  // 2. The bin's elements: [blo, bhi) of each source, need = p - C(lo) of
+  //    them precede p.
   uint32_t blo = act ? fence_at(f, fs, n, lo << cs) : 0u, bhi = act ? fence_at(f, fs, n, (lo + 1) << cs) : 0u;
+  const uint32_t cnt = bhi - blo;
+  const uint32_t tot = warp_sum(cnt);
+  const uint64_t need = p - warp_sum<uint64_t>(blo);
+  if (tot <= 32) {
+    // One element per lane in source order (which is the tie order); its
+    // rank in the bin by (key, lane) says whether it precedes p.
+    const uint32_t off = warp_incl_scan(cnt) - cnt;
+    int j = 0;
+    for (int q = 0; q < S; ++q)
+      if (lane >= __shfl_sync(0xffffffffu, off + cnt, q)) j = q + 1;
+    const bool has = lane < tot;
+    const uint32_t* aj =
+        reinterpret_cast<const uint32_t*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(a), j & 31));
+    const uint32_t offj = __shfl_sync(0xffffffffu, off, j & 31), bloj = __shfl_sync(0xffffffffu, blo, j & 31);
+    const uint32_t key = has ? key_of(__ldg(aj + bloj + (lane - offj))) : 0xFFFFFFFFu;
+    uint32_t rank = 0;
+    for (uint32_t q = 0; q < tot; ++q) {
+      const uint32_t kq = __shfl_sync(0xffffffffu, key, q);
+      rank += (kq < key || (kq == key && q < lane)) ? 1u : 0u;
+    }
+    const uint32_t before = __ballot_sync(0xffffffffu, has && rank < need);
+    const uint32_t mask = cnt ? ((cnt >= 32 ? 0xFFFFFFFFu : ((1u << cnt) - 1u)) << off) : 0u;
+    return blo + uint32_t(__popc(before & mask));
+  }
+  // A crowded bin (many equal or close keys): smallest key x in the bin
+  // with #{key <= x} > p by bisection over the bin's key range.
+  // Invariant per lane: blo = #{key <= xlo - 1}, bhi = #{key <= xhi} in
+  // this lane's source.  A bin at shift fc holds the keys
+  // [P << (fc - 1), (P + 1) << (fc - 1)).
   uint32_t xlo = lo << (fc - 1), xhi = ((lo + 1) << (fc - 1)) - 1;
   while (xlo < xhi) {
     const uint32_t mid = xlo + ((xhi - xlo) >> 1);
@@ -123,13 +170,13 @@ __device__ __forceinline__ uint32_t corank_lane(bool act, const uint32_t* a, con
       blo = u;
     }
   }
-  // 3. blo / bhi are now the lower / upper bound of key x in this source; the
-  //    p - sum(blo) elements of key x that precede p come from the lowest ranks.
-  const uint32_t cnt = bhi - blo;
-  const uint64_t need = p - warp_sum<uint64_t>(blo);
-  const uint64_t excl = warp_incl_scan<uint64_t>(cnt) - cnt;
+  // blo / bhi are now the lower / upper bound of key x in this source; the
+  // p - sum(blo) elements of key x that precede p come from the lowest ranks.
+  const uint32_t kc = bhi - blo;
+  const uint64_t kneed = p - warp_sum<uint64_t>(blo);
+  const uint64_t excl = warp_incl_scan<uint64_t>(kc) - kc;
   uint64_t take = 0;
-  if (need > excl) take = (need - excl) < cnt ? (need - excl) : cnt;
+  if (kneed > excl) take = (kneed - excl) < kc ? (kneed - excl) : kc;
   return blo + uint32_t(take);
 }
 
@@ -276,7 +323,7 @@ struct MergeShared {
   uint32_t rstart[kMaxSources], rlen[kMaxSources];
   uint32_t a0[kMaxSources], span[kMaxSources], slot[kMaxSources];
   uint32_t scan[kThreads / 32], last[kThreads / 32];
-  uint32_t prev_key, ok, ngap, landed;
+  uint32_t prev_mask, ok, ngap, landed;
   FenceGap gaps[kFenceGapSlots];
   uint64_t prefix;
 };
@@ -303,19 +350,19 @@ __device__ __forceinline__ bool merge_tile(const FoldSources& src, uint64_t tota
   uint2* Y = X + G::kTile;
 
   // Segment of each source in this tile, and its 16-byte aligned superset.
+  // The copy window starts one element early when there is one: the key
+  // just before the tile in merged order (the largest key among the
+  // sources' elements before their co-ranks) is then read from shared
+  // memory instead of by a dependent global load before the copies.
   if (warp == 0) {
-    uint32_t c0 = 0, c1 = 0, a0 = 0, span = 0, prev = 0;
-    bool has_prev = false;
+    uint32_t c0 = 0, c1 = 0, a0 = 0, span = 0;
     if (lane < uint32_t(S)) {
       c0 = part[uint64_t(tile) * pstride + lane];
       c1 = part[uint64_t(tile + 1) * pstride + lane];
-      if (c1 > c0) {
-        a0 = c0 & ~3u;
+      const uint32_t lo = c0 > 0 ? c0 - 1 : 0u;
+      if (c1 > lo) {
+        a0 = lo & ~3u;
         span = ((c1 + 3u) & ~3u) - a0;
-      }
-      if (c0 > 0) {
-        has_prev = true;
-        prev = key_of(__ldg(src.keys[lane] + c0 - 1));
       }
     }
     const uint32_t slot = warp_incl_scan(span) - span;
@@ -326,14 +373,9 @@ __device__ __forceinline__ bool merge_tile(const FoldSources& src, uint64_t tota
       sh.span[lane] = span;
       sh.slot[lane] = slot;
     }
-    // Key of the element just before this tile in merged order: the largest
-    // key among the sources' last elements before their co-ranks.
-    uint32_t mx = has_prev ? prev : 0u;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    const bool any_prev = __any_sync(0xffffffffu, has_prev);
+    const uint32_t pm = __ballot_sync(0xffffffffu, lane < uint32_t(S) && c0 > 0);
     if (lane == 0) {
-      sh.prev_key = any_prev ? mx : 0xFFFFFFFFu;  // no key equals 2^32 - 1
+      sh.prev_mask = pm;
       sh.ngap = 0;
     }
   }
@@ -385,6 +427,19 @@ __device__ __forceinline__ bool merge_tile(const FoldSources& src, uint64_t tota
     return false;
   }
 
+  // The element before the tile (for thread 0): only its key (and so its
+  // bin) matters; a key variable with the largest key before the co-ranks.
+  uint32_t prev0 = 0;
+  if (tid == 0) {
+    uint32_t pm = sh.prev_mask, mx = 0;
+    while (pm) {
+      const int j = __ffs(pm) - 1;
+      pm &= pm - 1;
+      mx = max(mx, key_of(sk[sh.rstart[j] - 1]));
+    }
+    prev0 = mx << 1;
+  }
+
   // Left-deep merge order: X = run 0 + run 1, then X = X + run r for each
   // further rank; the last step keeps its E outputs per thread in registers.
   // Runs grow with their rank (the batch and level 0 are the smallest), so
@@ -420,10 +475,8 @@ __device__ __forceinline__ bool merge_tile(const FoldSources& src, uint64_t tota
   if (lane == 31) sh.last[warp] = last;
   __syncthreads();
   if (lane == 0 && warp > 0) prev_kv = sh.last[warp - 1];
-  const bool has_prev = tid > 0 || sh.prev_key != 0xFFFFFFFFu;
-  // for tid 0 the previous element is the one before the tile: only its key
-  // (and so its bin) matters; rebuild a key variable with that key
-  if (tid == 0) prev_kv = sh.prev_key << 1;
+  const bool has_prev = tid > 0 || sh.prev_mask != 0;
+  if (tid == 0) prev_kv = prev0;
 
   if (!kCleanup) {
     if (cnt == uint32_t(E) && (E % 4) == 0 &&
@@ -544,7 +597,7 @@ __global__ void __launch_bounds__(kThreads) fold_merge(FoldSources src, uint64_t
     fence_mbar_init();
   }
   __syncthreads();
-  merge_tile<8, kCleanup>(src, total, part, uint32_t(src.count), s_tile, ntiles, out_k, out_v, out_fence, fshift, status, lookback,
+  merge_tile<kFoldE, kCleanup>(src, total, part, uint32_t(src.count), s_tile, ntiles, out_k, out_v, out_fence, fshift, status, lookback,
                           out_count, sm, sh, &s_bar, 0);
 }
 
@@ -736,7 +789,7 @@ cudaError_t fold_partition_launch(const FoldArgs& a, cudaStream_t st) {
 cudaError_t fold_merge_launch(const FoldArgs& a, cudaStream_t st) {
   static bool attr_set = false;
   cudaError_t e;
-  constexpr size_t smem = TileGeom<8>::kSmem;
+  constexpr size_t smem = TileGeom<kFoldE>::kSmem;
   if (!attr_set) {
     if ((e = set_smem(fold_merge<false>, smem)) != cudaSuccess) return e;
     if ((e = set_smem(fold_merge<true>, smem)) != cudaSuccess) return e;

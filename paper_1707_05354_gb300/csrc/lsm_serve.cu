@@ -186,8 +186,8 @@ uint64_t slot_bytes(const lsm_server_config& c, uint32_t max_levels, uint32_t ma
 uint64_t dict_bytes(uint32_t b, uint32_t L) {
   const uint64_t cap = uint64_t(b) * ((1ull << L) - 1);
   const uint64_t bp = rup(b, 32) + 32;
-  return 8 * cap + 8 * cap + 8 * (cap / 2048 + 2) + (kBatchBufs + 2) * 8 * bp + cap / 2 + 16 * bp +
-         4 * (cap / 2048 + 2) * (L + 1) +
+  return 8 * cap + 8 * cap + 8 * (cap / kFoldTile + 2) + (kBatchBufs + 2) * 8 * bp + cap / 2 + 16 * bp +
+         4 * (cap / kFoldTile + 2) * (L + 1) +
          (64ull << 20);
 }
 
