@@ -124,6 +124,22 @@ __device__ __forceinline__ uint32_t find_instance(const uint64_t* prefix, uint32
   return lo;
 }
 
+// Lanes of the warp whose value equals this lane's (values below 2^kBits):
+// the intersection, over the bits, of the lanes that agree with this lane on
+// that bit -- one ballot per bit, a fixed cost however many distinct values
+// the warp holds.
+template <int kBits>
+__device__ __forceinline__ uint32_t warp_peers(uint32_t d) {
+  uint32_t peers = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < kBits; ++b) {
+    const uint32_t bit = (d >> b) & 1u;
+    const uint32_t m = __ballot_sync(0xffffffffu, bit != 0u);
+    peers &= bit ? m : ~m;
+  }
+  return peers;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T x) {
 #pragma unroll

@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kThreads, LSM_SORT_MINB) sort_pass(Loader ld, 
   for (int j = 0; j < kIPT; ++j) {
     const uint32_t p = base + j * 32 + lane;
     const uint32_t d = (p < n) ? ((kv[j] >> shift) & 255u) : kNoDigit;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t peers = warp_peers<9>(d);  // d <= kNoDigit = 256
     const uint32_t before = __popc(peers & lt);
     const uint32_t cnt = (d != kNoDigit) ? s_whist[warp][d] : 0u;
     __syncwarp();
@@ -374,7 +374,7 @@ __device__ __forceinline__ void rank_block(const uint32_t (&kv)[IPT], uint32_t m
   for (int j = 0; j < IPT; ++j) {
     const uint32_t p = base + j * 32 + lane;
     const uint32_t d = (p < m && p >= lo) ? ((kv[j] >> shift) & 255u) : kNoDigit;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t peers = warp_peers<9>(d);  // d <= kNoDigit = 256
     const uint32_t before = __popc(peers & lt);
     const uint32_t cnt = (d != kNoDigit) ? s_whist[warp][d] : 0u;
     __syncwarp();
