@@ -789,12 +789,18 @@ cudaError_t fold_partition_launch(const FoldArgs& a, cudaStream_t st) {
 cudaError_t fold_merge_launch(const FoldArgs& a, cudaStream_t st) {
   static bool attr_set = false;
   cudaError_t e;
-  constexpr size_t smem = TileGeom<kFoldE>::kSmem;
+  constexpr size_t full = TileGeom<kFoldE>::kSmem;
   if (!attr_set) {
-    if ((e = set_smem(fold_merge<false>, smem)) != cudaSuccess) return e;
-    if ((e = set_smem(fold_merge<true>, smem)) != cudaSuccess) return e;
+    if ((e = set_smem(fold_merge<false>, full)) != cudaSuccess) return e;
+    if ((e = set_smem(fold_merge<true>, full)) != cudaSuccess) return e;
     attr_set = true;
   }
+  // the slots, plus the pair buffers the left-deep chain uses (X from three
+  // sources, Y from four): more CTAs fit per SM for the small folds
+  using G = TileGeom<kFoldE>;
+  const int S = a.src.count;
+  const size_t smem = 2 * size_t(G::kSlotCap) * sizeof(uint32_t) + (S >= 3 ? G::kTile * sizeof(uint2) : 0) +
+                      (S >= 4 ? G::kTile * sizeof(uint2) : 0);
   const uint64_t ntiles = fold_tiles(a.total);
   if (a.cleanup) {
     if ((e = cudaMemsetAsync(a.out_count, 0, sizeof(uint64_t), st)) != cudaSuccess) return e;

@@ -512,8 +512,8 @@ __device__ __forceinline__ void bucket_write(const uint32_t* a, const uint32_t* 
 //   Fast path (bucket in shared memory, no sub-bin above kSubBinMax): one
 //   counting pass on the top 12 of the `rest` bits places every element in
 //   its sub-bin (about one element each for spread keys), at an arbitrary
-//   slot; each thread then insertion-sorts whole sub-bins by (key variable,
-//   index in the bucket), which is the stable order.
+//   slot; every element then goes to its sub-bin's start plus its rank in
+//   the sub-bin by (key variable, index in the bucket), the stable order.
 //   Otherwise: ceil(rest / 8) stable 8-bit passes in shared memory, or, for
 //   a bucket above kBucketCap (heavy duplicate keys), the same passes in
 //   chunks through global memory.
@@ -590,26 +590,30 @@ __device__ __forceinline__ void bucket_body(uint32_t* tmp_k, uint32_t* tmp_v, ui
         }
       }
       __syncthreads();
-      // every sub-bin sorted by (key variable, index): the stable order
-      for (uint32_t b = tid; b < kSubBins; b += kBucketThreads) {
-        const uint32_t s0 = cnt[b], s1 = b + 1 < kSubBins ? cnt[b + 1] : m;
-        for (uint32_t x = s0 + 1; x < s1; ++x) {
+      // Every element's place: its sub-bin's start plus its rank there by
+      // (key variable, index), the stable order.  Each element counts the
+      // members of its sub-bin that precede it (independent loads, about
+      // two a sub-bin for spread keys) rather than a per-sub-bin insertion
+      // sort, whose shifting chain made a warp wait for its fullest sub-bin.
+#pragma unroll 2
+      for (int j = 0; j < kBucketIPT; ++j) {
+        const uint32_t x = tid + j * kBucketThreads;
+        if (x < m) {
           const uint32_t k = bk[x], vv = bv[x];
           const uint16_t ix = bi[x];
-          uint32_t y = x;
-          while (y > s0 && (bk[y - 1] > k || (bk[y - 1] == k && bi[y - 1] > ix))) {
-            bk[y] = bk[y - 1];
-            bv[y] = bv[y - 1];
-            bi[y] = bi[y - 1];
-            --y;
+          const uint32_t b = (k >> sh) & (kSubBins - 1);
+          const uint32_t s0 = cnt[b], s1 = b + 1 < kSubBins ? cnt[b + 1] : m;
+          uint32_t r = 0;
+          for (uint32_t y = s0; y < s1; ++y) {
+            const uint32_t ky = bk[y];
+            r += (ky < k || (ky == k && bi[y] < ix)) ? 1u : 0u;
           }
-          bk[y] = k;
-          bv[y] = vv;
-          bi[y] = ix;
+          ak[s0 + r] = k;
+          av[s0 + r] = vv;
         }
       }
       __syncthreads();
-      bucket_write(bk, bv, m, out_k, out_v, start, pad, pad_kv, pad_v, fence, fshift, bin0, nbins);
+      bucket_write(ak, av, m, out_k, out_v, start, pad, pad_kv, pad_v, fence, fshift, bin0, nbins);
       return;
     }
     __syncthreads();  // skewed bucket: the pass-by-pass path below reloads it
