@@ -317,10 +317,13 @@ def run_gpu(args):
     upd_rate = world * K * n_upd / ph["update"] / 1e6
     look_rate = world * K * nq / ph["lookup"] / 1e6
 
-    # roofline of the dominant kernel group (largest device time)
+    # Roofline of the dominant kernel: fold_merge, the kernel with the largest
+    # device-time share in the launch list of this workload (the "sort" group
+    # is four kernels; its largest, bucket_sort, has about a third of the
+    # merge's share).  Every group's fraction is reported beside it.
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
-    dom = max(("sort", "merge", "lookup", "count", "emit", "cleanup"), key=lambda g: prof[g]["ms"])
+    dom = "merge"
     d = prof[dom]
     achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9 if d["ms"] > 0 else 0.0
     tr = ncu_traffic().get(dom)
@@ -335,6 +338,28 @@ def run_gpu(args):
     groups = {g: {"launches": v["launches"], "ms": round(v["ms"], 4),
                   "GB/s": (v["bytes"] / (v["ms"] / 1000) / 1e9) if v["ms"] > 0 and v["bytes"] else None}
               for g, v in prof.items()}
+    for g in groups.values():
+        g["frac"] = g["GB/s"] / hbm if g["GB/s"] else None
+
+    # Worst case of the lookups: r = 2^m - 1 (m levels full), where a miss
+    # probes every level; the timed r = 2^m state holds one level (the
+    # sorted-array layout).
+    wl = []
+    wl_found = 0.0
+    for _ in range(3):
+        G.lsm_reset(h)
+        for t in range(nb - 1):
+            G.lsm_insert_batch(h, kp + 4 * t * b, vp + 4 * t * b, b, sp)
+        G.lsm_stream_wait(h, sp)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        G.lsm_lookup(h, d_q.data_ptr(), nq, o_val.data_ptr(), o_found.data_ptr(), sp)
+        e1.record(st)
+        e1.synchronize()
+        wl.append(nq / (e0.elapsed_time(e1) / 1000.0) / 1e6)
+        wl_found = float(o_found.float().mean().item())
+    lookups_worst = {"value": world * statistics.median(wl), "unit": "M lookups/s", "r": nb - 1,
+                     "levels": bin(nb - 1).count("1"), "found_fraction": wl_found}
 
     # end to end through the public API from pinned host buffers
     e2e = None
@@ -366,7 +391,9 @@ def run_gpu(args):
                        "b": b, "batches": nb, "lookup_mode": args.lookup_mode,
                        "l2": "inputs larger than L2 (1 GiB of updates per step), no flush",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "lookups": {"value": look_rate, "unit": "M lookups/s", "found_fraction": found_frac},
+            "lookups": {"value": look_rate, "unit": "M lookups/s", "found_fraction": found_frac,
+                        "r": nb, "levels": bin(nb).count("1")},
+            "lookups_worst_case": lookups_worst,
             "phases_ms_per_step": {p: 1000.0 * ph[p] / K for p in phases},
             "rates": {"count_M_per_s": world * K * ncq / ph["count"] / 1e6,
                       "range_M_per_s": world * K * len(r1) / ph["range"] / 1e6,
