@@ -328,17 +328,23 @@ struct MergeShared {
   uint64_t prefix;
 };
 
+// From this many sources a tile stages its windows with vector loads rather
+// than bulk copies (measured at b = 2^20: 4-5 % faster folds of four or more
+// sources, the same below).
+constexpr int kVecStageSources = 4;
+
 // Merge tile `tile` of a fold whose sources are `src` (rank order), whose
 // co-ranks are part[tile * pstride + j] .. part[(tile + 1) * pstride + j],
-// into out_k/out_v.  `bar` is an initialised mbarrier; `parity` the phase this
-// tile's copies complete.  Returns false if a copy never arrived (the CTA
-// must then stop).  Called by all threads of the CTA.
+// into out_k/out_v.  `bar` is an initialised mbarrier and `phase` the number
+// of its phases completed so far (a tile staged with bulk copies completes
+// one and advances it).  Returns false if a copy never arrived (the CTA must
+// then stop).  Called by all threads of the CTA.
 template <int E, bool kCleanup>
 __device__ __forceinline__ bool merge_tile(const FoldSources& src, uint64_t total, const uint32_t* __restrict__ part,
                                            uint32_t pstride, uint32_t tile, uint32_t ntiles, uint32_t* __restrict__ out_k,
                                            uint32_t* __restrict__ out_v, uint32_t* __restrict__ out_fence,
                                            int fshift, uint32_t* status, uint64_t* lookback, uint64_t* out_count,
-                                           uint32_t* sm, MergeShared& sh, uint64_t* bar, uint32_t parity) {
+                                           uint32_t* sm, MergeShared& sh, uint64_t* bar, uint32_t& phase) {
   using G = TileGeom<E>;
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const int S = src.count;
@@ -374,57 +380,78 @@ __device__ __forceinline__ bool merge_tile(const FoldSources& src, uint64_t tota
       sh.slot[lane] = slot;
     }
     const uint32_t pm = __ballot_sync(0xffffffffu, lane < uint32_t(S) && c0 > 0);
+    // every window 16-byte aligned (so by construction: level and buffer
+    // starts are multiples of 32 elements); otherwise plain loads
+    bool al = true;
+    if (span)
+      al = ((reinterpret_cast<uintptr_t>(src.keys[lane] + a0) | reinterpret_cast<uintptr_t>(src.vals[lane] + a0)) &
+            15u) == 0;
+    const bool ok = __all_sync(0xffffffffu, al);
     if (lane == 0) {
       sh.prev_mask = pm;
       sh.ngap = 0;
+      sh.ok = ok ? 1u : 0u;
+      if (!ok) atomicOr(status, kErrAlign);
     }
   }
   __syncthreads();
 
-  // Stage the segments with the TMA engine (one thread issues and waits).
-  if (tid == 0) {
-    uint32_t bytes = 0, ok = 1;
-    for (int r = 0; r < S; ++r) {
-      if (!sh.span[r]) continue;
-      const uintptr_t gk = reinterpret_cast<uintptr_t>(src.keys[r] + sh.a0[r]);
-      const uintptr_t gv = reinterpret_cast<uintptr_t>(src.vals[r] + sh.a0[r]);
-      if ((gk | gv) & 15u) ok = 0;
-      bytes += 2u * sh.span[r] * 4u;
+  if (S >= kVecStageSources && sh.ok) {
+    // Many sources: 16-byte asynchronous copies issued by every thread (two
+    // to three per thread and array, all in flight at once) stage the
+    // windows faster than one bulk copy per source and array, which the
+    // copy engine serves one after another.
+    const uint32_t chunks = (sh.slot[S - 1] + sh.span[S - 1]) >> 2;
+    int r = 0;
+    for (uint32_t u = tid; u < chunks; u += kThreads) {
+      const uint32_t w = u * 4u;
+      while (w >= sh.slot[r] + sh.span[r]) ++r;
+      const uint32_t off = sh.a0[r] + (w - sh.slot[r]);
+      cp_async16(sk + w, src.keys[r] + off);
+      cp_async16(sv + w, src.vals[r] + off);
     }
-    sh.ok = ok;
-    if (!ok) {
-      atomicOr(status, kErrAlign);
-      bytes = 0;
-    }
-    mbar_arrive_expect_tx(bar, bytes);
-    if (ok) {
-      for (int r = 0; r < S; ++r) {
-        if (!sh.span[r]) continue;
-        bulk_g2s(sk + sh.slot[r], src.keys[r] + sh.a0[r], sh.span[r] * 4u, bar);
-        bulk_g2s(sv + sh.slot[r], src.vals[r] + sh.a0[r], sh.span[r] * 4u, bar);
-      }
-    }
-    // One thread waits for the copies (bounded); the barrier below then
-    // releases the CTA, so the other threads do not spin on the mbarrier.
-    sh.landed = mbar_wait_bounded(bar, parity, status) ? 1u : 0u;
-  }
-  __syncthreads();
-  const bool landed = sh.landed != 0;
-  // each thread acquires the completed phase itself (returns at once)
-  if (landed) mbar_try_wait(bar, parity);
-  if (!sh.ok) {  // never expected: plain loads instead of the bulk copies
-    for (int r = 0; r < S; ++r)
-      for (uint32_t i = tid; i < sh.span[r]; i += kThreads) {
-        sk[sh.slot[r] + i] = __ldg(src.keys[r] + sh.a0[r] + i);
-        sv[sh.slot[r] + i] = __ldg(src.vals[r] + sh.a0[r] + i);
-      }
+    cp_async_wait_all();
     __syncthreads();
-  }
-  if (!__syncthreads_and(landed)) {
-    // A copy never completed; give it one more bounded wait before leaving
-    // so that no transfer lands in shared memory after this CTA is gone.
-    if (tid == 0) mbar_wait_bounded(bar, parity, status);
-    return false;
+  } else {
+    // Stage the segments with the TMA engine (one thread issues and waits);
+    // this completes one phase of the CTA's mbarrier.
+    const uint32_t parity = phase & 1u;
+    ++phase;
+    if (tid == 0) {
+      uint32_t bytes = 0;
+      const bool ok = sh.ok != 0;
+      for (int r = 0; r < S; ++r) bytes += 2u * sh.span[r] * 4u;
+      if (!ok) bytes = 0;
+      mbar_arrive_expect_tx(bar, bytes);
+      if (ok) {
+        for (int r = 0; r < S; ++r) {
+          if (!sh.span[r]) continue;
+          bulk_g2s(sk + sh.slot[r], src.keys[r] + sh.a0[r], sh.span[r] * 4u, bar);
+          bulk_g2s(sv + sh.slot[r], src.vals[r] + sh.a0[r], sh.span[r] * 4u, bar);
+        }
+      }
+      // One thread waits for the copies (bounded); the barrier below then
+      // releases the CTA, so the other threads do not spin on the mbarrier.
+      sh.landed = mbar_wait_bounded(bar, parity, status) ? 1u : 0u;
+    }
+    __syncthreads();
+    const bool landed = sh.landed != 0;
+    // each thread acquires the completed phase itself (returns at once)
+    if (landed) mbar_try_wait(bar, parity);
+    if (!sh.ok) {  // never expected: plain loads instead of the bulk copies
+      for (int r = 0; r < S; ++r)
+        for (uint32_t i = tid; i < sh.span[r]; i += kThreads) {
+          sk[sh.slot[r] + i] = __ldg(src.keys[r] + sh.a0[r] + i);
+          sv[sh.slot[r] + i] = __ldg(src.vals[r] + sh.a0[r] + i);
+        }
+      __syncthreads();
+    }
+    if (!__syncthreads_and(landed)) {
+      // A copy never completed; give it one more bounded wait before leaving
+      // so that no transfer lands in shared memory after this CTA is gone.
+      if (tid == 0) mbar_wait_bounded(bar, parity, status);
+      return false;
+    }
   }
 
   // The element before the tile (for thread 0): only its key (and so its
@@ -597,8 +624,9 @@ __global__ void __launch_bounds__(kThreads) fold_merge(FoldSources src, uint64_t
     fence_mbar_init();
   }
   __syncthreads();
+  uint32_t phase = 0;
   merge_tile<kFoldE, kCleanup>(src, total, part, uint32_t(src.count), s_tile, ntiles, out_k, out_v, out_fence, fshift, status, lookback,
-                          out_count, sm, sh, &s_bar, 0);
+                          out_count, sm, sh, &s_bar, phase);
 }
 
 // Persistent merge for every (instance, tile) of a round: each CTA takes
@@ -616,7 +644,8 @@ __global__ void __launch_bounds__(kThreads) multi_merge(MultiArena ar) {
     fence_mbar_init();
   }
   const uint64_t total_items = *reinterpret_cast<volatile const uint64_t*>(ar.tile_prefix + ar.n);
-  for (uint32_t iter = 0;; ++iter) {
+  uint32_t phase = 0;  // completed phases of s_bar (the same in every thread)
+  for (;;) {
     __syncthreads();  // the previous item is finished with the shared state
     if (threadIdx.x == 0) {
       const uint64_t w = atomicAdd(ar.work_ctr, 1u);
@@ -654,9 +683,9 @@ __global__ void __launch_bounds__(kThreads) multi_merge(MultiArena ar) {
     const bool done =
         in.tile == TileGeom<4>::kTile
             ? merge_tile<4, false>(s_src, total, part, kMultiPartStride, t, ntiles, ok, ov, of, fs, ar.status,
-                                   nullptr, nullptr, sm, sh, &s_bar, iter & 1u)
+                                   nullptr, nullptr, sm, sh, &s_bar, phase)
             : merge_tile<8, false>(s_src, total, part, kMultiPartStride, t, ntiles, ok, ov, of, fs, ar.status,
-                                   nullptr, nullptr, sm, sh, &s_bar, iter & 1u);
+                                   nullptr, nullptr, sm, sh, &s_bar, phase);
     if (!done) break;
   }
 }
