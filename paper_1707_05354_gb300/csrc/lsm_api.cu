@@ -593,8 +593,11 @@ lsm_status lsm_count(lsm_t* h, const uint32_t* d_k1, const uint32_t* d_k2, uint6
   LSM_TRY(join_side(h, st));
   const LevelSet ls = full_levels(h);
   if (ls.count == 0) return cuda_status(cudaMemsetAsync(d_count, 0, sizeof(uint32_t) * nq, st));
+  // scratch: the list of wide queries (counted by a warp each)
+  LSM_TRY(ensure_q(h, (nq + 1) * 4));
+  uint32_t* wide = reinterpret_cast<uint32_t*>(h->d_q);
   ProfScope ps(h, LSM_PROF_COUNT, double(nq) * (12.0 + 64.0 * ls.count), st);
-  return cuda_status(count_launch(ls, d_k1, d_k2, nq, d_count, nullptr, st));
+  return cuda_status(count_launch(ls, d_k1, d_k2, nq, d_count, nullptr, st, nullptr, wide));
 }
 
 lsm_status lsm_range(lsm_t* h, const uint32_t* d_k1, const uint32_t* d_k2, uint64_t nq, uint64_t* d_offsets,
@@ -609,17 +612,19 @@ lsm_status lsm_range(lsm_t* h, const uint32_t* d_k1, const uint32_t* d_k2, uint6
     *total_out = 0;
     return LSM_OK;
   }
-  // scratch: counts[nq] | bounds[nq * 2 * levels] | scan look-back[tiles]
+  // scratch: counts[nq] | bounds[nq * 2 * levels] | scan look-back[tiles] |
+  // wide-query list[nq + 1]
   const uint64_t cnt_words = round_up(nq, 2);
   const uint64_t bnd_words = round_up(nq * 2 * ls.count, 2);
   const uint64_t lb_words = scan_tiles(nq);
-  LSM_TRY(ensure_q(h, (cnt_words + bnd_words) * 4 + lb_words * 8));
+  LSM_TRY(ensure_q(h, (cnt_words + bnd_words) * 4 + lb_words * 8 + (nq + 1) * 4));
   uint32_t* counts = reinterpret_cast<uint32_t*>(h->d_q);
   uint32_t* bounds = counts + cnt_words;
   uint64_t* lb = reinterpret_cast<uint64_t*>(bounds + bnd_words);
+  uint32_t* wide = reinterpret_cast<uint32_t*>(lb + lb_words);
   {
     ProfScope ps(h, LSM_PROF_COUNT, double(nq) * (12.0 + 64.0 * ls.count), st);
-    LSM_TRY(count_launch(ls, d_k1, d_k2, nq, counts, bounds, st));
+    LSM_TRY(count_launch(ls, d_k1, d_k2, nq, counts, bounds, st, nullptr, wide));
     LSM_TRY(scan_launch(counts, nq, d_offsets, lb, h->d_misc + kMiscCtrB, h->d_misc + kMiscSticky, st));
   }
   LSM_TRY(cudaMemcpyAsync(h->h_u64, d_offsets + nq, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
@@ -629,7 +634,7 @@ lsm_status lsm_range(lsm_t* h, const uint32_t* d_k1, const uint32_t* d_k2, uint6
   if (total > capacity) return LSM_ERR_CAPACITY;
   if (total && (!d_keys || !d_vals)) return LSM_ERR_ARG;
   ProfScope ps(h, LSM_PROF_EMIT, 8.0 * double(total) + 8.0 * double(nq), st);
-  return cuda_status(range_emit_launch(ls, nq, bounds, d_offsets, d_keys, d_vals, st));
+  return cuda_status(range_emit_launch(ls, nq, bounds, d_offsets, d_keys, d_vals, st, nullptr, d_k1, d_k2, wide));
 }
 
 // Rebuild of the levels from sorted sources (rank order: newest first): the

@@ -321,9 +321,12 @@ cudaError_t lookup_sorted_launch(const LevelSet& ls, const uint32_t* sq, const u
 // level, the window [lo, hi) (2 * count words per query).  With `perm`, the
 // queries come sorted by k1 (k1 = sorted lower bounds, perm = their
 // positions; k2 stays in query order) and results go to position perm[i].
+// With `wide` (nq + 1 words of scratch), queries with many elements in their
+// windows are counted by a warp each (a second kernel); the list of them is
+// left in `wide` for range_emit_launch.
 cudaError_t count_launch(const LevelSet& ls, const uint32_t* k1, const uint32_t* k2,
                          uint64_t nq, uint32_t* count, uint32_t* bounds, cudaStream_t st,
-                         const uint32_t* perm = nullptr);
+                         const uint32_t* perm = nullptr, uint32_t* wide = nullptr);
 
 // Successor (smallest live key >= q) or predecessor (largest live key <= q)
 // of every query: key, value and found flag (0 / 0 / 0 when none).
@@ -337,8 +340,11 @@ inline uint64_t scan_tiles(uint64_t n) { return (n + 2047) / 2048; }
 
 // Range output from the windows of count_launch; with `perm`, thread i
 // serves query perm[i] (neighbouring threads, neighbouring windows).
+// With `wide` (the list count_launch left), the wide queries are emitted by
+// a warp each, from their bounds k1 / k2.
 cudaError_t range_emit_launch(const LevelSet& ls, uint64_t nq, const uint32_t* bounds,
                               const uint64_t* offsets, uint32_t* keys, uint32_t* vals,
-                              cudaStream_t st, const uint32_t* perm = nullptr);
+                              cudaStream_t st, const uint32_t* perm = nullptr, const uint32_t* k1 = nullptr,
+                              const uint32_t* k2 = nullptr, const uint32_t* wide = nullptr);
 
 }  // namespace gpulsm

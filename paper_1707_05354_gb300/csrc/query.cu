@@ -170,12 +170,27 @@ __device__ __forceinline__ uint32_t merge_windows(const LevelSet& ls, const uint
 // perm their positions), thread i serves query perm[i] and stores its count
 // and windows at that position; neighbouring threads then search
 // neighbouring parts of every level.
+// Queries whose windows hold more than kWideMin elements in all are wide:
+// with a wide list, the count kernel appends them to it (their count and
+// output are then written by the warp kernels below) instead of merging
+// hundreds of elements in one thread.
+constexpr uint32_t kWideMin = 96;
+
+template <int L>
+__device__ __forceinline__ uint32_t window_total(const uint32_t (&lo)[L], const uint32_t (&hi)[L]) {
+  uint32_t t = 0;
+#pragma unroll
+  for (int l = 0; l < L; ++l) t += hi[l] - lo[l];
+  return t;
+}
+
 template <int L>
 __global__ void __launch_bounds__(kThreads) count_kernel(LevelSet ls, const uint32_t* __restrict__ k1,
                                                          const uint32_t* __restrict__ k2, uint64_t nq,
                                                          uint32_t* __restrict__ out_count,
                                                          uint32_t* __restrict__ bounds,
-                                                         const uint32_t* __restrict__ perm) {
+                                                         const uint32_t* __restrict__ perm,
+                                                         uint32_t* __restrict__ wide) {
   for (uint64_t i0 = blockIdx.x * uint64_t(kThreads) + threadIdx.x; i0 < nq;
        i0 += uint64_t(gridDim.x) * kThreads) {
     const uint64_t i = perm ? __ldg(perm + i0) : i0;
@@ -190,7 +205,11 @@ __global__ void __launch_bounds__(kThreads) count_kernel(LevelSet ls, const uint
       lo[l] = hi[l] = 0;
       if (l < ls.count && !empty) level_window(ls, l, a << 1, (z + 1u) << 1, lo[l], hi[l]);
     }
-    out_count[i] = merge_windows<false, L>(ls, lo, hi, nullptr, nullptr, 0);
+    if (wide && window_total(lo, hi) > kWideMin) {
+      wide[1 + atomicAdd(wide, 1u)] = uint32_t(i0);
+    } else {
+      out_count[i] = merge_windows<false, L>(ls, lo, hi, nullptr, nullptr, 0);
+    }
     if (bounds) {
       uint32_t* b = bounds + i * 2 * ls.count;
 #pragma unroll
@@ -209,7 +228,7 @@ __global__ void __launch_bounds__(kThreads) range_emit(LevelSet ls, uint64_t nq,
                                                        const uint64_t* __restrict__ offsets,
                                                        uint32_t* __restrict__ keys,
                                                        uint32_t* __restrict__ vals,
-                                                       const uint32_t* __restrict__ perm) {
+                                                       const uint32_t* __restrict__ perm, bool wide) {
   for (uint64_t i0 = blockIdx.x * uint64_t(kThreads) + threadIdx.x; i0 < nq;
        i0 += uint64_t(gridDim.x) * kThreads) {
     const uint64_t i = perm ? __ldg(perm + i0) : i0;
@@ -221,8 +240,75 @@ __global__ void __launch_bounds__(kThreads) range_emit(LevelSet ls, uint64_t nq,
       lo[l] = l < ls.count ? b[2 * l] : 0u;
       hi[l] = l < ls.count ? b[2 * l + 1] : 0u;
     }
+    if (wide && window_total(lo, hi) > kWideMin) continue;  // emitted by range_wide
     const uint64_t o = offsets[i];
     merge_windows<true, L>(ls, lo, hi, keys + o, vals + o, offsets[i + 1] - o);
+  }
+}
+
+// Wide queries, one warp each: the key interval [k1, k2] is cut into 32
+// equal key sub-intervals, one per lane; every lane takes its windows in
+// each level and merges them as the one-thread path does (all versions of
+// a key fall in one lane's sub-interval, so the lanes' results are
+// disjoint).  The count is the warp's sum; the range output of a lane goes
+// after the lanes before it (a warp scan of their counts).
+template <int L>
+__device__ __forceinline__ uint32_t lane_windows(const LevelSet& ls, uint32_t a, uint32_t z, uint32_t (&lo)[L],
+                                                 uint32_t (&hi)[L]) {
+  const uint64_t w = (uint64_t(z) - a + 32) / 32;  // ceil((z - a + 1) / 32)
+  const uint64_t s0 = uint64_t(a) + lane_id() * w;
+  const uint64_t s1 = s0 + w - 1 < z ? s0 + w - 1 : uint64_t(z);
+  const bool empty = s0 > z;
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    lo[l] = hi[l] = 0;
+    if (l < ls.count && !empty) level_window(ls, l, uint32_t(s0) << 1, (uint32_t(s1) + 1u) << 1, lo[l], hi[l]);
+  }
+  return empty ? 0u : merge_windows<false, L>(ls, lo, hi, nullptr, nullptr, 0);
+}
+
+template <int L>
+__global__ void __launch_bounds__(kThreads) count_wide(LevelSet ls, const uint32_t* __restrict__ k1,
+                                                       const uint32_t* __restrict__ k2, uint64_t nq,
+                                                       uint32_t* __restrict__ out_count,
+                                                       const uint32_t* __restrict__ perm,
+                                                       const uint32_t* __restrict__ wide) {
+  const uint32_t nw = *reinterpret_cast<const volatile uint32_t*>(wide);
+  const uint32_t lane = lane_id();
+  for (uint32_t w = (blockIdx.x * kThreads + threadIdx.x) >> 5; w < nw; w += (gridDim.x * kThreads) >> 5) {
+    const uint32_t i0 = wide[1 + w];
+    const uint64_t i = perm ? __ldg(perm + i0) : i0;
+    if (i >= nq) continue;  // whole warp
+    const uint32_t a = __ldg(k1 + i0);
+    uint32_t z = __ldg(k2 + i);
+    if (z > kMaxUserKey) z = kMaxUserKey;
+    uint32_t lo[L], hi[L];
+    const uint32_t c = warp_sum(lane_windows<L>(ls, a, z, lo, hi));
+    if (lane == 0) out_count[i] = c;
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(kThreads) range_wide(LevelSet ls, const uint32_t* __restrict__ k1,
+                                                       const uint32_t* __restrict__ k2, uint64_t nq,
+                                                       const uint64_t* __restrict__ offsets,
+                                                       uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                       const uint32_t* __restrict__ perm,
+                                                       const uint32_t* __restrict__ wide) {
+  const uint32_t nw = *reinterpret_cast<const volatile uint32_t*>(wide);
+  for (uint32_t w = (blockIdx.x * kThreads + threadIdx.x) >> 5; w < nw; w += (gridDim.x * kThreads) >> 5) {
+    const uint32_t i0 = wide[1 + w];
+    const uint64_t i = perm ? __ldg(perm + i0) : i0;
+    if (i >= nq) continue;  // whole warp
+    const uint32_t a = __ldg(k1 + i0);
+    uint32_t z = __ldg(k2 + i);
+    if (z > kMaxUserKey) z = kMaxUserKey;
+    uint32_t lo[L], hi[L];
+    const uint32_t c = lane_windows<L>(ls, a, z, lo, hi);
+    const uint32_t before = warp_incl_scan(c) - c;
+    const uint64_t o = offsets[i], room = offsets[i + 1] - o;
+    if (c && before < room)
+      merge_windows<true, L>(ls, lo, hi, keys + o + before, vals + o + before, room - before);
   }
 }
 
@@ -443,16 +529,30 @@ cudaError_t lookup_sorted_launch(const LevelSet& ls, const uint32_t* sq, const u
 }
 
 cudaError_t count_launch(const LevelSet& ls, const uint32_t* k1, const uint32_t* k2, uint64_t nq,
-                         uint32_t* count, uint32_t* bounds, cudaStream_t st, const uint32_t* perm) {
+                         uint32_t* count, uint32_t* bounds, cudaStream_t st, const uint32_t* perm,
+                         uint32_t* wide) {
   if (nq == 0) return cudaSuccess;
+  cudaError_t e;
+  if (wide && (e = cudaMemsetAsync(wide, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
   const unsigned grid = persistent_grid(nq, kThreads, 152 * 8);
   count_launches(1);
-  if (ls.count <= 1) count_kernel<1><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds, perm);
-  else if (ls.count <= 2) count_kernel<2><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds, perm);
-  else if (ls.count <= 4) count_kernel<4><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds, perm);
-  else if (ls.count <= 8) count_kernel<8><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds, perm);
-  else if (ls.count <= 16) count_kernel<16><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds, perm);
-  else count_kernel<kMaxLevels><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds, perm);
+  if (ls.count <= 1) count_kernel<1><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds, perm, wide);
+  else if (ls.count <= 2) count_kernel<2><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds, perm, wide);
+  else if (ls.count <= 4) count_kernel<4><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds, perm, wide);
+  else if (ls.count <= 8) count_kernel<8><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds, perm, wide);
+  else if (ls.count <= 16) count_kernel<16><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds, perm, wide);
+  else count_kernel<kMaxLevels><<<grid, kThreads, 0, st>>>(ls, k1, k2, nq, count, bounds, perm, wide);
+  if ((e = cudaGetLastError()) != cudaSuccess || !wide) return e;
+  // the wide queries, one warp each (the grid covers every query's warp when
+  // all are wide; an empty list ends at once)
+  const unsigned wgrid = persistent_grid(nq * 32, kThreads, 152 * 8);
+  count_launches(1);
+  if (ls.count <= 1) count_wide<1><<<wgrid, kThreads, 0, st>>>(ls, k1, k2, nq, count, perm, wide);
+  else if (ls.count <= 2) count_wide<2><<<wgrid, kThreads, 0, st>>>(ls, k1, k2, nq, count, perm, wide);
+  else if (ls.count <= 4) count_wide<4><<<wgrid, kThreads, 0, st>>>(ls, k1, k2, nq, count, perm, wide);
+  else if (ls.count <= 8) count_wide<8><<<wgrid, kThreads, 0, st>>>(ls, k1, k2, nq, count, perm, wide);
+  else if (ls.count <= 16) count_wide<16><<<wgrid, kThreads, 0, st>>>(ls, k1, k2, nq, count, perm, wide);
+  else count_wide<kMaxLevels><<<wgrid, kThreads, 0, st>>>(ls, k1, k2, nq, count, perm, wide);
   return cudaGetLastError();
 }
 
@@ -469,16 +569,28 @@ cudaError_t scan_launch(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t*
 }
 
 cudaError_t range_emit_launch(const LevelSet& ls, uint64_t nq, const uint32_t* bounds, const uint64_t* offsets,
-                              uint32_t* keys, uint32_t* vals, cudaStream_t st, const uint32_t* perm) {
+                              uint32_t* keys, uint32_t* vals, cudaStream_t st, const uint32_t* perm,
+                              const uint32_t* k1, const uint32_t* k2, const uint32_t* wide) {
   if (nq == 0) return cudaSuccess;
+  cudaError_t e;
+  const bool w = wide != nullptr;
   const unsigned grid = persistent_grid(nq, kThreads, 152 * 8);
   count_launches(1);
-  if (ls.count <= 1) range_emit<1><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals, perm);
-  else if (ls.count <= 2) range_emit<2><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals, perm);
-  else if (ls.count <= 4) range_emit<4><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals, perm);
-  else if (ls.count <= 8) range_emit<8><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals, perm);
-  else if (ls.count <= 16) range_emit<16><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals, perm);
-  else range_emit<kMaxLevels><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals, perm);
+  if (ls.count <= 1) range_emit<1><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals, perm, w);
+  else if (ls.count <= 2) range_emit<2><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals, perm, w);
+  else if (ls.count <= 4) range_emit<4><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals, perm, w);
+  else if (ls.count <= 8) range_emit<8><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals, perm, w);
+  else if (ls.count <= 16) range_emit<16><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals, perm, w);
+  else range_emit<kMaxLevels><<<grid, kThreads, 0, st>>>(ls, nq, bounds, offsets, keys, vals, perm, w);
+  if ((e = cudaGetLastError()) != cudaSuccess || !w) return e;
+  const unsigned wgrid = persistent_grid(nq * 32, kThreads, 152 * 8);
+  count_launches(1);
+  if (ls.count <= 1) range_wide<1><<<wgrid, kThreads, 0, st>>>(ls, k1, k2, nq, offsets, keys, vals, perm, wide);
+  else if (ls.count <= 2) range_wide<2><<<wgrid, kThreads, 0, st>>>(ls, k1, k2, nq, offsets, keys, vals, perm, wide);
+  else if (ls.count <= 4) range_wide<4><<<wgrid, kThreads, 0, st>>>(ls, k1, k2, nq, offsets, keys, vals, perm, wide);
+  else if (ls.count <= 8) range_wide<8><<<wgrid, kThreads, 0, st>>>(ls, k1, k2, nq, offsets, keys, vals, perm, wide);
+  else if (ls.count <= 16) range_wide<16><<<wgrid, kThreads, 0, st>>>(ls, k1, k2, nq, offsets, keys, vals, perm, wide);
+  else range_wide<kMaxLevels><<<wgrid, kThreads, 0, st>>>(ls, k1, k2, nq, offsets, keys, vals, perm, wide);
   return cudaGetLastError();
 }
 

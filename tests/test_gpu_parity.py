@@ -246,6 +246,33 @@ def test_deep_fold_many_sources(g):
     assert lsm.device_errors() == 0
 
 
+def test_wide_count_range_queries(g):
+    """Queries whose windows hold hundreds to thousands of elements (the
+    warp-per-query path: the interval cut into 32 key sub-intervals) mixed
+    with narrow ones in one call, over several levels with stale versions and
+    tombstones; intervals reaching past the key domain and empty ones."""
+    b = 4096
+    lsm = g.LSM(b, 64 * b)
+    o1 = oracle.MapOracle(b)
+    rng = np.random.default_rng(77)
+    for t in range(23):                     # r = 23: levels 0, 1, 2, 4
+        keys = rng.integers(0, 1 << 14, size=b).astype(np.uint32)
+        vals = rng.integers(0, 1 << 32, size=b, dtype=np.uint64).astype(np.uint32)
+        dels = (rng.random(b) < 0.2).astype(np.uint8)
+        lsm.update(keys, vals, dels)
+        o1.call("update", keys, vals, dels)
+    n = 3000
+    k1 = rng.integers(0, 1 << 14, size=n).astype(np.uint32)
+    w = np.where(rng.random(n) < 0.5, rng.integers(1, 16, size=n), rng.integers(64, 1 << 14, size=n))
+    k2 = (k1.astype(np.int64) + w).clip(0, 2**32 - 1).astype(np.uint32)
+    k1[:3] = [0, 0, 5000]
+    k2[:3] = [2**32 - 1, (1 << 31) - 1, 4000]   # whole domain, past the key domain, empty
+    assert_queries(lsm, o1, k1[:10], k1, k2)
+    np.testing.assert_array_equal(u32(lsm.count(k1, k2)), o1.count(k1, k2))
+    assert int(u32(lsm.count(k1[:1], k2[:1]))[0]) == len(o1.items()[0])
+    assert lsm.device_errors() == 0
+
+
 # ------------------------------------------------------------------- edges --
 def test_edges(g):
     b = 64
