@@ -174,7 +174,7 @@ __device__ __forceinline__ uint32_t merge_windows(const LevelSet& ls, const uint
 // with a wide list, the count kernel appends them to it (their count and
 // output are then written by the warp kernels below) instead of merging
 // hundreds of elements in one thread.
-constexpr uint32_t kWideMin = 96;
+constexpr uint32_t kWideMin = 40;
 
 template <int L>
 __device__ __forceinline__ uint32_t window_total(const uint32_t (&lo)[L], const uint32_t (&hi)[L]) {
