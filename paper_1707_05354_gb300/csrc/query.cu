@@ -56,23 +56,47 @@ __device__ __forceinline__ void level_window(const LevelSet& ls, int l, uint32_t
   else hi = lower_bound_kv(ls.keys[l], fence_at(f, fs, n, b2), fence_at(f, fs, n, b2 + 1), t2);
 }
 
-// Lookup of one key over the levels (newest first).
+// Lookup of one key over the levels (newest first).  The elements of the
+// key, if any, lie in the target's prefix-index bin [lo, hi) (both status
+// bits of a key share its bin).  A bin of up to eight elements from its
+// 16-byte aligned start is read with two 16-byte loads and searched in
+// registers, so the search and the key at the found position cost one round
+// trip instead of a chain of dependent loads; longer bins are bisected.
+// Levels are 128-byte aligned with readable slack after them.
 __device__ __forceinline__ void lookup_one(const LevelSet& ls, uint32_t key, uint32_t& val, uint8_t& found) {
   val = 0;
   found = 0;
   if (key > kMaxUserKey) return;
   const uint32_t target = key << 1;
   for (int l = 0; l < ls.count; ++l) {
-    const uint32_t pos = level_lower_bound(ls, l, target);
-    if (pos < ls.n[l]) {
-      const uint32_t kv = __ldg(ls.keys[l] + pos);
-      if (key_of(kv) == key) {
-        if (kv & 1u) {
-          found = 1;
-          val = __ldg(ls.vals[l] + pos);
-        }
-        return;
+    const uint32_t* f = ls.fence[l];
+    const int fs = ls.fshift[l];
+    const uint32_t n = ls.n[l], bin = fence_bin(target, fs);
+    const uint32_t lo = fence_at(f, fs, n, bin), hi = fence_at(f, fs, n, bin + 1);
+    const uint32_t* a = ls.keys[l];
+    const uint32_t a0 = lo & ~3u;
+    uint32_t pos, kv = 0;
+    if (hi <= a0 + 8) {
+      const uint4 x = __ldg(reinterpret_cast<const uint4*>(a + a0));
+      const uint4 y = __ldg(reinterpret_cast<const uint4*>(a + a0 + 4));
+      const uint32_t w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+      uint32_t c = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) c += (a0 + j >= lo && a0 + j < hi && w[j] < target) ? 1u : 0u;
+      pos = lo + c;
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (a0 + j == pos) kv = w[j];
+    } else {
+      pos = lower_bound_kv(a, lo, hi, target);
+      if (pos < hi) kv = __ldg(a + pos);
+    }
+    if (pos < hi && key_of(kv) == key) {
+      if (kv & 1u) {
+        found = 1;
+        val = __ldg(ls.vals[l] + pos);
       }
+      return;
     }
   }
 }
