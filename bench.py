@@ -74,6 +74,18 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def max_over_ranks(vec, device, world):
+    """Element-wise maximum of a list of floats over all ranks of the
+    process group (the timed quantities: the slowest rank defines each)."""
+    if world <= 1:
+        return list(vec)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(vec, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 def workload_arrays(args):
     from paper_1707_05354_gb300 import workload
     b = 1 << args.b_log2
@@ -305,12 +317,7 @@ def run_gpu(args):
     assert errs == 0, "device error bits %d" % errs
 
     # max over ranks of the timed quantities
-    vec = [ph[p] for p in phases] + [step_s, t_wall]
-    if world > 1:
-        import torch.distributed as dist
-        tv = torch.tensor(vec, dtype=torch.float64, device=dev)
-        dist.all_reduce(tv, op=dist.ReduceOp.MAX)
-        vec = tv.tolist()
+    vec = max_over_ranks([ph[p] for p in phases] + [step_s, t_wall], dev, world)
     ph = dict(zip(phases, vec[:5]))
     step_s, t_wall = vec[5], vec[6]
     K = args.steps
@@ -361,6 +368,28 @@ def run_gpu(args):
     lookups_worst = {"value": world * statistics.median(wl), "unit": "M lookups/s", "r": nb - 1,
                      "levels": bin(nb - 1).count("1"), "found_fraction": wl_found}
 
+    # Per-batch rates over r (each insert timed alone: the stream drained
+    # before it, its fold joined after it), as the paper tabulates min / max
+    # beside the mean; grouped by k = ffz(r), the level the batch folds into.
+    G.lsm_reset(h)
+    per_k = {}
+    for t in range(nb):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(st)
+        G.lsm_insert_batch(h, kp + 4 * t * b, vp + 4 * t * b, b, sp)
+        G.lsm_stream_wait(h, sp)
+        e1.record(st)
+        e1.synchronize()
+        k = (~t & (t + 1)).bit_length() - 1
+        per_k.setdefault(k, []).append(e0.elapsed_time(e1))
+    all_ms = [x for v in per_k.values() for x in v]
+    per_batch = {"min_M_updates_per_s": b / (max(all_ms) / 1000.0) / 1e6,
+                 "max_M_updates_per_s": b / (min(all_ms) / 1000.0) / 1e6,
+                 "mean_M_updates_per_s": nb * b / (sum(all_ms) / 1000.0) / 1e6,
+                 "ms_by_k": {str(k): round(statistics.median(v), 4) for k, v in sorted(per_k.items())},
+                 "note": "each batch alone (stream drained before, fold joined after): no sort/fold overlap"}
+
     # end to end through the public API from pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -394,6 +423,7 @@ def run_gpu(args):
             "lookups": {"value": look_rate, "unit": "M lookups/s", "found_fraction": found_frac,
                         "r": nb, "levels": bin(nb).count("1")},
             "lookups_worst_case": lookups_worst,
+            "per_batch": per_batch,
             "phases_ms_per_step": {p: 1000.0 * ph[p] / K for p in phases},
             "rates": {"count_M_per_s": world * K * ncq / ph["count"] / 1e6,
                       "range_M_per_s": world * K * len(r1) / ph["range"] / 1e6,
@@ -584,13 +614,17 @@ def run_batched(args):
     sampler.start()
     time.sleep(0.5)
     l0 = G.kernel_launches()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.synchronize(dev)
+        dist.barrier()
     secs = timed(step_multi, args.steps, 0)
     launches = G.kernel_launches() - l0
     clocks = sampler.stop()
     status, _ = m.sync()
     assert status == G.LSM_OK
     per_round_kernels = G.lsm_multi_get_option(m.h, G.LSM_MULTI_OPT_GRAPH_KERNELS)
-    mult_s = statistics.median(secs)
+    mult_s = max_over_ranks([statistics.median(secs)], dev, world)[0]
 
     # the same rounds as separate per-instance plain calls (one handle each)
     plain = None

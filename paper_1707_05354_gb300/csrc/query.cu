@@ -45,24 +45,54 @@ __device__ __forceinline__ uint32_t level_lower_bound(const LevelSet& ls, int l,
 // interval usually has both bounds in one prefix-index bin: the bin's two
 // entries are then loaded once and the second search starts at the first
 // bound.
+__device__ __forceinline__ uint32_t bin_lower_bound(const uint32_t* a, uint32_t lo, uint32_t hi, uint32_t target,
+                                                    uint32_t& kv);
+
 __device__ __forceinline__ void level_window(const LevelSet& ls, int l, uint32_t t1, uint32_t t2, uint32_t& lo,
                                              uint32_t& hi) {
   const uint32_t* f = ls.fence[l];
   const int fs = ls.fshift[l];
   const uint32_t n = ls.n[l], b1 = fence_bin(t1, fs), b2 = fence_bin(t2, fs);
-  const uint32_t e1 = fence_at(f, fs, n, b1 + 1);
-  lo = lower_bound_kv(ls.keys[l], fence_at(f, fs, n, b1), e1, t1);
-  if (b2 == b1) hi = lower_bound_kv(ls.keys[l], lo, e1, t2);
-  else hi = lower_bound_kv(ls.keys[l], fence_at(f, fs, n, b2), fence_at(f, fs, n, b2 + 1), t2);
+  const uint32_t s1 = fence_at(f, fs, n, b1), e1 = fence_at(f, fs, n, b1 + 1);
+  const uint32_t s2 = b2 == b1 ? s1 : fence_at(f, fs, n, b2), e2 = b2 == b1 ? e1 : fence_at(f, fs, n, b2 + 1);
+  uint32_t kv;
+  // the two bounds' searches are independent (each bin read in one round trip)
+  lo = bin_lower_bound(ls.keys[l], s1, e1, t1, kv);
+  hi = bin_lower_bound(ls.keys[l], s2, e2, t2, kv);
+}
+
+// lower_bound of key variable `target` inside the bin [lo, hi) of a level's
+// keys `a` (128-byte aligned, readable slack after the end), with the key
+// variable at the result in kv when it is < hi.  A bin of up to eight
+// elements from its 16-byte aligned start is read with two 16-byte loads and
+// searched in registers, so the search and the key at the found position
+// cost one round trip instead of a chain of dependent loads; longer bins are
+// bisected.
+__device__ __forceinline__ uint32_t bin_lower_bound(const uint32_t* a, uint32_t lo, uint32_t hi, uint32_t target,
+                                                    uint32_t& kv) {
+  const uint32_t a0 = lo & ~3u;
+  kv = 0;
+  if (hi <= a0 + 8) {
+    const uint4 x = __ldg(reinterpret_cast<const uint4*>(a + a0));
+    const uint4 y = __ldg(reinterpret_cast<const uint4*>(a + a0 + 4));
+    const uint32_t w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+    uint32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) c += (a0 + j >= lo && a0 + j < hi && w[j] < target) ? 1u : 0u;
+    const uint32_t pos = lo + c;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (a0 + j == pos) kv = w[j];
+    return pos;
+  }
+  const uint32_t pos = lower_bound_kv(a, lo, hi, target);
+  if (pos < hi) kv = __ldg(a + pos);
+  return pos;
 }
 
 // Lookup of one key over the levels (newest first).  The elements of the
 // key, if any, lie in the target's prefix-index bin [lo, hi) (both status
-// bits of a key share its bin).  A bin of up to eight elements from its
-// 16-byte aligned start is read with two 16-byte loads and searched in
-// registers, so the search and the key at the found position cost one round
-// trip instead of a chain of dependent loads; longer bins are bisected.
-// Levels are 128-byte aligned with readable slack after them.
+// bits of a key share its bin).
 __device__ __forceinline__ void lookup_one(const LevelSet& ls, uint32_t key, uint32_t& val, uint8_t& found) {
   val = 0;
   found = 0;
@@ -72,25 +102,9 @@ __device__ __forceinline__ void lookup_one(const LevelSet& ls, uint32_t key, uin
     const uint32_t* f = ls.fence[l];
     const int fs = ls.fshift[l];
     const uint32_t n = ls.n[l], bin = fence_bin(target, fs);
-    const uint32_t lo = fence_at(f, fs, n, bin), hi = fence_at(f, fs, n, bin + 1);
-    const uint32_t* a = ls.keys[l];
-    const uint32_t a0 = lo & ~3u;
-    uint32_t pos, kv = 0;
-    if (hi <= a0 + 8) {
-      const uint4 x = __ldg(reinterpret_cast<const uint4*>(a + a0));
-      const uint4 y = __ldg(reinterpret_cast<const uint4*>(a + a0 + 4));
-      const uint32_t w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
-      uint32_t c = 0;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) c += (a0 + j >= lo && a0 + j < hi && w[j] < target) ? 1u : 0u;
-      pos = lo + c;
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        if (a0 + j == pos) kv = w[j];
-    } else {
-      pos = lower_bound_kv(a, lo, hi, target);
-      if (pos < hi) kv = __ldg(a + pos);
-    }
+    const uint32_t hi = fence_at(f, fs, n, bin + 1);
+    uint32_t kv;
+    const uint32_t pos = bin_lower_bound(ls.keys[l], fence_at(f, fs, n, bin), hi, target, kv);
     if (pos < hi && key_of(kv) == key) {
       if (kv & 1u) {
         found = 1;
@@ -516,16 +530,15 @@ __global__ void __launch_bounds__(kThreads) multi_lookup(MultiArena ar, const ui
         const uint32_t* f = ar.fence + d.lvl_fence[l];
         const int fs = d.lvl_fshift[l];
         const uint32_t n = d.b << l, bin = fence_bin(target, fs);
-        const uint32_t pos = lower_bound_kv(keys, fence_at(f, fs, n, bin), fence_at(f, fs, n, bin + 1), target);
-        if (pos < n) {
-          const uint32_t kv = __ldg(keys + pos);
-          if (key_of(kv) == key) {
-            if (kv & 1u) {
-              found = 1;
-              val = __ldg(ar.vals + d.lvl_off[l] + pos);
-            }
-            break;
+        const uint32_t hi = fence_at(f, fs, n, bin + 1);
+        uint32_t kv;
+        const uint32_t pos = bin_lower_bound(keys, fence_at(f, fs, n, bin), hi, target, kv);
+        if (pos < hi && key_of(kv) == key) {
+          if (kv & 1u) {
+            found = 1;
+            val = __ldg(ar.vals + d.lvl_off[l] + pos);
           }
+          break;
         }
       }
     }
