@@ -328,9 +328,10 @@ struct MergeShared {
   uint64_t prefix;
 };
 
-// From this many sources a tile stages its windows with vector loads rather
-// than bulk copies (measured at b = 2^20: 4-5 % faster folds of four or more
-// sources, the same below).
+// From this many sources a tile stages its windows with 16-byte cp.async
+// copies from every thread rather than bulk copies (at b = 2^20 the k = 7
+// fold took 1.49 instead of 1.69 ms; folds of two or three sources, a few
+// bulk copies each, gained nothing).
 constexpr int kVecStageSources = 4;
 
 // Merge tile `tile` of a fold whose sources are `src` (rank order), whose
