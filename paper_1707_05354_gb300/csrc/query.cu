@@ -160,6 +160,46 @@ template <bool kEmit, int L>
 __device__ __forceinline__ uint32_t merge_windows(const LevelSet& ls, const uint32_t (&lo)[L],
                                                   const uint32_t (&hi)[L], uint32_t* out_k, uint32_t* out_v,
                                                   uint64_t room) {
+  if (L == 1 && ls.count == 1 && hi[0] - (lo[0] & ~3u) <= 16) {
+    // One level and a short window: its keys (and values) from the 16-byte
+    // aligned start in four 16-byte loads each, walked in registers; a key's
+    // first element is its newest (level order), kept when regular.
+    const uint32_t* a = ls.keys[0];
+    const uint32_t a0 = lo[0] & ~3u;
+    uint32_t w[16], v[16];
+#pragma unroll
+    for (int c4 = 0; c4 < 4; ++c4) {
+      const uint4 x = __ldg(reinterpret_cast<const uint4*>(a + a0) + c4);
+      w[4 * c4] = x.x;
+      w[4 * c4 + 1] = x.y;
+      w[4 * c4 + 2] = x.z;
+      w[4 * c4 + 3] = x.w;
+      if (kEmit) {
+        const uint4 y = __ldg(reinterpret_cast<const uint4*>(ls.vals[0] + a0) + c4);
+        v[4 * c4] = y.x;
+        v[4 * c4 + 1] = y.y;
+        v[4 * c4 + 2] = y.z;
+        v[4 * c4 + 3] = y.w;
+      }
+    }
+    uint32_t c = 0, prev = 0xFFFFFFFFu;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const uint32_t pos = a0 + j;
+      if (pos >= lo[0] && pos < hi[0]) {
+        const uint32_t k = key_of(w[j]);
+        if (k != prev && (w[j] & 1u)) {
+          if (kEmit && c < room) {
+            out_k[c] = k;
+            out_v[c] = v[j];
+          }
+          ++c;
+        }
+        prev = k;
+      }
+    }
+    return c;
+  }
   uint32_t cur[L], head[L];
 #pragma unroll
   for (int l = 0; l < L; ++l) {
