@@ -13,15 +13,18 @@
 //   partition   one warp per output tile boundary p finds the co-rank vector
 //               (how many elements of each source precede position p).  The
 //               sources' prefix indexes (fences) give the bin holding the
-//               p-th element: each round the 32 lanes probe 31 bins of the
-//               bracket at once.  A bin of at most 32 elements (the usual
+//               p-th element: the lanes, in groups of one lane per source,
+//               probe several bins of the bracket each round.  A bin of at
+//               most 32 elements (the usual
 //               case: about 8 per source) is loaded one element per lane and
 //               ranked by (key, source rank, index); a crowded bin is
 //               bisected over its key range instead, each lane keeping a
 //               bracket in its own source, and the elements of the key found
 //               are split among the sources in rank order.
-//   merge       one tile per CTA: the TMA engine copies the k + 1 source
-//               segments into shared memory (16-byte aligned supersets); a
+//   merge       one tile per CTA: the k + 1 source segments are staged in
+//               shared memory (16-byte aligned supersets starting one
+//               element early), by TMA bulk copies for up to three sources
+//               and by 16-byte cp.async copies from every thread for more; a
 //               left-deep chain of merge-path merges in shared memory (ranks
 //               0 and 1, then the result with rank 2, ...; ties to the lower
 //               rank) builds the tile as (key, value) pairs in an
