@@ -31,7 +31,10 @@
  *    (key << 1) | status, status 1 = regular element, 0 = tombstone (§IV-A).
  *  - Errors: a call that returns anything but LSM_OK has changed nothing in
  *    the dictionary (all or nothing), unless its description says otherwise.
- *  - A handle is not thread-safe; distinct handles are independent.
+ *  - A handle is not thread-safe, and its query calls share one scratch area:
+ *    calls on one handle are issued from one thread, and query calls on
+ *    different streams are ordered by the caller.  Distinct handles are
+ *    independent.
  *  - Batch semantics (§III-A): batches apply in call order; within a batch a
  *    delete of a key beats every insert of it (rule 6) and among several
  *    inserts of one key the last in input order wins (the library's reading
@@ -146,7 +149,10 @@ lsm_status lsm_lookup(lsm_t* h, const uint32_t* d_q, uint64_t nq, uint32_t* d_va
 /*
  * lsm_count - number of live keys k with k1[i] <= k <= k2[i] (§III-E, §IV-C,
  * Fig. 2(c)).  Bounds are inclusive; k1 > k2 gives 0; k2 >= 2^31 - 1 is treated
- * as 2^31 - 2.  d_count receives nq counts.  Asynchronous.
+ * as 2^31 - 2.  d_count receives nq counts.  Asynchronous.  Uses the handle's
+ * query scratch (4 (nq + 1) bytes, grown on demand; growing it synchronises
+ * the device): a query whose level windows hold many elements is counted by
+ * a warp of its own (see the note on handles above).
  */
 lsm_status lsm_count(lsm_t* h, const uint32_t* d_k1, const uint32_t* d_k2, uint64_t nq,
                      uint32_t* d_count, void* stream);
