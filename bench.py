@@ -74,6 +74,18 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def paper_config(args, world):
+    """The `config` of the paper-scale line (both arms)."""
+    b, nb = 1 << args.b_log2, args.batches
+    return {"workload": "paper-scale plain LSM: b=2^%d, %d insert batches (2^%d updates), 2^%d lookups "
+                        "(half hits), 2^%d count + 2^%d range queries (expected 8 results), cleanup"
+                        % (args.b_log2, nb, int(np.log2(nb * b)), args.lookups_log2, args.queries_log2,
+                           args.queries_log2),
+            "b": b, "batches": nb, "lookup_mode": args.lookup_mode,
+            "l2": "inputs larger than L2 (1 GiB of updates per step), no flush",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def max_over_ranks(vec, device, world):
     """Element-wise maximum of a list of floats over all ranks of the
     process group (the timed quantities: the slowest rank defines each)."""
@@ -214,8 +226,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(secs),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_UPDATE_RATE_B20,
         "dtype": "u32", "data": "synthetic (seeded uniform 31-bit keys, u32 values)",
-        "config": {"workload": "paper-scale plain LSM, b=2^%d, %d batches (bounded sample)" % (args.b_log2, args.batches),
-                   "b": b, "batches": args.batches},
+        "config": paper_config(args, 1),
         "lookups": {"value": statistics.median(lrates), "unit": "M lookups/s"},
         "cpu_baseline": {"value": value, "unit": "M updates/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "M updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -413,13 +424,7 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": 1000.0 * step_s / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": upd_rate / PAPER_UPDATE_RATE_B20, "dtype": "u32",
             "data": "synthetic (seeded uniform 31-bit keys, u32 values; PCG64)",
-            "config": {"workload": "paper-scale plain LSM: b=2^%d, %d insert batches (2^%d updates), 2^%d lookups "
-                                   "(half hits), 2^%d count + 2^%d range queries (expected 8 results), cleanup"
-                                   % (args.b_log2, nb, int(np.log2(n_upd)), args.lookups_log2,
-                                      args.queries_log2, args.queries_log2),
-                       "b": b, "batches": nb, "lookup_mode": args.lookup_mode,
-                       "l2": "inputs larger than L2 (1 GiB of updates per step), no flush",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": paper_config(args, world),
             "lookups": {"value": look_rate, "unit": "M lookups/s", "found_fraction": found_frac,
                         "r": nb, "levels": bin(nb).count("1")},
             "lookups_worst_case": lookups_worst,
