@@ -225,6 +225,42 @@ def test_offline_oracle_matches_map_oracle():
             np.testing.assert_array_equal(a, c)
 
 
+@pytest.mark.parametrize("dist,frac", [("uniform", 0.25), ("zipf", 0.5)])
+def test_oracles_agree_on_sweep_recipe(dist, frac):
+    """The config-3 recipe at a small size (mixed batches, deletes of earlier
+    inserts, Zipf-skewed keys with heavy repeats): O1, O2, S and brute force
+    give the same live set and the same query answers."""
+    from paper_1707_05354_gb300 import workload as W
+    b = 64
+    calls = W.sweep_updates(3, b, 12 * b, frac, dist)
+    o1 = oracle.MapOracle(b)
+    s = oracle.StructuralOracle(b)
+    for c in calls:
+        o1.call(*c)
+        s.call(*c)
+    o2 = oracle.OfflineOracle.from_calls(calls, b)
+    k, v = o1.items()
+    np.testing.assert_array_equal(o2.keys, k)
+    np.testing.assert_array_equal(o2.vals, v)
+    g = np.random.default_rng(1)
+    ks = np.concatenate([c[1] for c in calls])
+    q = np.concatenate([ks[g.integers(0, len(ks), size=200)], g.integers(0, 1 << 30, size=100)]).astype(np.uint32)
+    ev, ef = o1.lookup(q)
+    for a, c in zip((ev, ef), o2.lookup(q)):
+        np.testing.assert_array_equal(a, c)
+    # brute force from the raw log, and the lookup rule of §III-D on S's levels
+    log = [list(zip(c[1].tolist(), c[2].tolist(), c[3].tolist())) for c in calls]
+    levels = [s.level(i) for i in range(12)]
+    for i, qq in enumerate(q.tolist()):
+        assert brute.state_of(log, qq) == (bool(ef[i]), int(ev[i]))
+        assert levels_lookup(levels, qq) == (int(ef[i]), int(ev[i]))
+    k1 = np.sort(ks[g.integers(0, len(ks), size=100)])
+    k2 = (k1.astype(np.int64) + g.integers(0, 1 << 24, size=100)).clip(0, (1 << 31) - 2).astype(np.uint32)
+    np.testing.assert_array_equal(o1.count(k1, k2), o2.count(k1, k2))
+    for a, c in zip(o1.range(k1, k2), o2.range(k1, k2)):
+        np.testing.assert_array_equal(a, c)
+
+
 # ------------------------------------------------------------ closed forms --
 def test_closed_form_distinct_inserts():
     g = np.random.default_rng(11)
