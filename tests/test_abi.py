@@ -54,3 +54,73 @@ def test_library_resolves_its_own_symbols(lsm_lib):
     out = subprocess.run([nm, "-D", "-C", "--undefined-only", lsm_lib.LIB_PATH], capture_output=True, text=True)
     missing = [ln for ln in out.stdout.splitlines() if "gpulsm::" in ln]
     assert not missing, missing
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    """Importing the binding from a package copy without libgpulsm.so raises:
+    there is no CPU fallback to fall back on."""
+    import shutil
+    import subprocess
+    import sys
+    pkg = tmp_path / "paper_1707_05354_gb300"
+    pkg.mkdir()
+    for f in ("__init__.py", "gpulsm.py"):
+        shutil.copy2(os.path.join(ROOT, "paper_1707_05354_gb300", f), pkg / f)
+    env = dict(os.environ)
+    env.pop("PYTHONPATH", None)
+    p = subprocess.run([sys.executable, "-c", "import paper_1707_05354_gb300.gpulsm"],
+                       cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=120)
+    assert p.returncode != 0
+    assert "ImportError" in p.stderr and "libgpulsm.so is not built" in p.stderr
+
+
+def _oracle_imports(path):
+    """(line, enclosing function names, enclosing if-tests) of every import of
+    the oracle package in a Python file."""
+    import ast
+    with open(path) as f:
+        tree = ast.parse(f.read())
+    found = []
+
+    def walk(node, funcs, tests):
+        for ch in ast.iter_child_nodes(node):
+            f2, t2 = funcs, tests
+            if isinstance(ch, (ast.FunctionDef, ast.AsyncFunctionDef)):
+                f2 = funcs + [ch.name]
+            if isinstance(ch, ast.If):
+                t2 = tests + [ast.unparse(ch.test)]
+            if isinstance(ch, ast.Import):
+                mods = [a.name for a in ch.names]
+            elif isinstance(ch, ast.ImportFrom):
+                mods = [ch.module or ""]
+            else:
+                mods = []
+            if any(m.split(".")[0] == "oracle" for m in mods):
+                found.append((ch.lineno, f2, t2))
+            walk(ch, f2, t2)
+
+    walk(tree, [], [])
+    return found
+
+
+def test_product_path_never_reaches_the_oracle():
+    """The package, its CUDA sources and the header never name the oracle;
+    the benchmark imports it only in its CPU-baseline legs."""
+    pkg = os.path.join(ROOT, "paper_1707_05354_gb300")
+    for base, _, files in os.walk(pkg):
+        if "__pycache__" in base or "_build" in base:
+            continue
+        for f in files:
+            if f.endswith(".py"):
+                assert not _oracle_imports(os.path.join(base, f)), f
+            if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+                with open(os.path.join(base, f)) as fh:
+                    assert "oracle" not in fh.read().lower(), f
+    with open(os.path.join(ROOT, "include", "gpulsm.h")) as fh:
+        assert "oracle" not in fh.read().lower()
+    sites = _oracle_imports(os.path.join(ROOT, "bench.py"))
+    assert sites
+    for line, funcs, tests in sites:
+        assert funcs and funcs[0] in ("oracle_sample", "run_reference", "run_gpu", "run_batched"), line
+        if funcs[0] in ("run_gpu", "run_batched"):
+            assert any("no_cpu_baseline" in t for t in tests), line
