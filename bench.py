@@ -86,6 +86,21 @@ def paper_config(args, world):
             "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e nominal bandwidth, for context beside the measured copy peak
+
+
+def update_roofline(upd_rate_m, nb, peak_gbs):
+    """Whole insert phase against the HBM roofline: a batch folding into
+    level k = ffz(r) moves 16 * 2^k * b bytes (read the batch and levels
+    0..k-1, write level k), so nb batches from r = 0 move
+    sum_r 16 * 2^ffz(r) bytes per batch element (72 B at nb = 128)."""
+    bpu = sum(16.0 * (1 << ((~r & (r + 1)).bit_length() - 1)) for r in range(nb)) / nb
+    gbs = upd_rate_m * 1e6 * bpu / 1e9
+    return {"bytes_per_update": bpu, "achieved_GB/s": gbs, "frac": gbs / peak_gbs,
+            "frac_of_nominal": gbs / NOMINAL_HBM_GBS, "nominal_GB/s": NOMINAL_HBM_GBS,
+            "roofline_M_updates_per_s": peak_gbs * 1e9 / bpu / 1e6}
+
+
 def max_over_ranks(vec, device, world):
     """Element-wise maximum of a list of floats over all ranks of the
     process group (the timed quantities: the slowest rank defines each)."""
@@ -350,7 +365,8 @@ def run_gpu(args):
         units_per_launch = d["bytes"] / d["launches"] / tr.get("algorithmic_bytes_per_unit", 16.0)
         traffic = tr["bytes_per_unit"] * units_per_launch
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_kind,
+                "frac": achieved / hbm, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+                "traffic": traffic, "peak_source": peak_kind,
                 "launches": d["launches"], "avg_launch_ms": d["ms"] / max(1, d["launches"]),
                 "algorithmic_bytes_per_launch": d["bytes"] / max(1, d["launches"])}
     groups = {g: {"launches": v["launches"], "ms": round(v["ms"], 4),
@@ -436,6 +452,7 @@ def run_gpu(args):
                       "range_results_per_step": int(totals[-1])},
             "kernel_groups": groups,
             "roofline": roofline,
+            "update_phase_roofline": update_roofline(upd_rate / world, nb, hbm),
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches),

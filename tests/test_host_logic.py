@@ -91,3 +91,16 @@ def test_batched_byte_model():
     m = 5
     upd = sum(16.0 * (1 << ((~r & (r + 1)).bit_length() - 1)) for r in range(1 << m))
     assert upd / (1 << m) == 8 * m + 16
+
+
+def test_update_phase_roofline():
+    import bench
+    r = bench.update_roofline(1000.0, 128, 6786.9)
+    assert r["bytes_per_update"] == 72.0                      # 8m + 16 at m = 7
+    assert abs(r["achieved_GB/s"] - 72.0) < 1e-9              # 10^9 updates/s x 72 B
+    assert abs(r["frac"] - 72.0 / 6786.9) < 1e-12
+    assert abs(r["roofline_M_updates_per_s"] - 6786.9e3 / 72.0) < 1e-6
+    for m in range(0, 9):
+        assert bench.update_roofline(1.0, 1 << m, 1.0)["bytes_per_update"] == 8 * m + 16
+    # not a power of two: batches 0..2 fold into levels 0, 1, 0
+    assert bench.update_roofline(1.0, 3, 1.0)["bytes_per_update"] == (16 + 32 + 16) / 3
