@@ -124,3 +124,38 @@ def test_product_path_never_reaches_the_oracle():
         assert funcs and funcs[0] in ("oracle_sample", "run_reference", "run_gpu", "run_batched"), line
         if funcs[0] in ("run_gpu", "run_batched"):
             assert any("no_cpu_baseline" in t for t in tests), line
+
+
+def test_header_is_plain_c_and_links(lsm_lib, tmp_path):
+    """include/gpulsm.h compiles as strict C99 and C++17 (no C++ or torch types
+    in the signatures), and a C program links against libgpulsm.so and calls
+    its host-only entry points."""
+    import shutil
+    import subprocess
+    gcc, gxx = shutil.which("gcc"), shutil.which("g++")
+    if gcc is None or gxx is None:
+        pytest.skip("gcc / g++ not available")
+    src = tmp_path / "abi.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <string.h>\n#include "gpulsm.h"\n'
+        "int main(void) {\n"
+        "  lsm_t* h = NULL;\n"
+        "  uint64_t r = 0, n = 0; uint32_t b = 0;\n"
+        '  if (strcmp(lsm_status_str(LSM_OK), "LSM_OK") != 0) return 1;\n'
+        '  if (strcmp(lsm_status_str(LSM_ERR_TIMEOUT), "LSM_ERR_TIMEOUT") != 0) return 2;\n'
+        "  if (lsm_create(&h, 0, 100, 0) != LSM_ERR_ARG || h != NULL) return 3;\n"
+        "  if (lsm_stats(NULL, &r, &n, &b, NULL) != LSM_ERR_ARG) return 4;\n"
+        "  if (lsm_capacity(NULL) != 0) return 5;\n"
+        '  printf("ok\\n");\n'
+        "  return 0;\n}\n")
+    inc = os.path.join(ROOT, "include")
+    libdir = os.path.dirname(lsm_lib.LIB_PATH)
+    exe = tmp_path / "abi"
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc, str(src),
+                    "-L", libdir, "-lgpulsm", "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    cpp = tmp_path / "abi.cpp"
+    cpp.write_text('#include "gpulsm.h"\nint main() { return lsm_capacity(nullptr) == 0 ? 0 : 1; }\n')
+    subprocess.run([gxx, "-std=c++17", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-I", inc,
+                    str(cpp)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", (out.returncode, out.stdout, out.stderr)
