@@ -104,3 +104,28 @@ def test_update_phase_roofline():
         assert bench.update_roofline(1.0, 1 << m, 1.0)["bytes_per_update"] == 8 * m + 16
     # not a power of two: batches 0..2 fold into levels 0, 1, 0
     assert bench.update_roofline(1.0, 3, 1.0)["bytes_per_update"] == (16 + 32 + 16) / 3
+
+
+def test_tuning_cache_round_trip(tmp_path, monkeypatch):
+    """load_or_tune reads a cached table (keys back to ints), and on a
+    missing or corrupt cache tunes once and writes the cache it then reads."""
+    import json
+    from paper_1707_05354_gb300 import autotune
+    path = tmp_path / "multi_tuning_test.json"
+    monkeypatch.setattr(autotune, "cache_path", lambda device=0: str(path))
+    calls = []
+
+    def fake_tune(device=0, verbose=False):
+        calls.append(device)
+        return {12: {"tile": 1024, "bin_log2": 4, "ms": {}}, 16: {"tile": 2048, "bin_log2": 2, "ms": {}}}
+
+    monkeypatch.setattr(autotune, "tune", fake_tune)
+    path.write_text("{not json")
+    t1 = autotune.load_or_tune()
+    assert calls == [0] and sorted(t1) == [12, 16]
+    t2 = autotune.load_or_tune()                                  # from the cache now
+    assert calls == [0] and t2 == {12: t1[12], 16: t1[16]}
+    assert json.loads(path.read_text())["buckets"]["12"]["tile"] == 1024
+    assert autotune.tuning_for([3000, 1 << 16, 1 << 20], t2) == [(1024, 4), (2048, 2), (2048, 2)]
+    autotune.load_or_tune(retune=True)
+    assert calls == [0, 0]
