@@ -1,4 +1,4 @@
-"""The benchmark's GPU arms (paper scale, batched form), dry-run on the
+"""The benchmark's GPU arms (paper scale, batched and serving forms), dry-run on the
 CPU: the library binding and torch's CUDA calls replaced by stand-ins that
 do no work, so that the Python around the timed region (argument handling, phase timing, the
 roofline, per-batch and worst-case figures, the end-to-end leg, the oracle
@@ -11,6 +11,7 @@ import json
 import sys
 import types
 
+import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -49,7 +50,7 @@ def fake_library(real):
     ten launches, 1 ms and 1 GB for every kernel group."""
     g = types.SimpleNamespace()
     for name in dir(real):
-        if name.startswith(("LSM_", "PROF_")):
+        if name.startswith(("LSM_", "PROF_", "SERVE_", "REQ_")):
             setattr(g, name, getattr(real, name))
     state = {"launches": 0}
 
@@ -84,6 +85,32 @@ def fake_library(real):
             pass
 
     g.MultiLSM = MultiLSM
+
+    class Server:
+        def __init__(self, b, budget, **kw):
+            self.b = b
+
+        def set_pool(self, a, v, c):
+            self.pool = len(a)
+
+        def preload(self, k, v):
+            launch()
+
+        def run(self, kind, arrival, start, size, keep_results=False):
+            launch()
+            n = len(kind)
+            return {"wall_us": float(arrival[-1]) + 500.0, "done_us": arrival.astype(float) + 100.0,
+                    "status": np.zeros(n, np.int32), "update_batches": 3,
+                    "padded_ops": 0, "retrieval_groups": 5, "cleanups": 0, "refused": 0, "range_total": 7,
+                    "time_split": {"host_admission_s": 0.0}}
+
+        def stats(self):
+            return {"levels": 11, "device_bytes": 1 << 30, "resident": 1 << 20}
+
+        def close(self):
+            pass
+
+    g.Server = Server
     return g
 
 
@@ -151,3 +178,25 @@ def test_batched_arm_prints_the_contract_line(dry_gpu, monkeypatch, capsys):
     assert line["e2e"]["h2d_bytes_per_step"] == 4 * tot * 13
     assert line["roofline"]["algorithmic_bytes_per_step"] > 16 * tot
     assert line["cpu_baseline"]["kind"] == "oracle" and line["plain_calls"]["value"] > 0
+
+
+def test_serving_arm_prints_the_contract_line(dry_gpu, monkeypatch, capsys):
+    import bench
+    from paper_1707_05354_gb300 import workload
+    real_pools = workload.serving_pools
+    monkeypatch.setattr(workload, "serving_pools", lambda n=0, **k: real_pools(n=1 << 12, **k))
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "serving", "--requests", "2000", "--b-log2", "10",
+                                      "--preload-batches", "2", "--warmup", "1"])
+    assert bench.run_serving(bench.parse_args()) == 0
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "dtype", "data", "config", "latency_ms", "continuous", "fixed_batching", "vs_fixed",
+                "heavier_load", "e2e", "gpu_launches", "clocks"):
+        assert key in line, key
+    assert line["metric"] == bench.SERVING_METRIC and line["config"]["requests"] == 2000
+    assert line["latency_ms"]["p50"] == pytest.approx(0.1)                 # done = arrival + 100 us
+    assert line["e2e"]["h2d_bytes_per_step"] == 21 * 2000
+    assert line["heavier_load"]["rate_per_s"] == 6.0e5
+    assert np.isfinite(line["value"]) and line["value"] > 0
