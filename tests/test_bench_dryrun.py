@@ -1,10 +1,10 @@
-"""The benchmark's GPU arms (paper scale, batched and serving forms), dry-run on the
-CPU: the library binding and torch's CUDA calls replaced by stand-ins that
-do no work, so that the Python around the timed region (argument handling, phase timing, the
-roofline, per-batch and worst-case figures, the end-to-end leg, the oracle
-baseline and the JSON line) runs without a GPU.  The numbers it prints mean
-nothing; the test checks that the line is printed once and has the
-contract's shape."""
+"""The benchmark's GPU arms (paper scale, batched and serving forms),
+dry-run on the CPU: the library binding and torch's CUDA calls replaced by
+stand-ins that do no work, so that the Python around the timed region
+(argument handling, phase timing, the roofline, per-batch and worst-case
+figures, the end-to-end leg, the oracle baseline and the JSON line) runs
+without a GPU.  The numbers it prints mean nothing; the tests check that
+each arm prints its line once, with the contract's shape."""
 
 import contextlib
 import json
