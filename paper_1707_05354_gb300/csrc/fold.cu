@@ -27,10 +27,13 @@
 //               and by 16-byte cp.async copies from every thread for more; a
 //               left-deep chain of merge-path merges in shared memory (ranks
 //               0 and 1, then the result with rank 2, ...; ties to the lower
-//               rank) builds the tile as (key, value) pairs in an
-//               XOR-swizzled layout, the last step keeping its outputs in
-//               registers, which are written out with 16-byte stores.  The
-//               plain fold also writes the new level's prefix index.
+//               rank) builds the tile as key variables with the 16-bit
+//               index of each element's window slot (6 bytes per element
+//               instead of a key-value pair's 8, so five tiles fit per SM
+//               instead of four), the last step keeping its outputs in
+//               registers and gathering their values through the indices;
+//               they are written out with 16-byte stores.  The plain fold
+//               also writes the new level's prefix index.
 // Cleanup uses the same two kernels over all full levels; the merge then keeps
 // only the first element of every key when it is regular and compacts the
 // survivors with a decoupled look-back scan across tiles.
@@ -52,17 +55,19 @@ template <int E>
 struct TileGeom {
   static constexpr uint32_t kTile = kThreads * E;
   static constexpr uint32_t kSlotCap = (kTile + 8 * kMaxSources + 15) / 16 * 16;  // TMA slots + slack
-  static constexpr size_t kSmem = 2 * size_t(kSlotCap) * sizeof(uint32_t) + 2 * size_t(kTile) * sizeof(uint2);
+  // a chain buffer: kTile keys (u32) + kTile slot indices (u16)
+  static constexpr size_t kChainBytes = size_t(kTile) * (sizeof(uint32_t) + sizeof(uint16_t));
+  static constexpr size_t kSmem = 2 * size_t(kSlotCap) * sizeof(uint32_t) + 2 * kChainBytes;
 };
 constexpr int kFoldE = kFoldTile / kThreads;  // outputs per thread of the plain fold
 static_assert(TileGeom<kFoldE>::kTile == kFoldTile, "the plain fold's tile");
 
-// Slot of pair q of a merge step in shared memory: q with its low 4 bits
-// XORed by bits 4..7.  A thread writing 8 consecutive pairs (q = 8 t + e)
-// then hits pair slot 8 (t & 1) + (e ^ (t >> 1)) modulo 16: the 16 lanes of
-// each half-warp phase of a 64-bit access use 16 different bank pairs, and 16
-// consecutive pairs stay a permutation of one 128-byte row.
-__device__ __forceinline__ uint32_t psw(uint32_t q) { return q ^ ((q >> 4) & 15u); }
+// Slot of element q of a chain buffer (32-bit keys, 16-bit indices): q with
+// its low 3 bits XORed by bits 5..7.  A thread writing 8 consecutive elements
+// (q = 8 t + e) then hits word 8 (t & 3) + (e ^ ((t >> 2) & 7)) modulo 32 of
+// the key array, and word 4 t + ((e ^ ((t >> 2) & 7)) >> 1) of the 16-bit
+// index array: either way the 32 lanes of a warp use 32 different banks.
+__device__ __forceinline__ uint32_t ksw(uint32_t q) { return q ^ ((q >> 5) & 7u); }
 
 // This lane's co-rank at output position p < total (warp-collective; lane j
 // holds source j when act, the active lanes being 0 .. S-1).
@@ -255,12 +260,14 @@ __global__ void __launch_bounds__(256) multi_partition(MultiArena ar) {
 
 // One merge step of the tile: output[0, nA + nB) = merge of run A (the
 // newer ranks) and run B (the next rank), ties to A.  B always sits in the
-// TMA slot area (separate key and value arrays); A is either there too (the
-// first step) or the (key, value) pair buffer X written by the step before.
+// staged windows (separate key and value arrays, the slots); A is either
+// there too (the first step) or the chain buffer X written by the step
+// before: key variables Xk and the 16-bit slot index Xi of each element.
 // Thread t produces `per` consecutive outputs from per * t after a
 // merge-path search for its first one (threads past the end idle); the
-// outputs go to the swizzled pair buffer Y, or stay in registers (kToRegs,
-// per = E) when this is the last step.  An intermediate step spreads its
+// outputs go to the swizzled chain buffer Y (key and slot index), or stay in
+// registers (kToRegs, per = E) when this is the last step, which then reads
+// each output's value from its slot.  An intermediate step spreads its
 // m outputs over all threads (per = ceil(m / threads)), so the short early
 // steps of the chain cost one or two outputs per thread instead of E.
 // An exhausted run's head key becomes kSentinel, above every key, so the
@@ -269,15 +276,15 @@ constexpr uint32_t kSentinel = 0x80000000u;
 
 template <int E, bool kAFromSlot, bool kToRegs>
 __device__ __forceinline__ void merge_step(const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv,
-                                           const uint2* __restrict__ X, uint2* __restrict__ Y, uint32_t aS,
+                                           const uint32_t* __restrict__ Xk, const uint16_t* __restrict__ Xi,
+                                           uint32_t* __restrict__ Yk, uint16_t* __restrict__ Yi, uint32_t aS,
                                            uint32_t nA, uint32_t bS, uint32_t nB, uint2 (&out)[E]) {
   const uint32_t m = nA + nB;
   const uint32_t per = kToRegs ? uint32_t(E) : (m + kThreads - 1) / kThreads;
   const uint32_t q0 = threadIdx.x * per;
   if (q0 >= m) return;
-  const uint32_t* xk = reinterpret_cast<const uint32_t*>(X);
-  auto keyA = [&](uint32_t i) { return kAFromSlot ? sk[aS + i] : xk[2 * psw(i)]; };
-  auto pairA = [&](uint32_t i) { return kAFromSlot ? make_uint2(sk[aS + i], sv[aS + i]) : X[psw(i)]; };
+  auto keyA = [&](uint32_t i) { return kAFromSlot ? sk[aS + i] : Xk[ksw(i)]; };
+  auto idxA = [&](uint32_t i) { return kAFromSlot ? aS + i : uint32_t(Xi[ksw(i)]); };
   // merge path: how many of the first q0 outputs come from A
   uint32_t lo = q0 > nB ? q0 - nB : 0u, hi = q0 < nA ? q0 : nA;
   while (lo < hi) {
@@ -285,39 +292,52 @@ __device__ __forceinline__ void merge_step(const uint32_t* __restrict__ sk, cons
     if (key_of(keyA(mid)) <= key_of(sk[bS + q0 - 1 - mid])) lo = mid + 1; else hi = mid;
   }
   uint32_t ia = lo, ib = q0 - lo;
-  uint2 a = make_uint2(0u, 0u), b = make_uint2(0u, 0u);
+  uint32_t va = 0, xa = 0, vb = 0, xb = 0;   // key variable and slot index of each head
   uint32_t ka = kSentinel, kb = kSentinel;
   if (ia < nA) {
-    a = pairA(ia);
-    ka = key_of(a.x);
+    va = keyA(ia);
+    xa = idxA(ia);
+    ka = key_of(va);
   }
   if (ib < nB) {
-    b = make_uint2(sk[bS + ib], sv[bS + ib]);
-    kb = key_of(b.x);
+    vb = sk[bS + ib];
+    xb = bS + ib;
+    kb = key_of(vb);
   }
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     if ((kToRegs || uint32_t(e) < per) && q0 + e < m) {
       const bool take_a = ka <= kb;
-      const uint2 o = take_a ? a : b;
-      if (kToRegs) out[e] = o;
-      else Y[psw(q0 + e)] = o;
+      const uint32_t v = take_a ? va : vb, x = take_a ? xa : xb;
+      if (kToRegs) {
+        out[e] = make_uint2(v, x);   // the value is gathered by slot index after the step
+      } else {
+        Yk[ksw(q0 + e)] = v;
+        Yi[ksw(q0 + e)] = uint16_t(x);
+      }
       if (take_a) {
         if (++ia < nA) {
-          a = pairA(ia);
-          ka = key_of(a.x);
+          va = keyA(ia);
+          xa = idxA(ia);
+          ka = key_of(va);
         } else {
           ka = kSentinel;
         }
       } else {
         if (++ib < nB) {
-          b = make_uint2(sk[bS + ib], sv[bS + ib]);
-          kb = key_of(b.x);
+          vb = sk[bS + ib];
+          xb = bS + ib;
+          kb = key_of(vb);
         } else {
           kb = kSentinel;
         }
       }
     }
+  }
+  if (kToRegs) {
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (q0 + e < m) out[e].y = sv[out[e].y];
   }
 }
 
@@ -356,8 +376,11 @@ __device__ __forceinline__ bool merge_tile(const FoldSources& src, uint64_t tota
   const uint32_t tile_n = uint32_t((total - obase) < G::kTile ? (total - obase) : G::kTile);
   uint32_t* sk = sm;                                           // slot keys
   uint32_t* sv = sm + G::kSlotCap;                             // slot values
-  uint2* X = reinterpret_cast<uint2*>(sm + 2 * G::kSlotCap);   // pair buffers
-  uint2* Y = X + G::kTile;
+  // chain buffers X and Y: kTile keys, then kTile 16-bit slot indices each
+  uint32_t* Xk = sm + 2 * G::kSlotCap;
+  uint16_t* Xi = reinterpret_cast<uint16_t*>(Xk + G::kTile);
+  uint32_t* Yk = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(Xk) + G::kChainBytes);
+  uint16_t* Yi = reinterpret_cast<uint16_t*>(Yk + G::kTile);
 
   // Segment of each source in this tile, and its 16-byte aligned superset.
   // The copy window starts one element early when there is one: the key
@@ -477,21 +500,25 @@ __device__ __forceinline__ bool merge_tile(const FoldSources& src, uint64_t tota
   // every element moves about twice in all.
   uint2 out[E];
   if (S <= 2) {
-    merge_step<E, true, true>(sk, sv, nullptr, nullptr, sh.rstart[0], sh.rlen[0], S == 2 ? sh.rstart[1] : 0u,
-                              S == 2 ? sh.rlen[1] : 0u, out);
+    merge_step<E, true, true>(sk, sv, nullptr, nullptr, nullptr, nullptr, sh.rstart[0], sh.rlen[0],
+                              S == 2 ? sh.rstart[1] : 0u, S == 2 ? sh.rlen[1] : 0u, out);
   } else {
-    merge_step<E, true, false>(sk, sv, nullptr, X, sh.rstart[0], sh.rlen[0], sh.rstart[1], sh.rlen[1], out);
+    merge_step<E, true, false>(sk, sv, nullptr, nullptr, Xk, Xi, sh.rstart[0], sh.rlen[0], sh.rstart[1],
+                               sh.rlen[1], out);
     uint32_t m = sh.rlen[0] + sh.rlen[1];
     for (int r = 2; r < S - 1; ++r) {
       __syncthreads();
-      merge_step<E, false, false>(sk, sv, X, Y, 0u, m, sh.rstart[r], sh.rlen[r], out);
+      merge_step<E, false, false>(sk, sv, Xk, Xi, Yk, Yi, 0u, m, sh.rstart[r], sh.rlen[r], out);
       m += sh.rlen[r];
-      uint2* t = X;
-      X = Y;
-      Y = t;
+      uint32_t* tk = Xk;
+      Xk = Yk;
+      Yk = tk;
+      uint16_t* ti = Xi;
+      Xi = Yi;
+      Yi = ti;
     }
     __syncthreads();
-    merge_step<E, false, true>(sk, sv, X, nullptr, 0u, m, sh.rstart[S - 1], sh.rlen[S - 1], out);
+    merge_step<E, false, true>(sk, sv, Xk, Xi, nullptr, nullptr, 0u, m, sh.rstart[S - 1], sh.rlen[S - 1], out);
   }
   // Outputs q0 .. q0 + cnt - 1 are in out[]; the key before q0 in merged
   // order comes from the thread before (a shuffle, or across warps through
@@ -828,12 +855,12 @@ cudaError_t fold_merge_launch(const FoldArgs& a, cudaStream_t st) {
     if ((e = set_smem(fold_merge<true>, full)) != cudaSuccess) return e;
     attr_set = true;
   }
-  // the slots, plus the pair buffers the left-deep chain uses (X from three
+  // the slots, plus the chain buffers the left-deep chain uses (X from three
   // sources, Y from four): more CTAs fit per SM for the small folds
   using G = TileGeom<kFoldE>;
   const int S = a.src.count;
-  const size_t smem = 2 * size_t(G::kSlotCap) * sizeof(uint32_t) + (S >= 3 ? G::kTile * sizeof(uint2) : 0) +
-                      (S >= 4 ? G::kTile * sizeof(uint2) : 0);
+  const size_t smem = 2 * size_t(G::kSlotCap) * sizeof(uint32_t) + (S >= 3 ? G::kChainBytes : 0) +
+                      (S >= 4 ? G::kChainBytes : 0);
   const uint64_t ntiles = fold_tiles(a.total);
   if (a.cleanup) {
     if ((e = cudaMemsetAsync(a.out_count, 0, sizeof(uint64_t), st)) != cudaSuccess) return e;
