@@ -250,9 +250,11 @@ lsm_status lsm_stream_wait(lsm_t* h, void* stream);
 uint64_t lsm_capacity(const lsm_t* h);
 
 /*
- * lsm_sort_pairs - the library's batch sort as a stand-alone call: stable LSD
- * radix sort of n (key, value) pairs on the full 32-bit key, 8 bits per pass
- * (§IV-A sorts each batch with a radix sort over the whole key variable).
+ * lsm_sort_pairs - the library's batch sort as a stand-alone call: stable
+ * radix sort of n (key, value) pairs on the full 32-bit key (§IV-A sorts each
+ * batch with a radix sort over the whole key variable): for n <= 2^20 a
+ * bucket sort on the top byte followed by a sort of each bucket on the low
+ * 24 bits, above that four 8-bit least-significant-digit passes.
  * d_keys_in/d_vals_in are read, d_keys_out/d_vals_out receive the sorted
  * pairs (they must not overlap the inputs).  Uses the handle's scratch, so
  * n <= b.  Asynchronous.  Used by tests of the sort in isolation.
@@ -268,7 +270,7 @@ lsm_status lsm_sort_pairs(lsm_t* h, const uint32_t* d_keys_in, const uint32_t* d
  * raw cudaMalloc, or a latency-bound loop that cannot take the device-wide
  * synchronisation and unbounded time of a cudaMalloc/cudaFree).  No handle
  * is needed and nothing is allocated: every byte of scratch comes from one
- * fixed array with static storage inside the library (about 11 MB), which
+ * fixed array with static storage inside the library (about 17 MB), which
  * each GPU that loads the library keeps until the process exits.
  *   n        at most LSM_SORT_NOALLOC_MAX_PAIRS; larger n is refused with
  *            LSM_ERR_CAPACITY before any work is queued.  n = 0 is a no-op.
@@ -296,11 +298,25 @@ lsm_status lsm_sort_pairs_noalloc(const uint32_t* d_keys_in, const uint32_t* d_v
  *                        copy avoided); synchronises; reading clears them.
  *   LSM_OPT_KERNEL_LAUNCHES read-only: CUDA kernels launched by the library
  *                        in this process so far (all handles); h may be NULL.
+ *   LSM_OPT_KEY_CHECK    0 (default) = an update call waits for the device
+ *                        check of its keys and returns LSM_ERR_KEY_RANGE,
+ *                        having changed nothing, if one is >= 2^31 - 1.
+ *                        1 = deferred, for callers that validate keys
+ *                        upstream and want update calls that never wait:
+ *                        a batch holding a bad key is applied as b placebo
+ *                        tombstones (the reserved key 2^31 - 1, which no
+ *                        query sees and cleanup drops), so it changes no
+ *                        query result; r still advances, the call returns
+ *                        LSM_OK, and bit 1 of LSM_OPT_DEVICE_ERROR records
+ *                        it.  A call of n > b ops is then all or nothing
+ *                        per batch.  Handles with b > 2^20 keep the
+ *                        synchronous check.  Not in the paper.
  */
 typedef enum {
   LSM_OPT_LOOKUP_MODE = 1,
   LSM_OPT_DEVICE_ERROR = 2,
-  LSM_OPT_KERNEL_LAUNCHES = 3
+  LSM_OPT_KERNEL_LAUNCHES = 3,
+  LSM_OPT_KEY_CHECK = 4
 } lsm_option;
 
 lsm_status lsm_set_option(lsm_t* h, lsm_option opt, int64_t value);
@@ -569,6 +585,32 @@ lsm_status lsm_server_stats(const lsm_server_t* s, uint64_t* r, uint64_t* reside
 
 /* The server's dictionary (owned by the server), for queries between runs. */
 lsm_t* lsm_server_dict(lsm_server_t* s);
+
+/*
+ * Fault injection for tests (the paper has no counterpart).  Both calls exist
+ * so that the error paths of the failure design can be exercised without a
+ * real out-of-memory condition and without faulting or hanging a GPU.
+ *
+ * lsm_debug_fail_allocs - from now on, let `skip` device or pinned-host
+ * allocations of the library succeed, then make the next `count` fail as if
+ * the memory were exhausted (the call that needed them returns LSM_ERR_OOM
+ * and, being all or nothing, leaves its handle as it was).  Nothing is
+ * allocated for a failed request.  Process-wide, all devices; (0, 0) disarms.
+ * Host-only: needs no device.
+ */
+lsm_status lsm_debug_fail_allocs(uint64_t skip, uint64_t count);
+
+/*
+ * lsm_debug_wait_flag - one device thread waits, with the same bounded spin
+ * as every wait inside the library (look-back scans, bulk-copy barriers),
+ * until the device word *d_flag is non-zero, giving up after limit_ns
+ * nanoseconds of the GPU's global timer.  d_status is a device word the call
+ * zeroes first; a wait that gives up sets bit 2 there (the library's timeout
+ * bit).  Synchronises with `stream`.  Returns LSM_OK when the flag was seen,
+ * LSM_ERR_TIMEOUT when the wait gave up (the context stays usable),
+ * LSM_ERR_ARG for null pointers or limit_ns = 0 or above 10 s.
+ */
+lsm_status lsm_debug_wait_flag(const uint32_t* d_flag, uint32_t* d_status, uint64_t limit_ns, void* stream);
 
 #ifdef __cplusplus
 }

@@ -69,42 +69,29 @@ static_assert(TileGeom<kFoldE>::kTile == kFoldTile, "the plain fold's tile");
 // index array: either way the 32 lanes of a warp use 32 different banks.
 __device__ __forceinline__ uint32_t ksw(uint32_t q) { return q ^ ((q >> 5) & 7u); }
 
-// This lane's co-rank at output position p < total (warp-collective; lane j
-// holds source j when act, the active lanes being 0 .. S-1).
-__device__ __forceinline__ uint32_t corank_lane(bool act, const uint32_t* a, const uint32_t* f, int fs,
-                                                uint32_t n, uint64_t p, uint64_t total) {
+// Number of elements of the sorted run a[0, n) whose key variable is below
+// x, from its prefix index f at shift fs: one table entry when x starts one
+// of its bins, else that bin's start plus a lower bound inside the bin
+// (about 2^3 elements).
+__device__ __forceinline__ uint32_t count_below(const uint32_t* a, const uint32_t* f, int fs, uint32_t n,
+                                                uint32_t x) {
+  const uint32_t P = x >> fs;
+  const uint32_t lo = fence_at(f, fs, n, P);
+  if ((x & ((1u << fs) - 1u)) == 0u) return lo;
+  return lower_bound_kv(a, lo, fence_at(f, fs, n, P + 1), x);
+}
+
+// Largest bin P in [lo, hi) (at shift `shift`) with C(P) <= p, where C(P) =
+// sum over the sources of count(P): the warp splits into G = 32 / S' groups
+// of S' >= S lanes (lane j of a group reads source j, count(j, P) its count);
+// each round the groups evaluate C at the points that split the bracket
+// into G parts (2 for a single group) and the bracket shrinks to the part
+// where C crosses p.  Requires C(lo) <= p < C(hi).
+template <class Count>
+__device__ __forceinline__ uint32_t group_search(uint32_t lo, uint32_t hi, uint64_t p, int lg, const Count& count) {
   const uint32_t lane = lane_id();
-  const int S = __popc(__ballot_sync(0xffffffffu, act));
-  // The search runs at the coarsest of the sources' prefix-index resolutions
-  // (shift fc), which every source's table can answer.
-  int fc = act ? fs : 0;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) fc = max(fc, __shfl_xor_sync(0xffffffffu, fc, o));
-  const int cs = act ? fc - fs : 0;
-  const uint32_t nbins = 1u << (32 - fc);
-  uint32_t bmin = 0, bmax = 0;
-  if (act) {
-    bmin = __ldg(f + fence_bins(fs) + 2);
-    bmax = __ldg(f + fence_bins(fs) + 3);
-  }
-  // 1. The bin: largest P with C(P) <= p, C(P) = sum over the sources of
-  //    their counts below bin P (C(0) = 0 <= p < C(nbins) = total).  The
-  //    warp splits into G = 32 / S' groups of S' >= S lanes (lane j of a
-  //    group reads source j); each round the groups evaluate C at the
-  //    points that split the bracket into G parts (2 for a single group),
-  //    one table load per lane, and the bracket shrinks to the part where
-  //    C crosses p.
-  int lg = 0;
-  while ((1 << lg) < S) ++lg;
-  const uint32_t G = 32u >> lg, q = lane >> lg, j = lane & ((1u << lg) - 1u);
-  const bool jact = j < uint32_t(S);
-  const uint32_t* fj = reinterpret_cast<const uint32_t*>(
-      __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(f), int(j)));
-  const int csj = __shfl_sync(0xffffffffu, cs, int(j));
-  const uint32_t bminj = __shfl_sync(0xffffffffu, bmin, int(j)), bmaxj = __shfl_sync(0xffffffffu, bmax, int(j));
-  const uint32_t nj = __shfl_sync(0xffffffffu, n, int(j));
-  uint32_t lo = 0, hi = nbins;
-  // at most log2(nbins) <= 32 rounds; the bound only guards the loop
+  const uint32_t G = 32u >> lg, q = lane >> lg;
+  // at most log2(2^32) rounds; the bound only guards the loop
   for (int round = 0; hi - lo > 1 && round < 64; ++round) {
     const uint32_t span = hi - lo;
     uint32_t P;
@@ -117,15 +104,10 @@ __device__ __forceinline__ uint32_t corank_lane(bool act, const uint32_t* a, con
       P = lo + uint32_t((uint64_t(q + 1) * span) >> parts);
       valid = q + 1 < (1u << parts);
     }
-    uint32_t c = 0;  // C(P) <= total < 2^32
-    if (jact && valid) {
-      const uint32_t Pj = P << csj;
-      // an entry inside the populated range is always loaded, then selected
-      const uint32_t v = __ldg(fj + (Pj <= bminj ? bminj : (Pj > bmaxj ? bmaxj : Pj)));
-      c = Pj <= bminj ? 0u : (Pj > bmaxj ? nj : v);
-    }
+    uint32_t c = valid ? count(P) : 0u;  // C(P) <= total < 2^32
     for (uint32_t o = (1u << lg) >> 1; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, int(o));
     // C is non-decreasing and the probes ascend with the group: a prefix
+    const uint32_t j = lane & ((1u << lg) - 1u);
     const int cnt = __popc(__ballot_sync(0xffffffffu, j == 0 && valid && c <= p));
     const uint32_t p_lo = __shfl_sync(0xffffffffu, P, ((cnt + 31) & 31) << lg & 31);
     const uint32_t p_hi = __shfl_sync(0xffffffffu, P, (cnt << lg) & 31);
@@ -133,9 +115,68 @@ __device__ __forceinline__ uint32_t corank_lane(bool act, const uint32_t* a, con
     if (cnt > 0) lo = p_lo;
     if (uint32_t(cnt) < G && v_hi) hi = p_hi;
   }
-  // 2. The bin's elements: [blo, bhi) of each source, need = p - C(lo) of
+  return lo;
+}
+
+// This lane's co-rank at output position p < total (warp-collective; lane j
+// holds source j when act, the active lanes being 0 .. S-1).
+__device__ __forceinline__ uint32_t corank_lane(bool act, const uint32_t* a, const uint32_t* f, int fs,
+                                                uint32_t n, uint64_t p, uint64_t total) {
+  const uint32_t lane = lane_id();
+  const int S = __popc(__ballot_sync(0xffffffffu, act));
+  // The first search runs at the coarsest of the sources' prefix-index
+  // resolutions (shift fc), which every source's table answers with one
+  // load; a crowded bin there is searched again at the finest (fm).
+  int fc = act ? fs : 0, fm = act ? fs : 32;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    fc = max(fc, __shfl_xor_sync(0xffffffffu, fc, o));
+    fm = min(fm, __shfl_xor_sync(0xffffffffu, fm, o));
+  }
+  const int cs = act ? fc - fs : 0;
+  uint32_t bmin = 0, bmax = 0;
+  if (act) {
+    bmin = __ldg(f + fence_bins(fs) + 2);
+    bmax = __ldg(f + fence_bins(fs) + 3);
+  }
+  int lg = 0;
+  while ((1 << lg) < S) ++lg;
+  const uint32_t j = lane & ((1u << lg) - 1u);
+  const bool jact = j < uint32_t(S);
+  const uint32_t* fj = reinterpret_cast<const uint32_t*>(
+      __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(f), int(j)));
+  const uint32_t* aj = reinterpret_cast<const uint32_t*>(
+      __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(a), int(j)));
+  const int csj = __shfl_sync(0xffffffffu, cs, int(j));
+  const uint32_t bminj = __shfl_sync(0xffffffffu, bmin, int(j)), bmaxj = __shfl_sync(0xffffffffu, bmax, int(j));
+  const uint32_t nj = __shfl_sync(0xffffffffu, n, int(j));
+  // 1. The bin at shift fc: largest P with C(P) <= p (C(0) = 0 <= p <
+  //    C(nbins) = total).
+  uint32_t bin = group_search(0u, 1u << (32 - fc), p, lg, [&](uint32_t P) -> uint32_t {
+    if (!jact) return 0u;
+    const uint32_t Pj = P << csj;
+    // an entry inside the populated range is always loaded, then selected
+    const uint32_t v = __ldg(fj + (Pj <= bminj ? bminj : (Pj > bmaxj ? bmaxj : Pj)));
+    return Pj <= bminj ? 0u : (Pj > bmaxj ? nj : v);
+  });
+  int bs = fc;  // shift of the bin found
+  // 2. The bin's elements: [blo, bhi) of each source, need = p - C(bin) of
   //    them precede p.
-  uint32_t blo = act ? fence_at(f, fs, n, lo << cs) : 0u, bhi = act ? fence_at(f, fs, n, (lo + 1) << cs) : 0u;
+  uint32_t blo = act ? fence_at(f, fs, n, bin << cs) : 0u, bhi = act ? fence_at(f, fs, n, (bin + 1) << cs) : 0u;
+  if (warp_sum(bhi - blo) > 32u && fm < fc) {
+    // A crowded bin at fc: its 2^(fc - fm) bins at the finest shift fm,
+    // counted with count_below (a table entry, or a short search inside a
+    // coarser source's bin).
+    const int d = fc - fm;
+    const int fsj = fc - csj;
+    bin = group_search(bin << d, (bin + 1) << d, p, lg, [&](uint32_t P) -> uint32_t {
+      return jact ? count_below(aj, fj, fsj, nj, P << fm) : 0u;
+    });
+    bs = fm;
+    blo = act ? count_below(a, f, fs, n, bin << fm) : 0u;
+    const uint32_t nb_fm = 1u << (32 - fm);
+    bhi = act ? (bin + 1 < nb_fm ? count_below(a, f, fs, n, (bin + 1) << fm) : n) : 0u;
+  }
   const uint32_t cnt = bhi - blo;
   const uint32_t tot = warp_sum(cnt);
   const uint64_t need = p - warp_sum<uint64_t>(blo);
@@ -143,14 +184,14 @@ __device__ __forceinline__ uint32_t corank_lane(bool act, const uint32_t* a, con
     // One element per lane in source order (which is the tie order); its
     // rank in the bin by (key, lane) says whether it precedes p.
     const uint32_t off = warp_incl_scan(cnt) - cnt;
-    int j = 0;
+    int jj = 0;
     for (int q = 0; q < S; ++q)
-      if (lane >= __shfl_sync(0xffffffffu, off + cnt, q)) j = q + 1;
+      if (lane >= __shfl_sync(0xffffffffu, off + cnt, q)) jj = q + 1;
     const bool has = lane < tot;
-    const uint32_t* aj =
-        reinterpret_cast<const uint32_t*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(a), j & 31));
-    const uint32_t offj = __shfl_sync(0xffffffffu, off, j & 31), bloj = __shfl_sync(0xffffffffu, blo, j & 31);
-    const uint32_t key = has ? key_of(__ldg(aj + bloj + (lane - offj))) : 0xFFFFFFFFu;
+    const uint32_t* ajj = reinterpret_cast<const uint32_t*>(
+        __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(a), jj & 31));
+    const uint32_t offj = __shfl_sync(0xffffffffu, off, jj & 31), bloj = __shfl_sync(0xffffffffu, blo, jj & 31);
+    const uint32_t key = has ? key_of(__ldg(ajj + bloj + (lane - offj))) : 0xFFFFFFFFu;
     uint32_t rank = 0;
     for (uint32_t q = 0; q < tot; ++q) {
       const uint32_t kq = __shfl_sync(0xffffffffu, key, q);
@@ -163,9 +204,9 @@ __device__ __forceinline__ uint32_t corank_lane(bool act, const uint32_t* a, con
   // A crowded bin (many equal or close keys): smallest key x in the bin
   // with #{key <= x} > p by bisection over the bin's key range.
   // Invariant per lane: blo = #{key <= xlo - 1}, bhi = #{key <= xhi} in
-  // this lane's source.  A bin at shift fc holds the keys
-  // [P << (fc - 1), (P + 1) << (fc - 1)).
-  uint32_t xlo = lo << (fc - 1), xhi = ((lo + 1) << (fc - 1)) - 1;
+  // this lane's source.  A bin at shift bs holds the keys
+  // [P << (bs - 1), (P + 1) << (bs - 1)).
+  uint32_t xlo = bin << (bs - 1), xhi = ((bin + 1) << (bs - 1)) - 1;
   while (xlo < xhi) {
     const uint32_t mid = xlo + ((xhi - xlo) >> 1);
     const uint32_t u = act ? upper_bound_key(a, blo, bhi, mid) : 0u;
@@ -606,11 +647,7 @@ __device__ __forceinline__ bool merge_tile(const FoldSources& src, uint64_t tota
       while (t >= 0) {
         const uint64_t w = ld_relaxed_u64(lookback + t);
         if (!(w & (kLbAgg | kLbIncl))) {
-          if (t0 == 0) t0 = globaltimer_ns();
-          else if (globaltimer_ns() - t0 > kWaitLimitNs) {
-            atomicOr(status, kErrTimeout);
-            break;
-          }
+          if (!spin_continue(t0, kWaitLimitNs, status)) break;
           continue;
         }
         prefix += w & kLbMask;
@@ -846,15 +883,15 @@ cudaError_t fold_partition_launch(const FoldArgs& a, cudaStream_t st) {
                     uint32_t(kFoldTile), a.part);
 }
 
+PerDeviceFlags g_merge_attr[2];
+
 cudaError_t fold_merge_launch(const FoldArgs& a, cudaStream_t st) {
-  static bool attr_set = false;
   cudaError_t e;
   constexpr size_t full = TileGeom<kFoldE>::kSmem;
-  if (!attr_set) {
-    if ((e = set_smem(fold_merge<false>, full)) != cudaSuccess) return e;
-    if ((e = set_smem(fold_merge<true>, full)) != cudaSuccess) return e;
-    attr_set = true;
-  }
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = set_smem_attr_once(fold_merge<false>, full, dev, g_merge_attr[0])) != cudaSuccess) return e;
+  if ((e = set_smem_attr_once(fold_merge<true>, full, dev, g_merge_attr[1])) != cudaSuccess) return e;
   // the slots, plus the chain buffers the left-deep chain uses (X from three
   // sources, Y from four): more CTAs fit per SM for the small folds
   using G = TileGeom<kFoldE>;

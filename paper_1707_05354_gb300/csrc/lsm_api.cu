@@ -14,6 +14,7 @@
 // the fold that read it (an event per buffer).
 #include <atomic>
 #include <cstdlib>
+#include <mutex>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -27,6 +28,30 @@ namespace gpulsm {
 static std::atomic<uint64_t> g_launches{0};
 void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+// lsm_debug_fail_allocs: allocations still allowed, then failures to give.
+static std::mutex g_fail_mu;
+static uint64_t g_fail_skip = 0, g_fail_count = 0;
+static std::atomic<bool> g_fail_armed{false};
+cudaError_t alloc_gate() {
+  if (!g_fail_armed.load(std::memory_order_acquire)) return cudaSuccess;
+  std::lock_guard<std::mutex> lock(g_fail_mu);
+  if (g_fail_skip) {
+    --g_fail_skip;
+    return cudaSuccess;
+  }
+  if (g_fail_count) {
+    if (--g_fail_count == 0) g_fail_armed.store(false, std::memory_order_release);
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaSuccess;
+}
+void debug_fail_allocs(uint64_t skip, uint64_t count) {
+  std::lock_guard<std::mutex> lock(g_fail_mu);
+  g_fail_skip = skip;
+  g_fail_count = count;
+  g_fail_armed.store(count != 0, std::memory_order_release);
+}
 }  // namespace gpulsm
 
 struct lsm_t {
@@ -74,6 +99,7 @@ struct lsm_t {
   SortWorkspace qsws{};
   uint32_t* d_qctl = nullptr;
   int lookup_mode = 0;
+  bool key_check_deferred = false;  // LSM_OPT_KEY_CHECK
   // kernel profiler
   bool prof = false;
   struct ProfRec {
@@ -124,6 +150,8 @@ int ffz(uint64_t r) {
 
 template <typename T>
 cudaError_t dalloc(T** p, uint64_t count) {
+  const cudaError_t g = alloc_gate();
+  if (g != cudaSuccess) return g;
   return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (count ? count : 1));
 }
 
@@ -220,7 +248,8 @@ cudaError_t ensure_q(lsm_t* h, size_t bytes) {
     if (e != cudaSuccess) return e;
   }
   const size_t want = round_up(bytes + bytes / 4, 1 << 20);
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&h->d_q), want);
+  cudaError_t e = alloc_gate();
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&h->d_q), want);
   if (e == cudaSuccess) h->q_bytes = want;
   return e;
 }
@@ -248,7 +277,7 @@ cudaError_t sort_positions(lsm_t* h, const uint32_t* keys, uint64_t n, uint64_t 
     if ((e = cudaMemset(h->d_qctl, 0, sizeof(uint32_t) * 2 * kSortCtlWords)) != cudaSuccess) return e;
     h->qsws.flip = 0;
   }
-  if (!h->qsws.tilecnt && (e = dalloc(&h->qsws.tilecnt, kMsdTileWords)) != cudaSuccess) return e;
+  if (!h->qsws.tilecnt && (e = dalloc(&h->qsws.tilecnt, kMsdWsWords)) != cudaSuccess) return e;
   h->qsws.ctl = h->d_qctl;
   h->qsws.sticky = h->d_misc + kMiscSticky;
   uint32_t* base = reinterpret_cast<uint32_t*>(h->d_q);
@@ -266,11 +295,16 @@ cudaError_t sort_positions(lsm_t* h, const uint32_t* keys, uint64_t n, uint64_t 
   return sort_launch(a, h->qsws, st, nullptr, nullptr);
 }
 
-// One batch of n_in <= b ops into level ffz(r).  With `checked`, waits for
-// the device key check of this batch and leaves the dictionary alone if it
-// failed (the batch only wrote a free sorted-batch buffer).
+// One batch of n_in <= b ops into level ffz(r).  With `checked`, the keys
+// are checked on the device: by default the host waits for that check and
+// leaves the dictionary alone if it failed (the batch only wrote a free
+// sorted-batch buffer); with the deferred check (LSM_OPT_KEY_CHECK = 1, batch
+// sizes of the bucket sort) nothing waits, and a failed batch is applied as
+// placebos and recorded in the sticky error word.
 lsm_status apply_batch(lsm_t* h, int mode, const uint32_t* keys, const uint32_t* vals, const uint8_t* del,
                        uint64_t n_in, cudaStream_t st, bool checked) {
+  const bool deferred = checked && h->key_check_deferred && h->b <= kMsdMaxN;
+  if (deferred) checked = false;
   const int k = ffz(h->r);
   if (k >= int(h->L)) return LSM_ERR_FULL;
   // next buffer in rotation that does not hold level 0; wait for the fold
@@ -291,6 +325,7 @@ lsm_status apply_batch(lsm_t* h, int mode, const uint32_t* keys, const uint32_t*
   a.tmp_vals = h->d_tv;
   a.fence = buf_fence(h, j);
   a.fshift = h->fshift[0];
+  a.defer_err = deferred ? h->d_misc + kMiscSticky : nullptr;
   {
     ProfScope ps(h, LSM_PROF_SORT, 16.0 * h->b, st);
     if (checked) *reinterpret_cast<volatile uint32_t*>(h->h_status) = 0u;
@@ -362,6 +397,16 @@ lsm_status apply_call(lsm_t* h, int mode, const uint32_t* keys, const uint32_t* 
   const uint64_t limit = (h->L >= 64) ? ~0ull : ((1ull << h->L) - 1);
   if (h->r + nb > limit) return LSM_ERR_FULL;
   if (nb == 1) return apply_batch(h, mode, keys, vals, nullptr, n, st, true);
+  if (h->key_check_deferred && h->b <= kMsdMaxN) {
+    // deferred check: every batch checks its own keys on the device
+    for (uint64_t c = 0; c < nb; ++c) {
+      const uint64_t off = c * h->b;
+      const uint64_t m = (n - off) < h->b ? (n - off) : h->b;
+      lsm_status s = apply_batch(h, mode, keys + off, vals ? vals + off : nullptr, nullptr, m, st, true);
+      if (s != LSM_OK) return s;
+    }
+    return LSM_OK;
+  }
   LSM_TRY(cudaMemsetAsync(h->d_misc + kMiscCheck, 0, sizeof(uint32_t), st));
   LSM_TRY(check_keys_launch(keys, n, h->d_misc + kMiscCheck, st));
   LSM_TRY(cudaMemcpyAsync(h->h_status, h->d_misc + kMiscCheck, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -461,7 +506,7 @@ lsm_status lsm_create(lsm_t** out, uint32_t b, uint64_t max_elements, int device
   if (e == cudaSuccess) e = dalloc(&h->sws.ctl, 2 * kSortCtlWords);
   if (e == cudaSuccess) e = cudaMemset(h->sws.ctl, 0, sizeof(uint32_t) * 2 * kSortCtlWords);
   if (e == cudaSuccess) e = dalloc(&h->sws.lookback, uint64_t(kSortPasses) * sort_tiles * 256);
-  if (e == cudaSuccess && b <= kMsdMaxN) e = dalloc(&h->sws.tilecnt, kMsdTileWords);
+  if (e == cudaSuccess && b <= kMsdMaxN) e = dalloc(&h->sws.tilecnt, msd_ws_words(b));
   if (e == cudaSuccess) e = dalloc(&h->d_part, h->part_words);
   for (uint32_t i = 0; i < L + kBatchBufs; ++i) {
     h->fshift[i] = fence_shift_for(i < L ? (uint64_t(b) << i) : uint64_t(b));
@@ -470,8 +515,10 @@ lsm_status lsm_create(lsm_t** out, uint32_t b, uint64_t max_elements, int device
   if (e == cudaSuccess) e = dalloc(&h->d_fence, h->fence_off[L + kBatchBufs]);
   if (e == cudaSuccess) e = dalloc(&h->d_misc, kMiscWords);
   if (e == cudaSuccess) e = dalloc(&h->d_u64, 8);
+  if (e == cudaSuccess) e = alloc_gate();
   if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&h->h_status), 64, cudaHostAllocMapped);
   if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->d_status_map), h->h_status, 0);
+  if (e == cudaSuccess) e = alloc_gate();
   if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&h->h_u64), 64, cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemset(h->d_keys, 0, sizeof(uint32_t) * (h->capacity + kSlack));
@@ -740,7 +787,7 @@ lsm_status lsm_bulk_build(lsm_t* h, const uint32_t* d_keys, const uint32_t* d_va
   cudaError_t e = dalloc(&buf, 4 * npad + fence_words(fs));
   if (e == cudaSuccess) e = dalloc(&ctl, 2 * kSortCtlWords);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, 4ull * 2 * kSortCtlWords, st);
-  if (e == cudaSuccess) e = dalloc(&tilecnt, kMsdTileWords);
+  if (e == cudaSuccess) e = dalloc(&tilecnt, msd_ws_words(n < kMsdMaxN ? n : kMsdMaxN));
   if (e == cudaSuccess) e = dalloc(&lookback, uint64_t(kSortPasses) * tiles * 256);
   if (e == cudaSuccess) e = cudaMemsetAsync(lookback, 0, 8ull * kSortPasses * tiles * 256, st);
   if (e == cudaSuccess) {
@@ -897,6 +944,11 @@ lsm_status lsm_set_option(lsm_t* h, lsm_option opt, int64_t value) {
     h->lookup_mode = int(value);
     return LSM_OK;
   }
+  if (opt == LSM_OPT_KEY_CHECK) {
+    if (value < 0 || value > 1) return LSM_ERR_ARG;
+    h->key_check_deferred = value == 1;
+    return LSM_OK;
+  }
   return LSM_ERR_ARG;
 }
 
@@ -908,6 +960,10 @@ lsm_status lsm_get_option(lsm_t* h, lsm_option opt, int64_t* value) {
   if (!h || !value) return LSM_ERR_ARG;
   if (opt == LSM_OPT_LOOKUP_MODE) {
     *value = h->lookup_mode;
+    return LSM_OK;
+  }
+  if (opt == LSM_OPT_KEY_CHECK) {
+    *value = h->key_check_deferred ? 1 : 0;
     return LSM_OK;
   }
   if (opt == LSM_OPT_DEVICE_ERROR) {

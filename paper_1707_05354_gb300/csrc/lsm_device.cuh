@@ -210,16 +210,30 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Bounded spinning, shared by every wait of the library: a waiter calls
+// spin_continue after each unsuccessful poll, with t0 = 0 before the first;
+// once the wait has lasted limit_ns (globaltimer) it records kErrTimeout in
+// *status and returns false, and the waiter stops waiting and carries on
+// without the value (the call then reports LSM_ERR_TIMEOUT through the
+// status word instead of hanging the GPU).
+__device__ __forceinline__ bool spin_continue(uint64_t& t0, uint64_t limit_ns, uint32_t* status) {
+  const uint64_t now = globaltimer_ns();
+  if (t0 == 0) {
+    t0 = now | 1u;  // never 0 once started
+    return true;
+  }
+  if (now - t0 > limit_ns) {
+    atomicOr(status, kErrTimeout);
+    return false;
+  }
+  return true;
+}
+
 // Bounded wait on phase `parity`; false (and kErrTimeout) if it never completes.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t* status) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = globaltimer_ns();
-  while (!mbar_try_wait(bar, parity)) {
-    if (globaltimer_ns() - t0 > kWaitLimitNs) {
-      atomicOr(status, kErrTimeout);
-      return false;
-    }
-  }
+  uint64_t t0 = 0;
+  while (!mbar_try_wait(bar, parity))
+    if (!spin_continue(t0, kWaitLimitNs, status)) return false;
   return true;
 }
 

@@ -2,7 +2,9 @@
 // kernel translation units.  Plain structs of device pointers and sizes.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
 namespace gpulsm {
@@ -25,6 +27,30 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
+
+// Raises a kernel's dynamic shared-memory limit, an attribute of the current
+// device, once per device and thread-safely: `f` keeps one flag per device
+// ordinal for that kernel.
+constexpr int kMaxDevices = 64;
+struct PerDeviceFlags {
+  std::atomic<bool> done[kMaxDevices] = {};
+  std::mutex mu;
+};
+template <typename K>
+cudaError_t set_smem_attr_once(K kernel, size_t bytes, int dev, PerDeviceFlags& f) {
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (f.done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  std::lock_guard<std::mutex> lock(f.mu);
+  if (f.done[dev].load(std::memory_order_relaxed)) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  if (e == cudaSuccess) f.done[dev].store(true, std::memory_order_release);
+  return e;
+}
+
+// Allocation fault injection (lsm_debug_fail_allocs): every device or
+// pinned-host allocation of the library asks the gate first, and gets
+// cudaErrorMemoryAllocation instead of memory while a failure is armed.
+cudaError_t alloc_gate();
 
 // Number of kernels this library has launched (all handles); read through
 // LSM_OPT_KERNEL_LAUNCHES.  Incremented by every launcher below.
@@ -85,6 +111,10 @@ struct SortArgs {
   uint32_t* tmp_vals;
   uint32_t* fence;      // prefix index of the sorted output to write, or null
   int fshift;
+  // Deferred key check (bucket path only): when set, a batch holding a key
+  // above the user range is written as n placebo tombstones instead of being
+  // sorted, and kErrBadKey is ORed into *defer_err; nothing waits on the host.
+  uint32_t* defer_err;
 };
 
 struct SortWorkspace {
@@ -94,12 +124,19 @@ struct SortWorkspace {
   uint32_t max_tiles;
   uint32_t epoch;       // bumped per sort; 0 never used
   uint32_t* sticky;     // persistent device error word (wait timeouts)
-  uint32_t* tilecnt;    // kMsdTileWords words (bucket sort of n <= kMsdMaxN), or null
+  uint32_t* tilecnt;    // msd_ws_words(n) words for every sort of n <= kMsdMaxN it serves, or null
 };
-// The bucket sort (n <= kMsdMaxN): per-tile bucket counts and offsets.
+// The bucket sort (n <= kMsdMaxN): the run table (per bucket and tile, the
+// start and length of the bucket's run in the tile), then the spill area of
+// buckets too large for shared memory (n keys, then n values).
 constexpr uint32_t kMsdMaxN = 1u << 20;
 constexpr uint32_t kMsdTile = 4096;
-constexpr uint32_t kMsdTileWords = 2 * (kMsdMaxN / kMsdTile) * 256;
+constexpr uint32_t kMsdMaxTiles = kMsdMaxN / kMsdTile;
+constexpr uint32_t kMsdRunWords = 2 * kMsdMaxTiles * 256;
+// Workspace words for sorts of at most max_n <= kMsdMaxN elements (the spill
+// area holds a sort's n keys, then its n values).
+constexpr uint64_t msd_ws_words(uint64_t max_n) { return kMsdRunWords + 2 * max_n; }
+constexpr uint64_t kMsdWsWords = msd_ws_words(kMsdMaxN);
 constexpr int kSortCtlWords = kSortPasses * 256 + kSortPasses + 4;
 constexpr int kSortCtlStatus = kSortPasses * 256 + kSortPasses;
 

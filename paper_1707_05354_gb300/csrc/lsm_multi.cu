@@ -81,6 +81,8 @@ lsm_status cuda_status(cudaError_t e) {
 
 template <typename T>
 cudaError_t dalloc(T** p, uint64_t count) {
+  const cudaError_t g = alloc_gate();
+  if (g != cudaSuccess) return g;
   return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (count ? count : 1));
 }
 

@@ -165,10 +165,14 @@ namespace {
 
 template <typename T>
 cudaError_t dalloc(T** p, uint64_t count) {
+  const cudaError_t g = alloc_gate();
+  if (g != cudaSuccess) return g;
   return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (count ? count : 1));
 }
 template <typename T>
 cudaError_t halloc(T** p, uint64_t count) {
+  const cudaError_t g = alloc_gate();
+  if (g != cudaSuccess) return g;
   return cudaHostAlloc(reinterpret_cast<void**>(p), sizeof(T) * (count ? count : 1), cudaHostAllocDefault);
 }
 
@@ -177,7 +181,7 @@ uint64_t slot_bytes(const lsm_server_config& c, uint32_t max_levels, uint32_t ma
   const uint64_t b = rup(c.b, 32) + 32, G = rup(c.group_keys, 32) + 32;
   return b * 9 + G * (4 + 4 + 1) + G * 12 + G * (4 + 4 + 4 + 8ull * max_levels) + (G + 1) * 8 +
          (G / 2048 + 2) * 8 + uint64_t(c.range_cap) * 8 + uint64_t(max_req) * (8 + 8 + 1) + 8 * 4 * G +
-         4ull * kMsdTileWords + 64;
+         4ull * msd_ws_words(G < kMsdMaxN ? G : kMsdMaxN) + 64;
 }
 
 // Device bytes of a dictionary with L levels of batch size b, as lsm_create
@@ -255,7 +259,7 @@ cudaError_t alloc_slot(Slot& s, const lsm_server_config& c, uint32_t max_levels,
   for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreate(&s.ev_ph[i]);
   if (e == cudaSuccess) e = dalloc(&s.sort_ctl, 2 * kSortCtlWords);
   if (e == cudaSuccess) e = cudaMemset(s.sort_ctl, 0, 4ull * 2 * kSortCtlWords);
-  if (e == cudaSuccess) e = dalloc(&s.sort_tilecnt, kMsdTileWords);
+  if (e == cudaSuccess) e = dalloc(&s.sort_tilecnt, msd_ws_words(G < kMsdMaxN ? G : kMsdMaxN));
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
     e = dalloc(&s.sa[i], G);
     if (e == cudaSuccess) e = dalloc(&s.sb[i], G);
@@ -496,6 +500,7 @@ struct Run {
     uint32_t *dk = sl.rk, *dv = sl.rv, *hk = sl.h_rk, *hv = sl.h_rv;
     if (total > s->cfg.range_cap) {
       // rare: more results than the slot holds; buffers for this group only
+      LSM_TRY(alloc_gate());
       LSM_TRY(cudaMallocAsync(reinterpret_cast<void**>(&g.big_k), 4 * total, s->st));
       LSM_TRY(cudaMallocAsync(reinterpret_cast<void**>(&g.big_v), 4 * total, s->st));
       LSM_TRY(cudaHostAlloc(reinterpret_cast<void**>(&g.h_big_k), 4 * total, cudaHostAllocDefault));
@@ -767,7 +772,7 @@ lsm_status lsm_server_set_pool(lsm_server_t* s, const uint32_t* d_a, const uint3
   // update keys come from pool a: check them once here, so that batches need
   // no per-batch key check
   uint32_t* flag = nullptr;
-  LSM_TRY(cudaMalloc(reinterpret_cast<void**>(&flag), 4));
+  LSM_TRY(dalloc(&flag, 1));
   cudaError_t e = cudaMemsetAsync(flag, 0, 4, s->st);
   if (e == cudaSuccess) e = check_keys_launch(d_a, n, flag, s->st);
   uint32_t h = 0;

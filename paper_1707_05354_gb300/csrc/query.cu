@@ -516,11 +516,7 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const uint32_t* __restri
       while (t >= 0) {
         const uint64_t w = ld_relaxed_u64(lookback + t);
         if (!(w & (kLbAgg | kLbIncl))) {
-          if (t0 == 0) t0 = globaltimer_ns();
-          else if (globaltimer_ns() - t0 > kWaitLimitNs) {
-            atomicOr(status, kErrTimeout);
-            break;
-          }
+          if (!spin_continue(t0, kWaitLimitNs, status)) break;
           continue;
         }
         prefix += w & kLbMask;

@@ -230,14 +230,7 @@ __global__ void __launch_bounds__(kThreads, LSM_SORT_MINB) sort_pass(Loader ld, 
         if (flag == kFlagIncl) done = true;
       }
       t -= consumed;
-      if (!done && consumed == 0) {
-        if (t0 == 0) {
-          t0 = globaltimer_ns();
-        } else if (globaltimer_ns() - t0 > kWaitLimitNs) {
-          atomicOr(sticky, kErrTimeout);
-          break;
-        }
-      }
+      if (!done && consumed == 0 && !spin_continue(t0, kWaitLimitNs, sticky)) break;
     }
     st_relaxed_u64(my, lb_pack(epoch, kFlagIncl, prefix + total));
   }
@@ -260,20 +253,22 @@ __global__ void __launch_bounds__(kThreads, LSM_SORT_MINB) sort_pass(Loader ld, 
 // ---------------------------------------------------------------------------
 // Bucket sort for n <= kMsdMaxN (the batch sizes of the plain form): the top
 // byte of the key variable first, then the low 24 bits inside each bucket.
-//   msd_count    per 4096-element tile of the (encoded, reversed) input: the
-//                count of each top byte, and the grand totals; key check.
-//   msd_offsets  per bucket: the exclusive scan of its tile counts plus the
-//                bucket's start, i.e. where each tile's run of that bucket
-//                goes -- every offset is exact before any element moves, so
-//                the scatter needs no look-back between tiles.
-//   msd_scatter  per tile: stable rank by top byte in shared memory, then
-//                each element to its bucket run.
-//   bucket_sort  per bucket, one CTA: the bucket (at most kBucketCap
-//                elements) is sorted on bits 0..23 by three stable 8-bit
-//                passes entirely in shared memory and written out; the CTA
-//                also writes the prefix index entries of its 256 bins.  A
-//                larger bucket (heavy duplicate keys) is sorted by the same
-//                CTA in chunks through global memory, still stably.
+// Two kernels, so that a batch sort is one dependent launch after another:
+//   msd_tile     per 4096-element tile of the (encoded, reversed) input: the
+//                tile stably sorted by its top byte in shared memory and
+//                written back to the scratch at the tile's own place (one
+//                coalesced write), so bucket d's elements of tile t form the
+//                run runs[d][t] = (start, count) there; the grand total of
+//                each bucket (global atomics) and the key check.
+//   bucket_sort  per bucket, one CTA: the bucket's runs, in tile order (the
+//                stable order), gathered into shared memory -- the start of
+//                the bucket in the output is the sum of the totals before
+//                it, so no tile waits for another -- then sorted on bits
+//                0..23 and written out with the prefix index entries of its
+//                256 bins.  A bucket above kBucketCap elements (heavy
+//                duplicate keys) is gathered into the spill area and sorted
+//                by the same CTA in chunks through global memory, still
+//                stably.
 // ---------------------------------------------------------------------------
 constexpr int kBucketThreads = 512;
 constexpr int kBucketWarps = kBucketThreads / 32;
@@ -282,53 +277,13 @@ constexpr uint32_t kBucketCap = kBucketThreads * kBucketIPT;  // 5120
 constexpr uint32_t kSubBins = 4096;      // counting pass of the bucket fast path
 constexpr uint32_t kSubBinMax = 48;      // larger sub-bins take the pass-by-pass path
 
-// The count and the scatter run 512 threads of 8 elements per
-// 4096-element tile: many warps to keep loads in flight, and a short
-// ranking chain per warp in the scatter.
+// The tile kernel runs 512 threads of 8 elements per 4096-element tile:
+// many warps to keep loads in flight, and a short ranking chain per warp.
 constexpr int kScatterThreads = 512;
 constexpr int kScatterWarps = kScatterThreads / 32;
 constexpr int kScatterIPT = int(kMsdTile) / kScatterThreads;  // 8
 static_assert(kScatterIPT * kScatterThreads == int(kMsdTile), "tile");
-
-// The padding of a short batch (copies of its last op, the leading
-// positions of the reversed sequence) is neither counted per tile nor
-// scattered: it is one run of equal elements, added to its bucket's total
-// here and written by that bucket's sort at its sorted place.
-__global__ void __launch_bounds__(kScatterThreads) msd_count(Loader ld, uint32_t* __restrict__ tilecnt,
-                                                      uint32_t* __restrict__ ctl, uint32_t* status) {
-  __shared__ uint32_t s_h[kRadix];
-  pdl_trigger();
-  pdl_wait();
-  const uint32_t tid = threadIdx.x, tile = blockIdx.x;
-  const uint32_t npad = ld.npad();
-  if (tid < kRadix) s_h[tid] = 0;
-  __syncthreads();
-  uint32_t kv[kScatterIPT];
-  bool bad_any = false;
-#pragma unroll
-  for (int j = 0; j < kScatterIPT; ++j) {
-    const uint32_t p = tile * kMsdTile + j * kScatterThreads + tid;
-    bool bad = false;
-    kv[j] = (p < ld.n && p >= npad) ? ld.load_key(p, bad) : 0u;
-    bad_any |= bad;
-  }
-#pragma unroll
-  for (int j = 0; j < kScatterIPT; ++j) {
-    const uint32_t p = tile * kMsdTile + j * kScatterThreads + tid;
-    if (p < ld.n && p >= npad) atomicAdd(&s_h[kv[j] >> 24], 1u);
-  }
-  const int any_bad = __syncthreads_or(bad_any);
-  if (tid < kRadix) {
-    const uint32_t c = s_h[tid];
-    tilecnt[tile * kRadix + tid] = c;
-    if (c) atomicAdd(ctl + 3 * kRadix + tid, c);
-  }
-  if (tile == 0 && tid == 0 && npad) {
-    bool bad;
-    atomicAdd(ctl + 3 * kRadix + (ld.load_key(0, bad) >> 24), npad);
-  }
-  if (any_bad && tid == 0 && status) *reinterpret_cast<volatile uint32_t*>(status) = kErrBadKey;
-}
+static_assert(kMsdMaxTiles <= uint32_t(kBucketThreads), "one thread per tile run in the bucket kernel");
 
 // Start of bucket d in the output: the sum of the totals of the buckets
 // before it (every thread of the block gets it).
@@ -340,20 +295,6 @@ __device__ __forceinline__ uint32_t bucket_start(const uint32_t* ctl, uint32_t d
   uint32_t tot;
   block_excl_scan<NT>(x, s_scan, tot);
   return tot;
-}
-
-__global__ void __launch_bounds__(kThreads) msd_offsets(const uint32_t* __restrict__ tilecnt, uint32_t ntiles,
-                                                        const uint32_t* __restrict__ ctl,
-                                                        uint32_t* __restrict__ tileoff) {
-  __shared__ uint32_t s_scan[kWarps];
-  pdl_trigger();
-  pdl_wait();
-  const uint32_t d = blockIdx.x, t = threadIdx.x;
-  const uint32_t base = bucket_start<kThreads>(ctl, d, s_scan);
-  const uint32_t c = t < ntiles ? tilecnt[t * kRadix + d] : 0u;
-  uint32_t tot;
-  const uint32_t excl = block_excl_scan<kThreads>(c, s_scan, tot);
-  if (t < ntiles) tileoff[t * kRadix + d] = base + excl;
 }
 
 // Stable in-shared-memory rank of up to IPT items per thread of a warp-striped
@@ -401,21 +342,26 @@ __device__ __forceinline__ void rank_block(const uint32_t (&kv)[IPT], uint32_t m
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kScatterThreads) msd_scatter(Loader ld, const uint32_t* __restrict__ tileoff,
-                                                        uint32_t* __restrict__ out_k,
-                                                        uint32_t* __restrict__ out_v) {
+// The padding of a short batch (copies of its last op, the leading
+// positions of the reversed sequence) is neither ranked nor written: it is
+// one run of equal elements, added to its bucket's total here and written by
+// that bucket's sort at its sorted place.  A tile of padding only still
+// writes its (empty) runs.
+__global__ void __launch_bounds__(kScatterThreads) msd_tile(Loader ld, uint32_t* __restrict__ tmp_k,
+                                                     uint32_t* __restrict__ tmp_v, uint2* __restrict__ runs,
+                                                     uint32_t* __restrict__ ctl, uint32_t* status) {
   __shared__ __align__(16) uint32_t s_keys[kMsdTile];
   __shared__ __align__(16) uint32_t s_vals[kMsdTile];
   __shared__ uint32_t s_whist[kScatterWarps][kRadix];
-  __shared__ uint32_t s_excl[kRadix], s_gbase[kRadix], s_scan[kScatterWarps];
+  __shared__ uint32_t s_excl[kRadix], s_cnt[kRadix], s_scan[kScatterWarps];
   pdl_trigger();
   pdl_wait();
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5, tile = blockIdx.x;
   const uint32_t n = ld.n, npad = ld.npad();
   const uint32_t t0 = tile * kMsdTile;
-  if (t0 + kMsdTile <= npad) return;  // whole CTA: padding only
   const uint32_t base = t0 + warp * (32 * kScatterIPT);
   uint32_t kv[kScatterIPT], v[kScatterIPT], rank[kScatterIPT];
+  bool bad_any = false;
 #pragma unroll
   for (int j = 0; j < kScatterIPT; ++j) {
     const uint32_t p = base + j * 32 + lane;
@@ -424,10 +370,10 @@ __global__ void __launch_bounds__(kScatterThreads) msd_scatter(Loader ld, const 
     if (p < n && p >= npad) {
       bool bad;
       ld.load(p, kv[j], v[j], bad);
+      bad_any |= bad;
     }
   }
-  if (tid < kRadix) s_gbase[tid] = tileoff[tile * kRadix + tid];
-  rank_block<kScatterThreads, kScatterIPT>(kv, n, base, 24, rank, s_whist, s_excl, s_scan, nullptr, npad);
+  rank_block<kScatterThreads, kScatterIPT>(kv, n, base, 24, rank, s_whist, s_excl, s_scan, s_cnt, npad);
 #pragma unroll
   for (int j = 0; j < kScatterIPT; ++j) {
     const uint32_t p = base + j * 32 + lane;
@@ -438,18 +384,23 @@ __global__ void __launch_bounds__(kScatterThreads) msd_scatter(Loader ld, const 
       s_vals[pos] = v[j];
     }
   }
-  __syncthreads();
+  const int any_bad = __syncthreads_or(bad_any);  // also orders the writes above before the reads below
   const uint32_t lo_t = t0 > npad ? t0 : npad, hi_t = (n - t0) < kMsdTile ? n : t0 + kMsdTile;
   const uint32_t tile_n = hi_t > lo_t ? hi_t - lo_t : 0u;  // real elements of the tile
   for (uint32_t i = tid; i < tile_n; i += kScatterThreads) {
-    const uint32_t k = s_keys[i];
-    const uint32_t d = k >> 24;
-    const uint32_t dst = s_gbase[d] + (i - s_excl[d]);
-    if (dst < n) {
-      out_k[dst] = k;
-      out_v[dst] = s_vals[i];
-    }
+    tmp_k[t0 + i] = s_keys[i];
+    tmp_v[t0 + i] = s_vals[i];
   }
+  if (tid < kRadix) {
+    const uint32_t c = s_cnt[tid];
+    runs[tid * kMsdMaxTiles + tile] = make_uint2(t0 + s_excl[tid], c);
+    if (c) atomicAdd(ctl + 3 * kRadix + tid, c);
+  }
+  if (tile == 0 && tid == 0 && npad) {
+    bool bad;
+    atomicAdd(ctl + 3 * kRadix + (ld.load_key(0, bad) >> 24), npad);
+  }
+  if (any_bad && tid == 0 && status) *reinterpret_cast<volatile uint32_t*>(status) = kErrBadKey;
 }
 
 // First position i in [0, m) with (a[i] >> fshift) >= bin, a sorted.
@@ -504,11 +455,37 @@ __device__ __forceinline__ void bucket_write(const uint32_t* a, const uint32_t* 
   }
 }
 
-// One bucket, one CTA of kBucketThreads: sorts tmp[start, start + m) stably
-// by the low `rest` bits of the key variable (the bits above are the
-// bucket's and equal) into out[start, start + m), and writes the
-// prefix-index entries of the bucket's bins [bin0, bin0 + nbins) when fence
-// is given.
+// Where element i of a bucket lives in the scratch its sort reads.
+// ContigSrc: elements start .. start + m - 1 (the batched form's scatter
+// writes every bucket contiguously).  RunSrc: the bucket's runs over the
+// tiles, in tile order (the stable order); rstart[t] is the first bucket
+// position of run t (an exclusive scan of the run lengths) and run t's
+// element i - rstart[t] sits at rbase[t] + i (both in shared memory).
+struct ContigSrc {
+  uint32_t start;
+  __device__ __forceinline__ uint32_t at(uint32_t i) const { return start + i; }
+};
+struct RunSrc {
+  const uint32_t* rstart;
+  const uint32_t* rbase;
+  uint32_t nruns;  // >= 1
+  // the largest t with rstart[t] <= i: the run holding i (empty runs share
+  // their start with the next run, so they are never the largest)
+  __device__ __forceinline__ uint32_t at(uint32_t i) const {
+    uint32_t lo = 0, hi = nruns - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (rstart[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return rbase[lo] + i;
+  }
+};
+
+// One bucket, one CTA of kBucketThreads: sorts the m elements src.at(0 ..
+// m - 1) of (src_k, src_v) stably by the low `rest` bits of the key variable
+// (the bits above are the bucket's and equal) into out[start, start + m),
+// and writes the prefix-index entries of the bucket's bins [bin0, bin0 +
+// nbins) when fence is given.
 //   Fast path (bucket in shared memory, no sub-bin above kSubBinMax): one
 //   counting pass on the top 12 of the `rest` bits places every element in
 //   its sub-bin (about one element each for spread keys), at an arbitrary
@@ -516,12 +493,15 @@ __device__ __forceinline__ void bucket_write(const uint32_t* a, const uint32_t* 
 //   the sub-bin by (key variable, index in the bucket), the stable order.
 //   Otherwise: ceil(rest / 8) stable 8-bit passes in shared memory, or, for
 //   a bucket above kBucketCap (heavy duplicate keys), the same passes in
-//   chunks through global memory.
+//   chunks through global memory, alternating between out and spill (both
+//   indexed like out: [start, start + m) belongs to this bucket alone).
 // A run of `pad` copies of (pad_kv, pad_v) (a short batch's padding, which
 // comes first among equal key variables in the stable order) is written at
 // its sorted place: the output holds m + pad elements.
 // bsm holds 4 kBucketCap words plus kBucketCap 16-bit indexes.
-__device__ __forceinline__ void bucket_body(uint32_t* tmp_k, uint32_t* tmp_v, uint32_t* out_k, uint32_t* out_v,
+template <class Src>
+__device__ __forceinline__ void bucket_body(const uint32_t* src_k, const uint32_t* src_v, const Src& src,
+                                            uint32_t* spill_k, uint32_t* spill_v, uint32_t* out_k, uint32_t* out_v,
                                             uint32_t start, uint32_t m, int rest, uint32_t* __restrict__ fence,
                                             int fshift, uint32_t bin0, uint32_t nbins, uint32_t* bsm,
                                             uint32_t* s_scan, uint32_t pad, uint32_t pad_kv, uint32_t pad_v) {
@@ -550,9 +530,10 @@ __device__ __forceinline__ void bucket_body(uint32_t* tmp_k, uint32_t* tmp_v, ui
     for (int j = 0; j < kBucketIPT; ++j) {
       const uint32_t i = tid + j * kBucketThreads;
       if (i < m) {
-        const uint32_t k = tmp_k[start + i];
+        const uint32_t at = src.at(i);
+        const uint32_t k = src_k[at];
         ak[i] = k;
-        av[i] = tmp_v[start + i];
+        av[i] = src_v[at];
         slot[j] = atomicAdd(&cnt[(k >> sh) & (kSubBins - 1)], 1u);
       }
     }
@@ -620,11 +601,14 @@ __device__ __forceinline__ void bucket_body(uint32_t* tmp_k, uint32_t* tmp_v, ui
   }
 
   if (m <= kBucketCap) {
-    for (uint32_t i = tid; i < m; i += kBucketThreads) {
-      ak[i] = tmp_k[start + i];
-      av[i] = tmp_v[start + i];
+    if (rest < 12) {  // otherwise the fast path above has loaded the bucket already
+      for (uint32_t i = tid; i < m; i += kBucketThreads) {
+        const uint32_t at = src.at(i);
+        ak[i] = src_k[at];
+        av[i] = src_v[at];
+      }
+      __syncthreads();
     }
-    __syncthreads();
     uint32_t *sk = ak, *sv = av, *dk = bk, *dv = bv;
     for (int pass = 0; pass < npass; ++pass) {
       const int shift = 8 * pass;
@@ -653,18 +637,22 @@ __device__ __forceinline__ void bucket_body(uint32_t* tmp_k, uint32_t* tmp_v, ui
     bucket_write(sk, sv, m, out_k, out_v, start, pad, pad_kv, pad_v, fence, fshift, bin0, nbins);
     return;
   }
-  // Chunked: npass stable passes over [start, start + m) through global
-  // memory, alternating tmp -> out -> tmp ..., kBucketCap elements at a time
-  // in order; an even pass count ends in tmp and is copied to out.
-  const uint32_t* srck = tmp_k;
-  const uint32_t* srcv = tmp_v;
+  // Chunked: npass stable passes through global memory, kBucketCap elements
+  // at a time in order: pass 0 from the source to out, then alternating
+  // out -> spill -> out ...; an even pass count ends in spill and is copied
+  // to out.
+  const uint32_t* curk = out_k;
+  const uint32_t* curv = out_v;
   uint32_t* dstk = out_k;
   uint32_t* dstv = out_v;
   for (int pass = 0; pass < npass; ++pass) {
     const int shift = 8 * pass;
     if (tid < kRadix) s_tot[tid] = 0;
     __syncthreads();
-    for (uint32_t i = tid; i < m; i += kBucketThreads) atomicAdd(&s_tot[(srck[start + i] >> shift) & 255u], 1u);
+    for (uint32_t i = tid; i < m; i += kBucketThreads) {
+      const uint32_t k = pass == 0 ? src_k[src.at(i)] : curk[start + i];
+      atomicAdd(&s_tot[(k >> shift) & 255u], 1u);
+    }
     __syncthreads();
     uint32_t all;
     const uint32_t ex = block_excl_scan<kBucketThreads>(tid < kRadix ? s_tot[tid] : 0u, s_scan, all);
@@ -675,8 +663,18 @@ __device__ __forceinline__ void bucket_body(uint32_t* tmp_k, uint32_t* tmp_v, ui
 #pragma unroll
       for (int j = 0; j < kBucketIPT; ++j) {
         const uint32_t p = wbase + j * 32 + lane;
-        kv[j] = p < cm ? srck[start + c0 + p] : 0u;
-        v[j] = p < cm ? srcv[start + c0 + p] : 0u;
+        kv[j] = 0u;
+        v[j] = 0u;
+        if (p < cm) {
+          if (pass == 0) {
+            const uint32_t at = src.at(c0 + p);
+            kv[j] = src_k[at];
+            v[j] = src_v[at];
+          } else {
+            kv[j] = curk[start + c0 + p];
+            v[j] = curv[start + c0 + p];
+          }
+        }
       }
       rank_block<kBucketThreads, kBucketIPT>(kv, cm, wbase, shift, rank, s_whist, s_excl, s_scan, s_tot);
 #pragma unroll
@@ -693,16 +691,15 @@ __device__ __forceinline__ void bucket_body(uint32_t* tmp_k, uint32_t* tmp_v, ui
       if (tid < kRadix) s_run[tid] += s_tot[tid];
       __syncthreads();
     }
-    if (pass & 1) {
-      srck = tmp_k; srcv = tmp_v; dstk = out_k; dstv = out_v;
-    } else {
-      srck = out_k; srcv = out_v; dstk = tmp_k; dstv = tmp_v;
-    }
+    curk = dstk;
+    curv = dstv;
+    dstk = (dstk == out_k) ? spill_k : out_k;
+    dstv = (dstv == out_v) ? spill_v : out_v;
   }
-  if (!(npass & 1)) {
+  if (curk != out_k) {
     for (uint32_t i = tid; i < m; i += kBucketThreads) {
-      out_k[start + i] = tmp_k[start + i];
-      out_v[start + i] = tmp_v[start + i];
+      out_k[start + i] = curk[start + i];
+      out_v[start + i] = curv[start + i];
     }
     __syncthreads();
   }
@@ -744,33 +741,66 @@ __device__ __forceinline__ void bucket_body(uint32_t* tmp_k, uint32_t* tmp_v, ui
   if (fence) bucket_fence(out_k + start, m + pad, start, bin0, nbins, fence, fshift);
 }
 
-__global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort(Loader ld, uint32_t* __restrict__ tmp_k,
-                                                              uint32_t* __restrict__ tmp_v,
-                                                              uint32_t* __restrict__ out_k,
+__global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort(Loader ld, const uint32_t* __restrict__ tmp_k,
+                                                              const uint32_t* __restrict__ tmp_v,
+                                                              const uint2* __restrict__ runs, uint32_t* spill_k,
+                                                              uint32_t* spill_v, uint32_t* __restrict__ out_k,
                                                               uint32_t* __restrict__ out_v,
                                                               const uint32_t* __restrict__ ctl, uint32_t n,
                                                               uint32_t* __restrict__ fence, int fshift,
-                                                              uint32_t* __restrict__ next_ctl) {
+                                                              uint32_t* __restrict__ next_ctl,
+                                                              uint32_t* defer_err) {
   extern __shared__ __align__(16) uint32_t bsm[];
   __shared__ uint32_t s_scan[kBucketWarps];
+  __shared__ uint32_t s_rstart[kMsdMaxTiles], s_rbase[kMsdMaxTiles];
   pdl_trigger();
   pdl_wait();
   const uint32_t tid = threadIdx.x, d = blockIdx.x;
+  const uint32_t ntiles = (n + kMsdTile - 1) / kMsdTile;
   // the control block of the next sort starts zeroed (it is idle now)
   if (d == 0)
     for (uint32_t i = tid; i < uint32_t(kSortCtlWords); i += kBucketThreads) next_ctl[i] = 0u;
-  const uint32_t start = bucket_start<kBucketThreads>(ctl, d, s_scan);
-  uint32_t m = ctl[3 * kRadix + d];
+  if (defer_err && ctl[kSortCtlStatus]) {
+    // Deferred key check failed: the batch becomes n placebo tombstones (the
+    // key 2^31 - 1 that no query sees), all in the last bin.
+    const uint32_t chunk = (n + kRadix - 1) / kRadix;
+    const uint32_t lo = d * chunk, hi = (lo + chunk) < n ? lo + chunk : n;
+    for (uint32_t i = lo + tid; i < hi; i += kBucketThreads) {
+      out_k[i] = kPlaceboKv;
+      out_v[i] = 0u;
+    }
+    if (fence) {
+      const uint32_t per = 1u << (24 - fshift);
+      for (uint32_t i = tid; i < per; i += kBucketThreads) fence[d * per + i] = 0u;
+      if (d == kRadix - 1 && tid == 0) {
+        fence[fence_bins(fshift)] = n;
+        fence[fence_bins(fshift) + 2] = 0u;
+        fence[fence_bins(fshift) + 3] = fence_bins(fshift) - 1;
+      }
+    }
+    if (d == 0 && tid == 0) atomicOr(defer_err, kErrBadKey);
+    return;
+  }
+  // this bucket's run in every tile, in tile order
+  const uint2 run = tid < ntiles ? runs[d * kMsdMaxTiles + tid] : make_uint2(0u, 0u);
+  uint32_t m;
+  const uint32_t rs = block_excl_scan<kBucketThreads>(run.y, s_scan, m);
+  if (tid < ntiles) {
+    s_rstart[tid] = rs;
+    s_rbase[tid] = run.x - rs;
+  }
+  const uint32_t start = bucket_start<kBucketThreads>(ctl, d, s_scan);  // its barriers publish the table
   // a short batch's padding: one run in the bucket of its key variable
   uint32_t pad = ld.npad(), pad_kv = 0, pad_v = 0;
   if (pad) {
     bool bad;
     ld.load(0, pad_kv, pad_v, bad);
-    if ((pad_kv >> 24) == d) m -= pad; else pad = 0;
+    if ((pad_kv >> 24) != d) pad = 0;
   }
   const uint32_t per = fence ? 1u << (24 - fshift) : 0u;  // bins per bucket
-  bucket_body(tmp_k, tmp_v, out_k, out_v, start, m, 24, fence, fshift, d * per, per, bsm, s_scan, pad, pad_kv,
-              pad_v);
+  const RunSrc src{s_rstart, s_rbase, ntiles};
+  bucket_body(tmp_k, tmp_v, src, spill_k, spill_v, out_k, out_v, start, m, 24, fence, fshift, d * per, per, bsm,
+              s_scan, pad, pad_kv, pad_v);
   // the bucket sort writes every entry: the populated range is all bins
   if (fence && d == kRadix - 1 && tid == 0) {
     fence[fence_bins(fshift)] = n;
@@ -954,8 +984,10 @@ __global__ void __launch_bounds__(kBucketThreads, 2) mseg_bucket(MultiArena ar) 
   const int fs = d.fshift0;
   const int rest = 32 - int(d.msd_bits);              // bits below the bucket bits
   const uint32_t per = 1u << (rest - fs);             // bins per bucket
-  bucket_body(ar.tkeys + d.boff, ar.tvals + d.boff, ok, ov, start, m, rest, of, fs, bucket * per, per, bsm,
-              s_scan, 0u, 0u, 0u);
+  uint32_t* tk = ar.tkeys + d.boff;
+  uint32_t* tv = ar.tvals + d.boff;
+  bucket_body(tk, tv, ContigSrc{start}, tk, tv, ok, ov, start, m, rest, of, fs, bucket * per, per, bsm, s_scan, 0u,
+              0u, 0u);
   if (bucket == (1u << d.msd_bits) - 1 && threadIdx.x == 0) {
     const uint32_t nb = fence_bins(fs);
     of[nb] = d.b;
@@ -967,38 +999,33 @@ __global__ void __launch_bounds__(kBucketThreads, 2) mseg_bucket(MultiArena ar) 
 }  // namespace
 
 constexpr size_t kBucketSmem = 4 * size_t(kBucketCap) * sizeof(uint32_t) + size_t(kBucketCap) * sizeof(uint16_t);
+PerDeviceFlags g_bucket_attr;
 
 cudaError_t bucket_sort_launch(const SortArgs& a, SortWorkspace& ws, cudaStream_t st, uint32_t* status,
                                cudaEvent_t ev) {
-  static bool attr_set = false;
   cudaError_t e;
-  if (!attr_set) {
-    e = cudaFuncSetAttribute(bucket_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBucketSmem));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = set_smem_attr_once(bucket_sort, kBucketSmem, dev, g_bucket_attr)) != cudaSuccess) return e;
   const uint32_t ntiles = (a.n + kMsdTile - 1) / kMsdTile;
-  uint32_t* tilecnt = ws.tilecnt;
-  uint32_t* tileoff = ws.tilecnt + kMsdTileWords / 2;
+  uint2* runs = reinterpret_cast<uint2*>(ws.tilecnt);
+  uint32_t* spill_k = ws.tilecnt + kMsdRunWords;
+  uint32_t* spill_v = spill_k + a.n;
   uint32_t* ctl = ws.ctl + ws.flip * kSortCtlWords;
   uint32_t* next = ws.ctl + (ws.flip ^ 1) * kSortCtlWords;
   Loader ld{a.mode, a.in_keys, a.in_vals, a.in_del, a.n_in, a.n};
+  // a deferred check leaves its verdict in the sort's own control block
+  uint32_t* check = a.defer_err ? ctl + kSortCtlStatus : status;
   count_launches(1);
-  if ((e = launch_pdl(msd_count, dim3(ntiles), dim3(kScatterThreads), 0, st, ld, tilecnt, ctl, status)) !=
-      cudaSuccess)
+  if ((e = launch_pdl(msd_tile, dim3(ntiles), dim3(kScatterThreads), 0, st, ld, a.tmp_keys, a.tmp_vals, runs, ctl,
+                      check)) != cudaSuccess)
     return e;
-  if (status && (e = cudaEventRecord(ev, st)) != cudaSuccess) return e;
+  if (status && !a.defer_err && (e = cudaEventRecord(ev, st)) != cudaSuccess) return e;
   count_launches(1);
-  if ((e = launch_pdl(msd_offsets, dim3(kRadix), dim3(kThreads), 0, st, tilecnt, ntiles, ctl, tileoff)) !=
-      cudaSuccess)
-    return e;
-  count_launches(1);
-  if ((e = launch_pdl(msd_scatter, dim3(ntiles), dim3(kScatterThreads), 0, st, ld, tileoff, a.tmp_keys,
-                      a.tmp_vals)) != cudaSuccess)
-    return e;
-  count_launches(1);
-  if ((e = launch_pdl(bucket_sort, dim3(kRadix), dim3(kBucketThreads), kBucketSmem, st, ld, a.tmp_keys, a.tmp_vals,
-                      a.out_keys, a.out_vals, ctl, a.n, a.fence, a.fshift, next)) != cudaSuccess)
+  if ((e = launch_pdl(bucket_sort, dim3(kRadix), dim3(kBucketThreads), kBucketSmem, st, ld,
+                      static_cast<const uint32_t*>(a.tmp_keys), static_cast<const uint32_t*>(a.tmp_vals),
+                      static_cast<const uint2*>(runs), spill_k, spill_v, a.out_keys, a.out_vals,
+                      static_cast<const uint32_t*>(ctl), a.n, a.fence, a.fshift, next, a.defer_err)) != cudaSuccess)
     return e;
   ws.flip ^= 1;
   return cudaSuccess;
@@ -1093,10 +1120,11 @@ cudaError_t multi_sort_launch(const MultiArena& ar, const MultiBatch& in, cudaSt
 // process whose memory is handed out by its own pool allocator and forbids
 // raw cudaMalloc, or a latency-bound loop that cannot afford the implicit
 // device-wide synchronisation and the unbounded time a cudaMalloc/cudaFree
-// may take.  For them the sort below takes all of its scratch (ping-pong
-// buffers, histograms, look-back words) from one fixed array with static
-// storage in this file, which every GPU that loads the library holds until
-// the process exits.  Its size is set by kNoAllocMaxPairs.
+// may take.  For them the sort below takes all of its scratch (the
+// bucket sort's tile scratch, control words, run table and spill area) from
+// one fixed array with static storage in this file, which every GPU that
+// loads the library holds until the process exits.  Its size is set by
+// kNoAllocMaxPairs.
 // ---------------------------------------------------------------------------
 #include <mutex>
 
@@ -1106,19 +1134,19 @@ namespace gpulsm {
 namespace {
 
 constexpr uint32_t kNoAllocMaxPairs = LSM_SORT_NOALLOC_MAX_PAIRS;
-constexpr uint32_t kNoAllocTiles = (kNoAllocMaxPairs + kSortTile - 1) / kSortTile;
+// Up to kMsdMaxN pairs the sort is the two-kernel bucket sort, which needs
+// no look-back words; the array below holds only what that path uses.
+static_assert(kNoAllocMaxPairs <= kMsdMaxN, "the allocation-free sort stays on the bucket path");
 constexpr size_t kNoAllocCtl = 2112;                    // > 2 * kSortCtlWords, multiple of 64
-constexpr size_t kNoAllocSticky = kNoAllocCtl - 1;      // last ctl word: wait timeouts
+constexpr size_t kNoAllocSticky = kNoAllocCtl - 1;      // last ctl word: device error bits
 constexpr size_t kNoAllocTmpK = kNoAllocCtl;
 constexpr size_t kNoAllocTmpV = kNoAllocTmpK + kNoAllocMaxPairs;
-constexpr size_t kNoAllocLookback = kNoAllocTmpV + kNoAllocMaxPairs;   // u64 words from here
-constexpr size_t kNoAllocLookbackWords = size_t(kSortPasses) * kNoAllocTiles * 256;
-constexpr size_t kNoAllocTileCnt = kNoAllocLookback + 2 * kNoAllocLookbackWords;
-constexpr size_t kNoAllocWords = kNoAllocTileCnt + kMsdTileWords;
-static_assert(kNoAllocCtl > 2 * size_t(kSortCtlWords), "both control halves and the sticky word fit");
-static_assert(kNoAllocLookback % 2 == 0, "look-back words 8-byte aligned");
+constexpr size_t kNoAllocRuns = kNoAllocTmpV + kNoAllocMaxPairs;  // run table + spill area
+constexpr size_t kNoAllocWords = kNoAllocRuns + kMsdWsWords;
+static_assert(kNoAllocCtl > 2 * size_t(kSortCtlWords), "both control halves and the error word fit");
+static_assert(kNoAllocRuns % 2 == 0, "the run table holds 8-byte entries");
 
-// The scratch itself: about 11 MB for kNoAllocMaxPairs = 2^20.
+// The scratch itself: about 17 MB for kNoAllocMaxPairs = 2^20.
 static __device__ __align__(256) uint32_t g_sort_scratch[kNoAllocWords];
 
 constexpr int kNoAllocMaxDevices = 64;
@@ -1150,24 +1178,24 @@ extern "C" lsm_status lsm_sort_pairs_noalloc(const uint32_t* d_keys_in, const ui
   if (!d.base) {
     // Once per device, with that device current: the host needs the array's
     // device address (its name in host code is only a host-side stand-in),
-    // and the look-back words must start at zero.
+    // and the control words must start at zero.
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
       return LSM_ERR_CUDA;
     }
     uint32_t* base = static_cast<uint32_t*>(p);
-    if (cudaMemsetAsync(base, 0, kNoAllocWords * sizeof(uint32_t), st) != cudaSuccess) {
+    if (cudaMemsetAsync(base, 0, kNoAllocCtl * sizeof(uint32_t), st) != cudaSuccess) {
       cudaGetLastError();
       return LSM_ERR_CUDA;
     }
     d.ws.ctl = base;
-    d.ws.lookback = reinterpret_cast<uint64_t*>(base + kNoAllocLookback);
-    d.ws.max_tiles = kNoAllocTiles;
+    d.ws.lookback = nullptr;
+    d.ws.max_tiles = 0;
     d.ws.epoch = 0;
     d.ws.flip = 0;
     d.ws.sticky = base + kNoAllocSticky;
-    d.ws.tilecnt = base + kNoAllocTileCnt;
+    d.ws.tilecnt = base + kNoAllocRuns;
     d.base = base;
   }
   SortArgs a{};
@@ -1180,8 +1208,9 @@ extern "C" lsm_status lsm_sort_pairs_noalloc(const uint32_t* d_keys_in, const ui
   a.out_vals = d_vals_out;
   a.tmp_keys = d.base + kNoAllocTmpK;
   a.tmp_vals = d.base + kNoAllocTmpV;
-  // Each sort leaves the control block of the next one zeroed and tags its
-  // look-back words with a per-call epoch, so nothing else needs zeroing.
+  // Each sort leaves the control block of the next one zeroed; the run table
+  // and the tile scratch are fully rewritten by every call before they are
+  // read, so nothing else needs zeroing.
   cudaError_t e = sort_launch(a, d.ws, st, nullptr, nullptr);
   if (e != cudaSuccess) {
     cudaGetLastError();

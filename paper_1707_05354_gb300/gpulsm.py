@@ -29,7 +29,7 @@ STATUS = {0: "LSM_OK", 1: "LSM_ERR_ARG", 2: "LSM_ERR_KEY_RANGE", 3: "LSM_ERR_FUL
           5: "LSM_ERR_BUDGET", 6: "LSM_ERR_CAPACITY", 7: "LSM_ERR_CUDA", 8: "LSM_ERR_TIMEOUT"}
 LSM_OK, LSM_ERR_ARG, LSM_ERR_KEY_RANGE, LSM_ERR_FULL = 0, 1, 2, 3
 LSM_ERR_OOM, LSM_ERR_BUDGET, LSM_ERR_CAPACITY, LSM_ERR_CUDA, LSM_ERR_TIMEOUT = 4, 5, 6, 7, 8
-LSM_OPT_LOOKUP_MODE, LSM_OPT_DEVICE_ERROR, LSM_OPT_KERNEL_LAUNCHES = 1, 2, 3
+LSM_OPT_LOOKUP_MODE, LSM_OPT_DEVICE_ERROR, LSM_OPT_KERNEL_LAUNCHES, LSM_OPT_KEY_CHECK = 1, 2, 3, 4
 LOOKUP_AUTO, LOOKUP_DIRECT, LOOKUP_SORTED = 0, 1, 2
 LSM_MULTI_OPT_GRAPH, LSM_MULTI_OPT_GRAPH_KERNELS, LSM_MULTI_OPT_DEVICE_BYTES = 1, 2, 3
 REQ_INSERT, REQ_DELETE, REQ_LOOKUP, REQ_COUNT, REQ_RANGE = 0, 1, 2, 3, 4
@@ -106,6 +106,8 @@ _SIGS = {
     "lsm_profile": ([_vp, _i32], _i32),
     "lsm_profile_read": ([_vp, ctypes.POINTER(ProfileEntry)], _i32),
     "lsm_sort_pairs_noalloc": ([_vp, _vp, _vp, _vp, _u64, _vp], _i32),
+    "lsm_debug_fail_allocs": ([_u64, _u64], _i32),
+    "lsm_debug_wait_flag": ([_vp, _vp, _u64, _vp], _i32),
     "lsm_multi_create": ([ctypes.POINTER(_vp), _u32, _vp, _u32, _vp, _i32], _i32),
     "lsm_multi_destroy": ([_vp], None),
     "lsm_multi_update": ([_vp, _vp, _vp, _vp, _vp, _vp], _i32),
@@ -252,6 +254,22 @@ def lsm_sort_pairs_noalloc(d_kin, d_vin, d_kout, d_vout, n, stream=None):
     n > SORT_NOALLOC_MAX_PAIRS."""
     return _check(_lib.lsm_sort_pairs_noalloc(d_kin, d_vin, d_kout, d_vout, n, stream),
                   "lsm_sort_pairs_noalloc")
+
+
+def lsm_debug_fail_allocs(skip, count):
+    """Fault injection: after `skip` more library allocations succeed, the
+    next `count` fail (the calls needing them return LSM_ERR_OOM); (0, 0)
+    disarms."""
+    return _check(_lib.lsm_debug_fail_allocs(skip, count), "lsm_debug_fail_allocs")
+
+
+def lsm_debug_wait_flag(d_flag, d_status, limit_ns, stream=None):
+    """Fault injection: a bounded device wait on *d_flag != 0; returns the
+    status code (LSM_OK or LSM_ERR_TIMEOUT) instead of raising."""
+    s = _lib.lsm_debug_wait_flag(d_flag, d_status, limit_ns, stream)
+    if s not in (LSM_OK, LSM_ERR_TIMEOUT):
+        raise LSMError(s, "lsm_debug_wait_flag")
+    return s
 
 
 def lsm_reset(h):

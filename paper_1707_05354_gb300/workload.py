@@ -187,6 +187,51 @@ def sweep_width(expected_result, n_estimate, key_space=SWEEP_KEY_SPACE):
     return max(1, int(round(expected_result * key_space / max(1, n_estimate))))
 
 
+def sweep_device_seed(b_log2, delete_frac):
+    """Seed of the device-drawn sweep point (b = 2^b_log2, delete fraction)."""
+    return 1707053503 + b_log2 * 10 + int(delete_frac * 4)
+
+
+def sweep_batches_device(torch, dev, b, nb, frac, dist, seed):
+    """The sweep recipe drawn on the device (the inputs bench.py times): keys
+    uniform in [0, 2^30) or Zipf(1.1) over ranks 1 .. 2^30 (inverse transform
+    of the continuous power law, ranks mapped to keys by rank * 0x9E3779B1 mod
+    2^30); batch 0 all inserts, later batches round(frac * b) deletes of keys
+    drawn uniformly from the earlier inserts, shuffled among the inserts."""
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    space = 1 << 30
+    keys = torch.empty(nb * b, dtype=torch.int64, device=dev)
+    dele = torch.zeros(nb * b, dtype=torch.uint8, device=dev)
+    vals = torch.randint(0, 1 << 31, (nb * b,), device=dev, dtype=torch.int64, generator=gen).to(torch.int32)
+    inserted = torch.empty(nb * b, dtype=torch.int64, device=dev)
+    n_ins_total = 0
+    for t in range(nb):
+        n_del = 0 if t == 0 else int(round(b * frac))
+        n_ins = b - n_del
+        if dist == "zipf":
+            u = torch.rand(n_ins, device=dev, dtype=torch.float64, generator=gen)
+            a = 1.0 - 1.1
+            rank = torch.floor(((float(space) ** a - 1.0) * u + 1.0) ** (1.0 / a)).clamp_(1, space).to(torch.int64)
+            ins = (rank * 0x9E3779B1) % space
+        else:
+            ins = torch.randint(0, space, (n_ins,), device=dev, dtype=torch.int64, generator=gen)
+        if n_del:
+            idx = torch.randint(0, n_ins_total, (n_del,), device=dev, dtype=torch.int64, generator=gen)
+            batch = torch.cat([ins, inserted[idx]])
+            flags = torch.cat([torch.zeros(n_ins, dtype=torch.uint8, device=dev),
+                               torch.ones(n_del, dtype=torch.uint8, device=dev)])
+            perm = torch.randperm(b, device=dev, generator=gen)
+            batch, flags = batch[perm], flags[perm]
+        else:
+            batch, flags = ins, torch.zeros(b, dtype=torch.uint8, device=dev)
+        keys[t * b:(t + 1) * b] = batch
+        dele[t * b:(t + 1) * b] = flags
+        inserted[n_ins_total:n_ins_total + n_ins] = ins
+        n_ins_total += n_ins
+    return keys.to(torch.int32), vals, dele
+
+
 # --------------------------------------------------------------------------
 # Configuration "batched": many dictionaries with uneven batch sizes.
 # --------------------------------------------------------------------------

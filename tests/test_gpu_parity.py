@@ -107,15 +107,20 @@ def test_sort_pairs_matches_stable_sort(g, n):
     np.testing.assert_array_equal(u32(vo), vals[order])
 
 
-@pytest.mark.parametrize("dist", ["dup4", "sub_bin_skew", "one_bucket_spread"])
+@pytest.mark.parametrize("dist", ["dup4", "sub_bin_skew", "one_bucket_spread", "hot_key"])
 def test_sort_pairs_key_distributions(g, dist):
     """Stability and order for the bucket sort's paths: keys that repeat
     about 4 times each (ties inside the counting pass's sub-bins), buckets
-    whose keys crowd a few sub-bins (the pass-by-pass path), and every key in
-    one top-byte bucket of at most 5120 elements spread over its low bits."""
+    whose keys crowd a few sub-bins (the pass-by-pass path), every key in
+    one top-byte bucket of at most 5120 elements spread over its low bits,
+    and one key holding 40 % of the input beside uniform keys (its bucket,
+    far above shared memory, is sorted through the spill area)."""
     n = 1 << 20
     rng = np.random.default_rng(7)
-    if dist == "dup4":
+    if dist == "hot_key":
+        keys = rng.integers(0, 2**32, size=n, dtype=np.uint64).astype(np.uint32)
+        keys[rng.random(n) < 0.4] = np.uint32(0x9E3779B1)
+    elif dist == "dup4":
         keys = (rng.integers(0, 1 << 18, size=n).astype(np.uint64) * np.uint64(16411) % np.uint64(1 << 32))
         keys = keys.astype(np.uint32)
     elif dist == "sub_bin_skew":

@@ -6,7 +6,9 @@ or a latency-bound loop that cannot wait on cudaMalloc/cudaFree.  It takes
 its scratch from a fixed array inside the library instead of a handle.  Here
 it must give the same output as lsm_sort_pairs (integer keys: bit for bit)
 on two calls in a row, which also shows that the shared array carries nothing
-over from one call to the next, and it must refuse sizes above its limit.
+over from one call to the next; its output must equal numpy's stable sort;
+a call after the first one on a device must leave the device's free memory
+unchanged; and it must refuse sizes above its limit.
 
 Kept in a file of its own, named to be collected after every other test.
 """
@@ -53,8 +55,30 @@ def test_noalloc_sort_matches_handle_sort_on_two_calls(g):
         torch.cuda.synchronize()
         np.testing.assert_array_equal(_u32(out_k), _u32(ref_k))
         np.testing.assert_array_equal(_u32(out_v), _u32(ref_v))
-        assert np.all(np.diff(_u32(out_k).astype(np.int64)) >= 0)
+        order = np.argsort(keys, kind="stable")
+        np.testing.assert_array_equal(_u32(out_k), keys[order])
+        np.testing.assert_array_equal(_u32(out_v), vals[order])
     lsm.close()
+
+
+def test_noalloc_sort_allocates_no_device_memory(g):
+    """After a first call on the device (which looks up the array's address),
+    further calls leave the device's free memory exactly where it was."""
+    stream = torch.cuda.current_stream().cuda_stream
+    n = 1 << 20
+    rng = np.random.default_rng(99)
+    keys = rng.integers(0, 2**32, size=n, dtype=np.uint64).astype(np.uint32)
+    kd, vd = _dev(keys), _dev(np.arange(n, dtype=np.uint32))
+    out_k, out_v = torch.empty_like(kd), torch.empty_like(vd)
+    g.lsm_sort_pairs_noalloc(kd.data_ptr(), vd.data_ptr(), out_k.data_ptr(), out_v.data_ptr(), n, stream)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        g.lsm_sort_pairs_noalloc(kd.data_ptr(), vd.data_ptr(), out_k.data_ptr(), out_v.data_ptr(), n, stream)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    np.testing.assert_array_equal(_u32(out_k), np.sort(keys))
 
 
 def test_noalloc_sort_refuses_sizes_above_its_limit(g):
