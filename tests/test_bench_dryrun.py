@@ -59,8 +59,9 @@ def fake_library(real):
         return 0
 
     for name in ("lsm_set_option", "lsm_reset", "lsm_insert_batch", "lsm_stream_wait", "lsm_lookup",
-                 "lsm_count", "lsm_cleanup", "lsm_profile", "lsm_destroy"):
+                 "lsm_count", "lsm_cleanup", "lsm_profile", "lsm_destroy", "lsm_bulk_build"):
         setattr(g, name, launch)
+    g.lsm_stats = lambda h: dict(r=1, resident=1, b=1, levels=1)
     g.lsm_create = lambda b, n, dev=0: 1
     g.lsm_range = lambda h, k1, k2, nq, off, rk, rv, cap, s=None: (real.LSM_OK, min(cap, 8 * nq))
     g.lsm_get_option = lambda h, opt: 0

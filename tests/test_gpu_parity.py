@@ -278,6 +278,57 @@ def test_wide_count_range_queries(g):
     assert lsm.device_errors() == 0
 
 
+# ------------------------------------------------------ deferred key check --
+@pytest.mark.parametrize("b", [64, 5000])
+def test_deferred_key_check(g, b):
+    """LSM_OPT_KEY_CHECK = 1: update calls do not wait for the key check; a
+    batch holding a bad key is applied as b placebo tombstones (key 2^31 - 1,
+    which no query sees): the levels equal the oracle's for the same log with
+    that batch replaced by b deletes of key 2^31 - 1, every query answers as
+    if the batch had never been issued, the device error word records the bad
+    key, and cleanup drops the placebos."""
+    rng = np.random.default_rng(b)
+    calls = workload.sweep_updates(1707053511, b, 9 * b, 0.25, "uniform")
+    lsm = g.LSM(b, 16 * b)
+    g.lsm_set_option(lsm.h, g.LSM_OPT_KEY_CHECK, 1)
+    assert g.lsm_get_option(lsm.h, g.LSM_OPT_KEY_CHECK) == 1
+    s = oracle.StructuralOracle(b)
+    o1 = oracle.MapOracle(b)
+    placebo = np.full(b, (1 << 31) - 1, np.uint32)
+    for i, c in enumerate(calls):
+        if i in (3, 6):
+            kind, keys, vals, dele = c
+            keys = keys.copy()
+            keys[rng.integers(0, len(keys))] = np.uint32(2**31 + 5 if i == 3 else 2**32 - 1)
+            lsm.call(kind, keys, vals, dele)          # returns at once, no error
+            s.call("delete", placebo)                 # what the batch becomes
+            continue
+        lsm.call(*c)
+        s.call(*c)
+        o1.call(*c)
+    assert lsm.r == len(calls)
+    assert_levels(lsm, s)
+    ins = np.concatenate([c[1][c[3] == 0] for c in calls])
+    q = np.concatenate([workload.lookup_queries(5, ins, 2048, workload.SWEEP_KEY_SPACE),
+                        np.array([(1 << 31) - 1, 2**31 + 5], np.uint32)])
+    k1 = rng.integers(0, workload.SWEEP_KEY_SPACE, size=1024).astype(np.uint32)
+    k2 = (k1 + rng.integers(0, 1 << 22, size=1024)).astype(np.uint32)
+    k1[:2], k2[:2] = 0, 2**32 - 1
+    assert_queries(lsm, o1, q, k1, k2)
+    assert lsm.device_errors() & 1                   # the bad keys were recorded
+    lsm.cleanup()
+    s.cleanup()
+    assert_levels(lsm, s)
+    assert_queries(lsm, o1, q, k1, k2)
+    # back to the synchronous check: the same bad batch is refused
+    g.lsm_set_option(lsm.h, g.LSM_OPT_KEY_CHECK, 0)
+    r = lsm.r
+    with pytest.raises(g.LSMError) as e:
+        lsm.insert(np.array([1, 2**31], np.uint32), np.array([1, 2], np.uint32))
+    assert e.value.status == g.LSM_ERR_KEY_RANGE and lsm.r == r
+    assert lsm.device_errors() == 0
+
+
 # ------------------------------------------------------------------- edges --
 def test_edges(g):
     b = 64
