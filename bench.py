@@ -48,6 +48,8 @@ def parse_args():
     p.add_argument("--lookups-log2", type=int, default=24)
     p.add_argument("--queries-log2", type=int, default=22)
     p.add_argument("--lookup-mode", type=int, default=0, help="0 auto, 1 direct, 2 sorted")
+    p.add_argument("--key-check", default="sync", choices=["sync", "deferred"],
+                   help="paper/sweep: update calls wait for the key check (sync) or not (deferred)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default="paper", choices=["paper", "batched", "serving", "sweep"],
@@ -81,7 +83,7 @@ def paper_config(args, world):
                         "(half hits), 2^%d count + 2^%d range queries (expected 8 results), cleanup"
                         % (args.b_log2, nb, int(np.log2(nb * b)), args.lookups_log2, args.queries_log2,
                            args.queries_log2),
-            "b": b, "batches": nb, "lookup_mode": args.lookup_mode,
+            "b": b, "batches": nb, "lookup_mode": args.lookup_mode, "key_check": args.key_check,
             "l2": "inputs larger than L2 (1 GiB of updates per step), no flush",
             "parallelism": "replicas" if world > 1 else "single GPU"}
 
@@ -282,6 +284,7 @@ def run_gpu(args):
 
     h = G.lsm_create(b, n_upd, local)
     G.lsm_set_option(h, G.LSM_OPT_LOOKUP_MODE, args.lookup_mode)
+    G.lsm_set_option(h, G.LSM_OPT_KEY_CHECK, 1 if args.key_check == "deferred" else 0)
     kp, vp = d_keys.data_ptr(), d_vals.data_ptr()
     phases = ("update", "lookup", "count", "range", "cleanup")
 
@@ -934,6 +937,7 @@ def run_sweep(args):
                 keys, vals, dele = workload.sweep_batches_device(torch, dev, b, nb, frac, dist,
                                                                  workload.sweep_device_seed(bl, frac))
                 h = G.lsm_create(b, total, local)
+                G.lsm_set_option(h, G.LSM_OPT_KEY_CHECK, 1 if args.key_check == "deferred" else 0)
                 kp, vp, dp = keys.data_ptr(), vals.data_ptr(), dele.data_ptr()
 
                 def updates():
@@ -1017,7 +1021,7 @@ def run_sweep(args):
                 "config": {"workload": "update/delete sweep: b = 2^%s, 2^%d updates per point, delete fraction "
                                        "0/25/50%%, uniform or Zipf(1.1) keys; 2^22 count and range queries at "
                                        "expected sizes 8/64/512; cleanup" % (args.sweep_b, args.sweep_total_log2),
-                           "l2": "inputs larger than L2", "parallelism": "single GPU"},
+                           "key_check": args.key_check, "l2": "inputs larger than L2", "parallelism": "single GPU"},
                 "points": points, "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None}
         print(json.dumps(line), flush=True)
     return 0
