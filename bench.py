@@ -798,10 +798,17 @@ def run_batched(args):
 SERVING_METRIC = "serving: M keys/s and p50/p99 request latency (mixed stream, 64 GB HBM budget)"
 
 
-def latency_stats(out, arrival):
+def latency_stats(out, arrival, kind=None):
+    """p50 / p99 / mean / max latency; with `kind`, the same for the update
+    requests (insert, delete) and the retrievals (lookup, count, range)."""
     lat = (out["done_us"] - arrival) / 1000.0
-    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "max_ms": float(lat.max())}
+    st = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+          "mean_ms": float(lat.mean()), "max_ms": float(lat.max())}
+    if kind is not None:
+        for name, sel in (("updates", kind <= 1), ("retrievals", kind >= 2)):
+            if sel.any():
+                st[name] = {"p50_ms": float(np.percentile(lat[sel], 50)), "p99_ms": float(np.percentile(lat[sel], 99))}
+    return st
 
 
 def run_serving(args):
@@ -862,7 +869,7 @@ def run_serving(args):
                 clocks = sampler.stop()
             st1 = srv.stats()
             wall_s = out["wall_us"] / 1e6
-            res[name] = dict(latency=latency_stats(out, t_arr), requests_per_s=len(t_kind) / wall_s,
+            res[name] = dict(latency=latency_stats(out, t_arr, t_kind), requests_per_s=len(t_kind) / wall_s,
                              M_keys_per_s=t_keys / wall_s / 1e6, wall_s=wall_s,
                              arrivals_s=float(t_arr[-1]) / 1e6,
                              update_batches=int(out["update_batches"]), padded_ops=int(out["padded_ops"]),

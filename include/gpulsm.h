@@ -490,8 +490,9 @@ lsm_status lsm_multi_get_option(const lsm_multi_t* h, int opt, int64_t* value);
  * groups still run:
  *   - an update group is whole update requests, up to b ops, applied as one
  *     ordered batch (lsm_update_batch_ordered), admitted when b ops are
- *     pending, when its oldest request has waited flush_us, or at the end of
- *     the trace (a short batch is padded);
+ *     pending, when b/2 are pending and no update group is in flight, when
+ *     its oldest request has waited flush_us, or at the end of the trace (a
+ *     short batch is padded);
  *   - a retrieval group is every pending lookup / count / range request up
  *     to group_keys keys, admitted as soon as a slot is free.
  * Requests are linearised in admission order: each sees exactly the updates

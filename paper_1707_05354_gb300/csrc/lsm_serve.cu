@@ -288,10 +288,22 @@ struct Run {
   int pending_ranges = 0;         // range groups awaiting their totals (no update admitted meanwhile)
   uint64_t range_pos = 0;         // next free entry of the caller's range output
 
-  // The update queue is ready for a group (ignoring range groups in flight).
+  // Update groups admitted and not yet completed.
+  int updates_in_flight() const {
+    int c = 0;
+    for (const Group& g : inflight) c += g.update ? 1 : 0;
+    return c;
+  }
+
+  // The update queue is ready for a group (ignoring range groups in flight):
+  // a full batch, the end of the trace, a request that has waited flush_us,
+  // or -- continuous batching -- half a batch while no update group is on
+  // the device (the device would otherwise idle on updates until the batch
+  // fills or times out).
   bool updates_ready(double now) const {
     if (upd.empty()) return false;
     if (upd_ops >= s->cfg.b || next >= t->n) return true;
+    if (s->cfg.policy == LSM_SERVE_CONTINUOUS && 2 * upd_ops >= s->cfg.b && updates_in_flight() == 0) return true;
     return now - t->arrival_us[upd.front()] >= s->cfg.flush_us;
   }
   bool want_updates(double now) const { return pending_ranges == 0 && updates_ready(now); }

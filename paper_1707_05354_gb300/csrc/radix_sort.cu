@@ -466,12 +466,18 @@ struct ContigSrc {
   __device__ __forceinline__ uint32_t at(uint32_t i) const { return start + i; }
 };
 struct RunSrc {
-  const uint32_t* rstart;
+  const uint32_t* rstart;  // nruns + 1 entries, rstart[nruns] = the bucket's size
   const uint32_t* rbase;
-  uint32_t nruns;  // >= 1
+  const uint8_t* chunk;    // run holding element 16 c, per 16-element chunk c (buckets in shared memory), or null
+  uint32_t nruns;          // >= 1
   // the largest t with rstart[t] <= i: the run holding i (empty runs share
   // their start with the next run, so they are never the largest)
   __device__ __forceinline__ uint32_t at(uint32_t i) const {
+    if (chunk) {  // from the run of the chunk's first element, forward (runs of ~16 elements)
+      uint32_t t = chunk[i >> 4];
+      while (rstart[t + 1] <= i) ++t;
+      return rbase[t] + i;
+    }
     uint32_t lo = 0, hi = nruns - 1;
     while (lo < hi) {
       const uint32_t mid = (lo + hi + 1) >> 1;
@@ -480,6 +486,7 @@ struct RunSrc {
     return rbase[lo] + i;
   }
 };
+static_assert(kMsdMaxTiles <= 256u, "a run index fits in a byte");
 
 // One bucket, one CTA of kBucketThreads: sorts the m elements src.at(0 ..
 // m - 1) of (src_k, src_v) stably by the low `rest` bits of the key variable
@@ -594,7 +601,20 @@ __device__ __forceinline__ void bucket_body(const uint32_t* src_k, const uint32_
         }
       }
       __syncthreads();
-      bucket_write(ak, av, m, out_k, out_v, start, pad, pad_kv, pad_v, fence, fshift, bin0, nbins);
+      // The prefix-index entries come from the sub-bin starts when a bin is
+      // a whole number of sub-bins (fshift >= sh): entry bin0 + j is the
+      // start of sub-bin j << (fshift - sh), after the padding run when the
+      // bin lies above the padding's bin.
+      const bool direct_fence = fence && fshift >= sh;
+      bucket_write(ak, av, m, out_k, out_v, start, pad, pad_kv, pad_v, direct_fence ? nullptr : fence, fshift, bin0,
+                   nbins);
+      if (direct_fence) {
+        const uint32_t pad_bin = pad ? fence_bin(pad_kv, fshift) : 0xFFFFFFFFu;
+        for (uint32_t j = tid; j < nbins; j += kBucketThreads) {
+          const uint32_t sb = j << (fshift - sh);
+          fence[bin0 + j] = start + (sb < kSubBins ? cnt[sb] : m) + (bin0 + j > pad_bin ? pad : 0u);
+        }
+      }
       return;
     }
     __syncthreads();  // skewed bucket: the pass-by-pass path below reloads it
@@ -752,7 +772,8 @@ __global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort(Loader ld, cons
                                                               uint32_t* defer_err) {
   extern __shared__ __align__(16) uint32_t bsm[];
   __shared__ uint32_t s_scan[kBucketWarps];
-  __shared__ uint32_t s_rstart[kMsdMaxTiles], s_rbase[kMsdMaxTiles];
+  __shared__ uint32_t s_rstart[kMsdMaxTiles + 1], s_rbase[kMsdMaxTiles];
+  __shared__ uint8_t s_chunk[kBucketCap / 16];
   pdl_trigger();
   pdl_wait();
   const uint32_t tid = threadIdx.x, d = blockIdx.x;
@@ -788,8 +809,12 @@ __global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort(Loader ld, cons
   if (tid < ntiles) {
     s_rstart[tid] = rs;
     s_rbase[tid] = run.x - rs;
+    // the chunks (16 elements) whose first element lies in this run
+    if (m <= kBucketCap)
+      for (uint32_t c = (rs + 15) >> 4; c < ((rs + run.y + 15) >> 4); ++c) s_chunk[c] = uint8_t(tid);
   }
-  const uint32_t start = bucket_start<kBucketThreads>(ctl, d, s_scan);  // its barriers publish the table
+  if (tid == 0) s_rstart[ntiles] = m;
+  const uint32_t start = bucket_start<kBucketThreads>(ctl, d, s_scan);  // its barriers publish the tables
   // a short batch's padding: one run in the bucket of its key variable
   uint32_t pad = ld.npad(), pad_kv = 0, pad_v = 0;
   if (pad) {
@@ -798,7 +823,7 @@ __global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort(Loader ld, cons
     if ((pad_kv >> 24) != d) pad = 0;
   }
   const uint32_t per = fence ? 1u << (24 - fshift) : 0u;  // bins per bucket
-  const RunSrc src{s_rstart, s_rbase, ntiles};
+  const RunSrc src{s_rstart, s_rbase, m <= kBucketCap ? s_chunk : nullptr, ntiles};
   bucket_body(tmp_k, tmp_v, src, spill_k, spill_v, out_k, out_v, start, m, 24, fence, fshift, d * per, per, bsm,
               s_scan, pad, pad_kv, pad_v);
   // the bucket sort writes every entry: the populated range is all bins
