@@ -233,6 +233,30 @@ lsm_status lsm_level_offset(const lsm_t* h, uint32_t i, uint64_t* offset, uint64
 lsm_status lsm_dump_levels(const lsm_t* h, uint32_t* h_keys, uint32_t* h_vals, void* stream);
 
 /*
+ * Checkpoint and resume (not in the paper; the state of a dictionary is its
+ * batch size b, its batch count r and its full levels, §III-B).
+ *
+ * lsm_save - write the full levels, in ascending level order, to host
+ * memory: level i (bit i of r set) as b * 2^i key variables ((key << 1) |
+ * status, §IV-A) and as many values, one level after another.  h_keys and
+ * h_vals hold `capacity` elements; the call needs r * b of them (else
+ * LSM_ERR_CAPACITY, nothing written) and stores r in *r_out.  Synchronises
+ * with `stream` after the folds in flight.
+ *
+ * lsm_load - make an empty handle (r = 0) hold a saved state: r and the
+ * r * b elements written by lsm_save of a dictionary with the same b.  The
+ * handle needs the levels of r (else LSM_ERR_FULL); every level is copied
+ * to the device and its prefix index rebuilt.  b mismatch or r = 0 with
+ * data: LSM_ERR_ARG.  The arrays are trusted to come from lsm_save (sorted
+ * levels); the call does not re-sort them.  Asynchronous on `stream`: the
+ * host arrays must stay valid until the stream has passed the call.
+ */
+lsm_status lsm_save(lsm_t* h, uint32_t* h_keys, uint32_t* h_vals, uint64_t capacity, uint64_t* r_out,
+                    void* stream);
+lsm_status lsm_load(lsm_t* h, const uint32_t* h_keys, const uint32_t* h_vals, uint64_t r, uint32_t b,
+                    void* stream);
+
+/*
  * lsm_reset - drop every element (r = 0).  Host-side only, no device work; the
  * level memory is reused by later batches (after any fold still in flight,
  * which the handle's stream order guarantees).  Waits for nothing.

@@ -157,7 +157,7 @@ __device__ __forceinline__ uint32_t corank_lane(bool act, const uint32_t* a, con
     const uint32_t Pj = P << csj;
     // an entry inside the populated range is always loaded, then selected
     const uint32_t v = __ldg(fj + (Pj <= bminj ? bminj : (Pj > bmaxj ? bmaxj : Pj)));
-    return Pj <= bminj ? 0u : (Pj > bmaxj ? nj : v);
+    return Pj <= bminj ? 0u : (Pj > bmaxj ? nj : min(v, nj));
   });
   int bs = fc;  // shift of the bin found
   // 2. The bin's elements: [blo, bhi) of each source, need = p - C(bin) of

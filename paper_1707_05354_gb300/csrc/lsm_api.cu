@@ -919,6 +919,49 @@ lsm_status lsm_dump_levels(const lsm_t* h, uint32_t* h_keys, uint32_t* h_vals, v
   return cuda_status(cudaStreamSynchronize(st));
 }
 
+lsm_status lsm_save(lsm_t* h, uint32_t* h_keys, uint32_t* h_vals, uint64_t capacity, uint64_t* r_out,
+                    void* stream) {
+  if (!h || !r_out || (h->r && (!h_keys || !h_vals))) return LSM_ERR_ARG;
+  if (h->r * h->b > capacity) return LSM_ERR_CAPACITY;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  LSM_TRY(join_side(h, st));
+  uint64_t pos = 0;
+  for (uint32_t i = 0; i < h->L; ++i) {
+    if (!((h->r >> i) & 1u)) continue;
+    const uint64_t n = uint64_t(h->b) << i;
+    LSM_TRY(cudaMemcpyAsync(h_keys + pos, level_keys(h, int(i)), n * 4, cudaMemcpyDeviceToHost, st));
+    LSM_TRY(cudaMemcpyAsync(h_vals + pos, level_vals(h, int(i)), n * 4, cudaMemcpyDeviceToHost, st));
+    pos += n;
+  }
+  LSM_TRY(cudaStreamSynchronize(st));
+  *r_out = h->r;
+  return LSM_OK;
+}
+
+lsm_status lsm_load(lsm_t* h, const uint32_t* h_keys, const uint32_t* h_vals, uint64_t r, uint32_t b,
+                    void* stream) {
+  if (!h || b != h->b || h->r != 0 || (r && (!h_keys || !h_vals))) return LSM_ERR_ARG;
+  if (r == 0) return LSM_OK;
+  if (r >> h->L) return LSM_ERR_FULL;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  LSM_TRY(join_side(h, st));
+  h->l0_buf = -1;  // every level lives in the level array
+  uint64_t pos = 0;
+  for (uint32_t i = 0; i < h->L; ++i) {
+    if (!((r >> i) & 1u)) continue;
+    const uint64_t n = uint64_t(h->b) << i;
+    LSM_TRY(cudaMemcpyAsync(h->d_keys + h->level_off[i], h_keys + pos, n * 4, cudaMemcpyHostToDevice, st));
+    LSM_TRY(cudaMemcpyAsync(h->d_vals + h->level_off[i], h_vals + pos, n * 4, cudaMemcpyHostToDevice, st));
+    LSM_TRY(build_fence_launch(h->d_keys + h->level_off[i], uint32_t(n), h->d_fence + h->fence_off[i], h->fshift[i],
+                               st));
+    pos += n;
+  }
+  h->r = r;
+  return LSM_OK;
+}
+
 lsm_status lsm_sort_pairs(lsm_t* h, const uint32_t* d_keys_in, const uint32_t* d_vals_in, uint32_t* d_keys_out,
                           uint32_t* d_vals_out, uint64_t n, void* stream) {
   if (!h || n > h->b || (n && (!d_keys_in || !d_vals_in || !d_keys_out || !d_vals_out))) return LSM_ERR_ARG;

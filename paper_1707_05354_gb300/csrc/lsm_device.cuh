@@ -72,11 +72,13 @@ __device__ __forceinline__ uint32_t upper_bound_key(const uint32_t* __restrict__
 // only inside its populated bin range: the two words after entry nbins hold
 // bmin and bmax, the bins of the first and last element; below (and at)
 // bmin the answer is 0, above bmax it is n.
+// The answer is kept within [0, n], so that a search bounded by it stays
+// inside the run even if the table were damaged.
 __device__ __forceinline__ uint32_t fence_at(const uint32_t* f, int fshift, uint32_t n, uint32_t P) {
   const uint32_t nb = fence_bins(fshift);
   if (P <= __ldg(f + nb + 2)) return 0u;
   if (P > __ldg(f + nb + 3)) return n;
-  return __ldg(f + P);
+  return min(__ldg(f + P), n);
 }
 
 // Writing a prefix index from consecutive elements: the element at position

@@ -10,21 +10,27 @@
 //                    ordered batch (lsm_update_batch_ordered: the last op
 //                    on a key decides, so coalescing requests keeps the
 //                    meaning of applying them one after another); admitted
-//                    when b ops are pending, when its oldest request has
+//                    when b ops are pending, when b/2 are pending and no
+//                    update group is in flight, when its oldest request has
 //                    waited flush_us, or when no more requests will arrive.
 //   retrieval group  every pending retrieval up to group_keys keys, admitted
 //                    as soon as a slot is free: one lookup, one count and one
 //                    range launch for all of them.
-// All groups run in admission order on one stream (the dictionary's folds
-// on its own stream, joined by every retrieval), so a request sees exactly
-// the updates admitted before its group: requests are linearised in
-// admission order.  A request only waits with others that were pending at
-// the same time, so the order respects real time.  The work of several
-// groups overlaps on the device (a fold with the next batch's sort, copies
-// with kernels); the host keeps admitting while the device works, bounded by
-// the slots.  Range groups take two steps (counts and offsets, then the
-// emit once the host knows the total); no update group is admitted between
-// them, so the emit reads the state the counts saw.
+// Update groups run in admission order on the server's stream (the
+// dictionary's folds on its own stream); each retrieval group runs on its
+// slot's stream after an event that follows every update group admitted
+// before it, and beside the other retrieval groups; an update group first
+// waits for the retrieval groups in flight, whose levels its fold or a
+// cleanup may rewrite.  So a request sees exactly the updates admitted
+// before its group: requests are linearised in admission order.  A request
+// only waits with others that were pending at the same time, so the order
+// respects real time.  Groups complete in any order.  The work of several
+// groups overlaps on the device (retrieval groups with each other, a fold
+// with the next batch's sort, copies with kernels); the host keeps admitting
+// while the device works, bounded by the slots.  Range groups take two steps
+// (counts and offsets, then the emit once the host knows the total); no
+// update group is admitted between them, so the emit reads the state the
+// counts saw.
 //
 // Device memory is admitted against a budget: the dictionary's levels and
 // cleanup scratch, its batch scratch, and every slot's buffers (payload
@@ -113,6 +119,7 @@ struct Slot {
   uint64_t* h_roff = nullptr;
   uint32_t *h_rk = nullptr, *h_rv = nullptr;
   uint64_t* h_total = nullptr;
+  cudaStream_t st = nullptr;  // the slot's retrieval groups (update groups use the server's stream)
   cudaEvent_t ev_done = nullptr, ev_total = nullptr, ev_start = nullptr;
   cudaEvent_t ev_ph[6] = {};  // retrieval phases: after gathers+sorts ... before the emit
   // sorting the queries of a large group (by key, with their positions):
@@ -151,7 +158,8 @@ struct Group {
 struct lsm_server_t {
   lsm_server_config cfg{};
   lsm_t* dict = nullptr;
-  cudaStream_t st = nullptr;
+  cudaStream_t st = nullptr;  // update groups (and cleanups)
+  cudaEvent_t ev_applied = nullptr;  // after the latest admitted update group's sort and fold
   uint32_t L = 0;             // dictionary levels
   uint32_t max_levels = 0;    // bound on full levels (bounds scratch)
   uint32_t max_req = 0;       // descriptors per group
@@ -204,6 +212,7 @@ void free_slot(Slot& s) {
                s.h_total};
   for (void* p : h)
     if (p) cudaFreeHost(p);
+  if (s.st) cudaStreamDestroy(s.st);
   if (s.ev_done) cudaEventDestroy(s.ev_done);
   if (s.ev_total) cudaEventDestroy(s.ev_total);
   if (s.ev_start) cudaEventDestroy(s.ev_start);
@@ -253,6 +262,7 @@ cudaError_t alloc_slot(Slot& s, const lsm_server_config& c, uint32_t max_levels,
   if (e == cudaSuccess) e = halloc(&s.h_rv, R);
   if (e == cudaSuccess) e = halloc(&s.h_total, 8);
   if (e == cudaSuccess) e = cudaMemset(s.ctr, 0, 64);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreate(&s.ev_done);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_total, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreate(&s.ev_start);
@@ -339,6 +349,10 @@ struct Run {
     }
     upd_ops -= ops;
     if (g.reqs.empty()) return LSM_ERR_ARG;  // cannot happen: sizes are <= b
+    // retrieval groups still reading the levels finish before this group's
+    // sort and fold (and a cleanup) may rewrite level memory
+    for (const Group& o : inflight)
+      if (!o.update) LSM_TRY(cudaStreamWaitEvent(s->st, s->slots[o.slot].ev_done, 0));
     // budget: a full dictionary is cleaned first; refused if still full
     const uint32_t L = dict_L(s->dict);
     uint64_t r = dict_r(s->dict);
@@ -369,6 +383,7 @@ struct Run {
                                    sl.ud, s->st));
       LSM_TRY_S(dict_update_ordered(s->dict, sl.uk, sl.uv, sl.ud, n, s->st, false));
       LSM_TRY(dict_record_applied(s->dict, sl.ev_done, s->st));
+      LSM_TRY(dict_record_applied(s->dict, s->ev_applied, s->st));
       res->update_batches += 1;
       res->padded_ops += s->cfg.b - n;
     }
@@ -379,6 +394,7 @@ struct Run {
 
   lsm_status admit_retrievals(int slot_id) {
     Slot& sl = s->slots[slot_id];
+    cudaStream_t rs = sl.st;
     Group g;
     g.update = false;
     g.slot = slot_id;
@@ -410,73 +426,76 @@ struct Run {
       pos = e;
     }
     const uint32_t nd = uint32_t(g.reqs.size());
-    LSM_TRY(cudaEventRecord(sl.ev_start, s->st));
-    LSM_TRY(cudaMemcpyAsync(sl.d_start, sl.h_start, 8ull * nd, cudaMemcpyHostToDevice, s->st));
-    LSM_TRY(cudaMemcpyAsync(sl.d_dst, sl.h_dst, 8ull * nd, cudaMemcpyHostToDevice, s->st));
-    LSM_TRY(dict_join(s->dict, s->st));
+    LSM_TRY(cudaEventRecord(sl.ev_start, rs));
+    LSM_TRY(cudaMemcpyAsync(sl.d_start, sl.h_start, 8ull * nd, cudaMemcpyHostToDevice, rs));
+    LSM_TRY(cudaMemcpyAsync(sl.d_dst, sl.h_dst, 8ull * nd, cudaMemcpyHostToDevice, rs));
+    // the group sees every update group admitted before it (their sorts
+    // and folds), and runs beside other retrieval groups
+    LSM_TRY(cudaStreamWaitEvent(rs, s->ev_applied, 0));
+    LSM_TRY(dict_join(s->dict, rs));
     g.ls = dict_levels(s->dict);
     const LevelSet& ls = g.ls;
-    LSM_TRY(cudaEventRecord(sl.ev_ph[0], s->st));
+    LSM_TRY(cudaEventRecord(sl.ev_ph[0], rs));
     if (g.look.count) {
       const uint32_t f = g.look.first;
       LSM_TRY(gather_windows_launch(s->pool_a, nullptr, sl.d_start + f, sl.d_dst + f, g.look.count, g.look.keys,
-                                    sl.q, nullptr, s->st));
+                                    sl.q, nullptr, rs));
       lsm_status err = LSM_OK;
       if (ls.count && sort_queries(sl, sl.sa, sl.q, g.look.keys, err)) {
-        LSM_TRY(lookup_sorted_launch(ls, sl.sa[0], sl.sa[1], g.look.keys, sl.val, sl.found, s->st));
+        LSM_TRY(lookup_sorted_launch(ls, sl.sa[0], sl.sa[1], g.look.keys, sl.val, sl.found, rs));
       } else if (err != LSM_OK) {
         return err;
       } else if (ls.count) {
-        LSM_TRY(lookup_launch(ls, sl.q, g.look.keys, sl.val, sl.found, s->st));
+        LSM_TRY(lookup_launch(ls, sl.q, g.look.keys, sl.val, sl.found, rs));
       } else {
-        LSM_TRY(cudaMemsetAsync(sl.val, 0, 4 * g.look.keys, s->st));
-        LSM_TRY(cudaMemsetAsync(sl.found, 0, g.look.keys, s->st));
+        LSM_TRY(cudaMemsetAsync(sl.val, 0, 4 * g.look.keys, rs));
+        LSM_TRY(cudaMemsetAsync(sl.found, 0, g.look.keys, rs));
       }
-      LSM_TRY(cudaMemcpyAsync(sl.h_val, sl.val, 4 * g.look.keys, cudaMemcpyDeviceToHost, s->st));
-      LSM_TRY(cudaMemcpyAsync(sl.h_found, sl.found, g.look.keys, cudaMemcpyDeviceToHost, s->st));
+      LSM_TRY(cudaMemcpyAsync(sl.h_val, sl.val, 4 * g.look.keys, cudaMemcpyDeviceToHost, rs));
+      LSM_TRY(cudaMemcpyAsync(sl.h_found, sl.found, g.look.keys, cudaMemcpyDeviceToHost, rs));
     }
-    LSM_TRY(cudaEventRecord(sl.ev_ph[1], s->st));
+    LSM_TRY(cudaEventRecord(sl.ev_ph[1], rs));
     if (g.count.count) {
       const uint32_t f = g.count.first;
       LSM_TRY(gather_windows_launch(s->pool_a, s->pool_c, sl.d_start + f, sl.d_dst + f, g.count.count,
-                                    g.count.keys, sl.c1, sl.c2, s->st));
+                                    g.count.keys, sl.c1, sl.c2, rs));
       lsm_status err = LSM_OK;
       if (ls.count && sort_queries(sl, sl.sa, sl.c1, g.count.keys, err))
-        LSM_TRY(count_launch(ls, sl.sa[0], sl.c2, g.count.keys, sl.cnt, nullptr, s->st, sl.sa[1]));
+        LSM_TRY(count_launch(ls, sl.sa[0], sl.c2, g.count.keys, sl.cnt, nullptr, rs, sl.sa[1]));
       else if (err != LSM_OK)
         return err;
       else if (ls.count)
-        LSM_TRY(count_launch(ls, sl.c1, sl.c2, g.count.keys, sl.cnt, nullptr, s->st));
+        LSM_TRY(count_launch(ls, sl.c1, sl.c2, g.count.keys, sl.cnt, nullptr, rs));
       else
-        LSM_TRY(cudaMemsetAsync(sl.cnt, 0, 4 * g.count.keys, s->st));
-      LSM_TRY(cudaMemcpyAsync(sl.h_cnt, sl.cnt, 4 * g.count.keys, cudaMemcpyDeviceToHost, s->st));
+        LSM_TRY(cudaMemsetAsync(sl.cnt, 0, 4 * g.count.keys, rs));
+      LSM_TRY(cudaMemcpyAsync(sl.h_cnt, sl.cnt, 4 * g.count.keys, cudaMemcpyDeviceToHost, rs));
     }
-    LSM_TRY(cudaEventRecord(sl.ev_ph[2], s->st));
+    LSM_TRY(cudaEventRecord(sl.ev_ph[2], rs));
     if (g.range.count) {
       const uint32_t f = g.range.first;
       const uint64_t nr = g.range.keys;
       LSM_TRY(gather_windows_launch(s->pool_a, s->pool_c, sl.d_start + f, sl.d_dst + f, g.range.count,
-                                    g.range.keys, sl.r1, sl.r2, s->st));
+                                    g.range.keys, sl.r1, sl.r2, rs));
       if (ls.count) {
         lsm_status err = LSM_OK;
         g.range_sorted = sort_queries(sl, sl.sb, sl.r1, nr, err);
         if (err != LSM_OK) return err;
         if (g.range_sorted)
-          LSM_TRY(count_launch(ls, sl.sb[0], sl.r2, nr, sl.rcnt, sl.bounds, s->st, sl.sb[1]));
+          LSM_TRY(count_launch(ls, sl.sb[0], sl.r2, nr, sl.rcnt, sl.bounds, rs, sl.sb[1]));
         else
-          LSM_TRY(count_launch(ls, sl.r1, sl.r2, nr, sl.rcnt, sl.bounds, s->st));
-        LSM_TRY(scan_launch(sl.rcnt, nr, sl.roff, sl.lb, sl.ctr, dict_status_word(s->dict), s->st));
+          LSM_TRY(count_launch(ls, sl.r1, sl.r2, nr, sl.rcnt, sl.bounds, rs));
+        LSM_TRY(scan_launch(sl.rcnt, nr, sl.roff, sl.lb, sl.ctr, dict_status_word(s->dict), rs));
       } else {
-        LSM_TRY(cudaMemsetAsync(sl.roff, 0, 8 * (nr + 1), s->st));
+        LSM_TRY(cudaMemsetAsync(sl.roff, 0, 8 * (nr + 1), rs));
       }
-      LSM_TRY(cudaEventRecord(sl.ev_ph[3], s->st));
-      LSM_TRY(cudaMemcpyAsync(sl.h_total, sl.roff + nr, 8, cudaMemcpyDeviceToHost, s->st));
-      LSM_TRY(cudaEventRecord(sl.ev_total, s->st));
+      LSM_TRY(cudaEventRecord(sl.ev_ph[3], rs));
+      LSM_TRY(cudaMemcpyAsync(sl.h_total, sl.roff + nr, 8, cudaMemcpyDeviceToHost, rs));
+      LSM_TRY(cudaEventRecord(sl.ev_total, rs));
       g.stage = kRangePending;
       pending_ranges += 1;
     } else {
-      LSM_TRY(cudaEventRecord(sl.ev_ph[3], s->st));
-      LSM_TRY(cudaEventRecord(sl.ev_done, s->st));
+      LSM_TRY(cudaEventRecord(sl.ev_ph[3], rs));
+      LSM_TRY(cudaEventRecord(sl.ev_done, rs));
       g.stage = kRunning;
     }
     res->retrieval_groups += 1;
@@ -487,6 +506,7 @@ struct Run {
   // Sorts n query keys with their positions into set[0] (keys) / set[1]
   // (positions), when the group is large enough to profit.
   bool sort_queries(Slot& sl, uint32_t* const* set, const uint32_t* keys, uint64_t n, lsm_status& err) {
+    cudaStream_t rs = sl.st;
     if (n < kSortQueriesFrom || n > kMsdMaxN) return false;
     SortArgs a{};
     a.mode = kSortQueries;
@@ -498,7 +518,7 @@ struct Run {
     a.tmp_keys = set[2];
     a.tmp_vals = set[3];
     sl.sws.sticky = dict_status_word(s->dict);
-    err = cuda_status(sort_launch(a, sl.sws, s->st, nullptr, nullptr));
+    err = cuda_status(sort_launch(a, sl.sws, rs, nullptr, nullptr));
     return err == LSM_OK;
   }
 
@@ -506,6 +526,7 @@ struct Run {
   // the counts: no update group was admitted in between).
   lsm_status finish_range(Group& g) {
     Slot& sl = s->slots[g.slot];
+    cudaStream_t rs = sl.st;
     const uint64_t nr = g.range.keys;
     const uint64_t total = *sl.h_total;
     g.range_total = total;
@@ -513,8 +534,8 @@ struct Run {
     if (total > s->cfg.range_cap) {
       // rare: more results than the slot holds; buffers for this group only
       LSM_TRY(alloc_gate());
-      LSM_TRY(cudaMallocAsync(reinterpret_cast<void**>(&g.big_k), 4 * total, s->st));
-      LSM_TRY(cudaMallocAsync(reinterpret_cast<void**>(&g.big_v), 4 * total, s->st));
+      LSM_TRY(cudaMallocAsync(reinterpret_cast<void**>(&g.big_k), 4 * total, rs));
+      LSM_TRY(cudaMallocAsync(reinterpret_cast<void**>(&g.big_v), 4 * total, rs));
       LSM_TRY(cudaHostAlloc(reinterpret_cast<void**>(&g.h_big_k), 4 * total, cudaHostAllocDefault));
       LSM_TRY(cudaHostAlloc(reinterpret_cast<void**>(&g.h_big_v), 4 * total, cudaHostAllocDefault));
       dk = g.big_k;
@@ -522,21 +543,21 @@ struct Run {
       hk = g.h_big_k;
       hv = g.h_big_v;
     }
-    LSM_TRY(cudaEventRecord(sl.ev_ph[4], s->st));
+    LSM_TRY(cudaEventRecord(sl.ev_ph[4], rs));
     if (total && g.ls.count)
-      LSM_TRY(range_emit_launch(g.ls, nr, sl.bounds, sl.roff, dk, dv, s->st, g.range_sorted ? sl.sb[1] : nullptr));
-    LSM_TRY(cudaEventRecord(sl.ev_ph[5], s->st));
-    LSM_TRY(cudaMemcpyAsync(sl.h_roff, sl.roff, 8 * (nr + 1), cudaMemcpyDeviceToHost, s->st));
+      LSM_TRY(range_emit_launch(g.ls, nr, sl.bounds, sl.roff, dk, dv, rs, g.range_sorted ? sl.sb[1] : nullptr));
+    LSM_TRY(cudaEventRecord(sl.ev_ph[5], rs));
+    LSM_TRY(cudaMemcpyAsync(sl.h_roff, sl.roff, 8 * (nr + 1), cudaMemcpyDeviceToHost, rs));
     if (total) {
-      LSM_TRY(cudaMemcpyAsync(hk, dk, 4 * total, cudaMemcpyDeviceToHost, s->st));
-      LSM_TRY(cudaMemcpyAsync(hv, dv, 4 * total, cudaMemcpyDeviceToHost, s->st));
+      LSM_TRY(cudaMemcpyAsync(hk, dk, 4 * total, cudaMemcpyDeviceToHost, rs));
+      LSM_TRY(cudaMemcpyAsync(hv, dv, 4 * total, cudaMemcpyDeviceToHost, rs));
     }
     if (g.big_k) {
-      LSM_TRY(cudaFreeAsync(g.big_k, s->st));
-      LSM_TRY(cudaFreeAsync(g.big_v, s->st));
+      LSM_TRY(cudaFreeAsync(g.big_k, rs));
+      LSM_TRY(cudaFreeAsync(g.big_v, rs));
       g.big_k = g.big_v = nullptr;
     }
-    LSM_TRY(cudaEventRecord(sl.ev_done, s->st));
+    LSM_TRY(cudaEventRecord(sl.ev_done, rs));
     g.stage = kRunning;
     pending_ranges -= 1;
     return LSM_OK;
@@ -611,27 +632,35 @@ struct Run {
   }
 
   lsm_status poll(double now) {
-    // groups complete in admission order (one stream)
+    // range groups whose totals arrived get their emit (in admission order:
+    // no update group is admitted while one waits)
     for (size_t j = 0; j < inflight.size(); ++j) {
       Group& g = inflight[j];
       Slot& sl = s->slots[g.slot];
       if (g.stage == kRangePending) {
         const cudaError_t e = cudaEventQuery(sl.ev_total);
-        if (e == cudaErrorNotReady) break;
+        if (e == cudaErrorNotReady) continue;
         LSM_TRY(e);
         const double f0 = now_us(t0);
         LSM_TRY_S(finish_range(g));
         res->host_range_us += now_us(t0) - f0;
       }
     }
-    while (!inflight.empty()) {
-      Group& g = inflight.front();
-      if (g.stage != kRunning) break;
+    // groups on different streams complete in any order
+    for (size_t j = 0; j < inflight.size();) {
+      Group& g = inflight[j];
+      if (g.stage != kRunning) {
+        ++j;
+        continue;
+      }
       const cudaError_t e = cudaEventQuery(s->slots[g.slot].ev_done);
-      if (e == cudaErrorNotReady) break;
+      if (e == cudaErrorNotReady) {
+        ++j;
+        continue;
+      }
       LSM_TRY(e);
       complete(g, now);
-      inflight.erase(inflight.begin());
+      inflight.erase(inflight.begin() + long(j));
     }
     return LSM_OK;
   }
@@ -689,6 +718,7 @@ struct Run {
   lsm_status drain_all() {
     while (!inflight.empty()) {
       LSM_TRY(cudaStreamSynchronize(s->st));
+      for (const Slot& sl : s->slots) LSM_TRY(cudaStreamSynchronize(sl.st));
       LSM_TRY_S(poll(now_us(t0)));
     }
     return LSM_OK;
@@ -756,6 +786,7 @@ lsm_status lsm_server_create(lsm_server_t** out, const lsm_server_config* cfg) {
     return st;
   }
   cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_applied, cudaEventDisableTiming);
   s->slots.resize(nslots);
   for (uint32_t i = 0; i < nslots && e == cudaSuccess; ++i) e = alloc_slot(s->slots[i], *cfg, L, s->max_req);
   if (e != cudaSuccess) {
@@ -772,6 +803,7 @@ void lsm_server_destroy(lsm_server_t* s) {
   cudaDeviceSynchronize();
   for (Slot& sl : s->slots) free_slot(sl);
   if (s->st) cudaStreamDestroy(s->st);
+  if (s->ev_applied) cudaEventDestroy(s->ev_applied);
   if (s->dict) lsm_destroy(s->dict);
   delete s;
 }

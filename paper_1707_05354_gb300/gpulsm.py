@@ -107,6 +107,8 @@ _SIGS = {
     "lsm_profile_read": ([_vp, ctypes.POINTER(ProfileEntry)], _i32),
     "lsm_sort_pairs_noalloc": ([_vp, _vp, _vp, _vp, _u64, _vp], _i32),
     "lsm_debug_fail_allocs": ([_u64, _u64], _i32),
+    "lsm_save": ([_vp, _vp, _vp, _u64, _vp, _vp], _i32),
+    "lsm_load": ([_vp, _vp, _vp, _u64, _u32, _vp], _i32),
     "lsm_debug_wait_flag": ([_vp, _vp, _u64, _vp], _i32),
     "lsm_multi_create": ([ctypes.POINTER(_vp), _u32, _vp, _u32, _vp, _i32], _i32),
     "lsm_multi_destroy": ([_vp], None),
@@ -569,6 +571,29 @@ class LSM:
                 off, size = lsm_level_offset(self.h, i)
                 out[i] = (hk[off:off + size].copy(), hv[off:off + size].copy())
         return out
+
+    def save(self):
+        """Checkpoint: (r, key variables, values) of the full levels in
+        ascending level order, as host uint32 arrays (lsm_save)."""
+        import numpy as np
+        st = self.stats()
+        n = st["r"] * st["b"]
+        hk = np.empty(max(1, n), np.uint32)
+        hv = np.empty(max(1, n), np.uint32)
+        r = _u64()
+        _check(_lib.lsm_save(self.h, hk.ctypes.data, hv.ctypes.data, n, ctypes.byref(r), _stream(self.device)),
+               "lsm_save")
+        return r.value, hk[:n], hv[:n]
+
+    def load(self, r, keys, vals, b=None):
+        """Resume from a checkpoint (lsm_load) of a dictionary with batch size
+        b (default: this handle's; another b is refused)."""
+        import numpy as np
+        hk = np.ascontiguousarray(keys, dtype=np.uint32)
+        hv = np.ascontiguousarray(vals, dtype=np.uint32)
+        _check(_lib.lsm_load(self.h, hk.ctypes.data, hv.ctypes.data, r, self.b if b is None else b,
+                             _stream(self.device)), "lsm_load")
+        _torch().cuda.synchronize(self.device)   # the host arrays may be freed after the call returns
 
     def set_lookup_mode(self, mode):
         lsm_set_option(self.h, LSM_OPT_LOOKUP_MODE, mode)

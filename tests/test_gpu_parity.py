@@ -278,6 +278,54 @@ def test_wide_count_range_queries(g):
     assert lsm.device_errors() == 0
 
 
+# ------------------------------------------------------ checkpoint / resume --
+@pytest.mark.parametrize("b,ncalls", [(100, 13), (4096, 11)])
+def test_checkpoint_resume(g, b, ncalls):
+    """lsm_save / lsm_load: a dictionary restored from a checkpoint into a
+    fresh handle (same b, more room) has the same levels bit for bit and
+    answers like the oracle; further batches and a cleanup on both the
+    original and the restored one keep them identical."""
+    calls = workload.sweep_updates(1707053521, b, ncalls * b, 0.25, "uniform")
+    lsm = g.LSM(b, 16 * b)
+    s = oracle.StructuralOracle(b)
+    o1 = oracle.MapOracle(b)
+    for c in calls[:-2]:
+        lsm.call(*c)
+        s.call(*c)
+        o1.call(*c)
+    r, hk, hv = lsm.save()
+    assert r == lsm.r and len(hk) == r * b
+    lsm2 = g.LSM(b, 40 * b)
+    lsm2.load(r, hk, hv)
+    assert lsm2.r == r
+    assert_levels(lsm2, s)
+    rng = np.random.default_rng(b)
+    ins = np.concatenate([c[1][c[3] == 0] for c in calls])
+    q = workload.lookup_queries(9, ins, 4096, workload.SWEEP_KEY_SPACE)
+    k1 = rng.integers(0, workload.SWEEP_KEY_SPACE, size=1024).astype(np.uint32)
+    k2 = (k1 + rng.integers(0, 1 << 24, size=1024)).astype(np.uint32)
+    assert_queries(lsm2, o1, q, k1, k2)
+    for c in calls[-2:]:
+        lsm.call(*c)
+        lsm2.call(*c)
+        s.call(*c)
+    assert_levels(lsm, s)
+    assert_levels(lsm2, s)
+    lsm2.cleanup()
+    s.cleanup()
+    assert_levels(lsm2, s)
+    # errors: a handle that is not empty, another b, too few levels
+    with pytest.raises(g.LSMError):
+        lsm2.load(r, hk, hv)
+    with pytest.raises(g.LSMError) as e:
+        g.LSM(b + 1, 40 * b).load(r, hk, hv, b=b)
+    assert e.value.status == g.LSM_ERR_ARG
+    with pytest.raises(g.LSMError) as e:
+        g.LSM(b, b).load(r, hk, hv)
+    assert e.value.status == g.LSM_ERR_FULL
+    assert lsm.device_errors() == 0 and lsm2.device_errors() == 0
+
+
 # ------------------------------------------------------ deferred key check --
 @pytest.mark.parametrize("b", [64, 5000])
 def test_deferred_key_check(g, b):
