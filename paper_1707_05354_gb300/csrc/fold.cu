@@ -332,19 +332,15 @@ __device__ __forceinline__ void merge_step(const uint32_t* __restrict__ sk, cons
     const uint32_t mid = (lo + hi) >> 1;
     if (key_of(keyA(mid)) <= key_of(sk[bS + q0 - 1 - mid])) lo = mid + 1; else hi = mid;
   }
+  // Branch-free walk: after every output both heads are reloaded from their
+  // cursors clamped to the runs' last elements, and a run past its end has
+  // the head key kSentinel.  A data-dependent branch on which run advanced
+  // would make every warp execute both sides (a warp's lanes take either).
   uint32_t ia = lo, ib = q0 - lo;
-  uint32_t va = 0, xa = 0, vb = 0, xb = 0;   // key variable and slot index of each head
-  uint32_t ka = kSentinel, kb = kSentinel;
-  if (ia < nA) {
-    va = keyA(ia);
-    xa = idxA(ia);
-    ka = key_of(va);
-  }
-  if (ib < nB) {
-    vb = sk[bS + ib];
-    xb = bS + ib;
-    kb = key_of(vb);
-  }
+  const uint32_t lastA = nA ? nA - 1u : 0u, lastB = nB ? nB - 1u : 0u;
+  uint32_t ja = ia < nA ? ia : lastA, jb = ib < nB ? ib : lastB;
+  uint32_t va = keyA(ja), xa = idxA(ja), vb = sk[bS + jb], xb = bS + jb;   // key variable, slot index
+  uint32_t ka = ia < nA ? key_of(va) : kSentinel, kb = ib < nB ? key_of(vb) : kSentinel;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     if ((kToRegs || uint32_t(e) < per) && q0 + e < m) {
@@ -356,23 +352,16 @@ __device__ __forceinline__ void merge_step(const uint32_t* __restrict__ sk, cons
         Yk[ksw(q0 + e)] = v;
         Yi[ksw(q0 + e)] = uint16_t(x);
       }
-      if (take_a) {
-        if (++ia < nA) {
-          va = keyA(ia);
-          xa = idxA(ia);
-          ka = key_of(va);
-        } else {
-          ka = kSentinel;
-        }
-      } else {
-        if (++ib < nB) {
-          vb = sk[bS + ib];
-          xb = bS + ib;
-          kb = key_of(vb);
-        } else {
-          kb = kSentinel;
-        }
-      }
+      ia += take_a ? 1u : 0u;
+      ib += take_a ? 0u : 1u;
+      ja = ia < nA ? ia : lastA;
+      jb = ib < nB ? ib : lastB;
+      va = keyA(ja);
+      xa = idxA(ja);
+      vb = sk[bS + jb];
+      xb = bS + jb;
+      ka = ia < nA ? key_of(va) : kSentinel;
+      kb = ib < nB ? key_of(vb) : kSentinel;
     }
   }
   if (kToRegs) {
@@ -387,146 +376,10 @@ struct MergeShared {
   uint32_t rstart[kMaxSources], rlen[kMaxSources];
   uint32_t a0[kMaxSources], span[kMaxSources], slot[kMaxSources];
   uint32_t scan[kThreads / 32], last[kThreads / 32];
-  uint32_t prev_mask, ok, ngap, landed;
-  uint32_t kmin, csh, crowded, prev0;  // counting merge: key offset, sub-bin shift, fallback flag
+  uint32_t prev_mask, ok, ngap, landed, prev0;
   FenceGap gaps[kFenceGapSlots];
   uint64_t prefix;
 };
-
-// Counting merge (tiles of kCountSources or more sources): O(1) work per
-// element instead of the chain's S - 1 merge steps with a merge-path search
-// each.  The tile's order is (key, slot index): the windows sit in the slots
-// in rank order, so among equal keys the slot index is the fold's order
-// (newer source first, then index).  Every element gets the composite
-//     c = ((key - kmin) << 12) | slot,
-// which is strictly increasing in that order, and the sub-bin c >> csh of
-// kTile sub-bins (csh the smallest shift mapping the tile's largest c below
-// kTile: about one element per sub-bin, equal keys spread by their slots
-// when the tile's key range is narrow).  The sub-bins are counted, scanned
-// and filled, and every element is ranked inside its sub-bin by (key, slot).
-// A tile with a sub-bin of more than kCrowded elements (many copies of one
-// key inside a wide key range) is merged by the chain instead.
-#ifndef LSM_COUNT_SOURCES
-#define LSM_COUNT_SOURCES 8
-#endif
-constexpr int kCountSources = LSM_COUNT_SOURCES;
-constexpr uint32_t kCrowded = 24;
-constexpr uint32_t kPadMark = 0xFFFFFFFFu;  // no element has it: key 2^31 - 1 is only ever a tombstone
-
-template <int E>
-__device__ __forceinline__ uint32_t count_sub(uint32_t key, uint32_t q, uint32_t kmin, uint32_t csh) {
-  const uint32_t d = key - kmin;
-  return csh >= 12u ? d >> (csh - 12u) : ((d << 12) | q) >> csh;
-}
-
-// Steps after the windows are staged (sk / sv), the pad slots marked and the
-// counters zeroed (Y[0, kTile)); on success out[] holds this thread's E
-// outputs (key variable, value).  Called by all threads; returns the same
-// verdict in all of them.
-template <int E>
-__device__ __forceinline__ bool count_merge(uint32_t* sk, const uint32_t* sv, uint32_t* Xk, uint16_t* Xi,
-                                            uint32_t* Y, MergeShared& sh, int S, uint32_t tile_n, uint2 (&out)[E]) {
-  using G = TileGeom<E>;
-  constexpr uint32_t kSub = G::kTile;
-  constexpr int kPer = int(kSub) / kThreads;                  // counters per thread
-  constexpr int kIters = int((G::kSlotCap + kThreads - 1) / kThreads);
-  static_assert(G::kSlotCap <= 4096u, "slot indices fit in the composite's 12 low bits");
-  static_assert(kSub <= 65536u, "sub-bin and slot-in-sub-bin pack into 32 bits");
-  uint32_t* cnt = Y;                                           // counts, then starts
-  uint16_t* oslot = reinterpret_cast<uint16_t*>(Y + kSub);     // slot of each output
-  uint32_t* okey = sk;                                         // key variable of each output (over the slots)
-  const uint32_t tid = threadIdx.x;
-  const uint32_t nslots = sh.slot[S - 1] + sh.span[S - 1];
-  const uint32_t kmin = sh.kmin, csh = sh.csh;
-  // 1. count: sub-bin and arrival slot of every element
-  uint32_t reg[kIters];
-#pragma unroll
-  for (int j = 0; j < kIters; ++j) {
-    const uint32_t q = tid + uint32_t(j) * kThreads;
-    reg[j] = 0xFFFFFFFFu;
-    if (q < nslots) {
-      const uint32_t kv = sk[q];
-      if (kv != kPadMark) {
-        const uint32_t sub = count_sub<E>(key_of(kv), q, kmin, csh);
-        reg[j] = (sub << 16) | atomicAdd(&cnt[sub], 1u);
-      }
-    }
-  }
-  __syncthreads();
-  // 2. starts of the sub-bins; a crowded tile leaves for the chain
-  uint32_t c[kPer], sum = 0, mx = 0;
-#pragma unroll
-  for (int e = 0; e < kPer; ++e) {
-    c[e] = cnt[tid * kPer + e];
-    sum += c[e];
-    mx = max(mx, c[e]);
-  }
-  if (mx > kCrowded) sh.crowded = 1u;
-  uint32_t all;
-  uint32_t run = block_excl_scan<kThreads>(sum, sh.scan, all);  // its barriers publish sh.crowded
-  if (sh.crowded) return false;
-#pragma unroll
-  for (int e = 0; e < kPer; ++e) {
-    cnt[tid * kPer + e] = run;
-    run += c[e];
-  }
-  __syncthreads();
-  // 3. place every element in its sub-bin
-#pragma unroll
-  for (int j = 0; j < kIters; ++j) {
-    if (reg[j] != 0xFFFFFFFFu) {
-      const uint32_t q = tid + uint32_t(j) * kThreads;
-      const uint32_t pos = cnt[reg[j] >> 16] + (reg[j] & 0xFFFFu);
-      Xk[pos] = sk[q];
-      Xi[pos] = uint16_t(q);
-    }
-  }
-  __syncthreads();
-  // 4. rank inside the sub-bin by (key, slot): the output position
-#pragma unroll 2
-  for (int j = 0; j < E; ++j) {
-    const uint32_t x = tid + uint32_t(j) * kThreads;
-    if (x < tile_n) {
-      const uint32_t kv = Xk[x], q = Xi[x], key = key_of(kv);
-      const uint32_t sub = count_sub<E>(key, q, kmin, csh);
-      const uint32_t s0 = cnt[sub], s1 = sub + 1 < kSub ? cnt[sub + 1] : tile_n;
-      uint32_t r = 0;
-      for (uint32_t y = s0; y < s1; ++y) {
-        const uint32_t ky = key_of(Xk[y]);
-        r += (ky < key || (ky == key && uint32_t(Xi[y]) < q)) ? 1u : 0u;
-      }
-      okey[s0 + r] = kv;
-      oslot[s0 + r] = uint16_t(q);
-    }
-  }
-  __syncthreads();
-  // 5. this thread's E consecutive outputs, their values gathered by slot
-  const uint32_t q0 = tid * E;
-  if (q0 < tile_n) {
-    uint32_t kk[E];
-    uint16_t ss[E];
-    if constexpr (E == 8) {  // 16-byte loads: no bank conflicts between the lanes
-      const uint4 a = *reinterpret_cast<const uint4*>(okey + q0);
-      const uint4 b = *reinterpret_cast<const uint4*>(okey + q0 + 4);
-      const uint4 t = *reinterpret_cast<const uint4*>(oslot + q0);
-      kk[0] = a.x; kk[1] = a.y; kk[2] = a.z; kk[3] = a.w;
-      kk[4] = b.x; kk[5] = b.y; kk[6] = b.z; kk[7] = b.w;
-      const uint32_t tw[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-      for (int e = 0; e < E; ++e) ss[e] = uint16_t(tw[e >> 1] >> (16 * (e & 1)));
-    } else {
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        kk[e] = okey[q0 + e];
-        ss[e] = oslot[q0 + e];
-      }
-    }
-#pragma unroll
-    for (int e = 0; e < E; ++e)
-      if (q0 + e < tile_n) out[e] = make_uint2(kk[e], sv[ss[e]]);
-  }
-  return true;
-}
 
 // From this many sources a tile stages its windows with 16-byte cp.async
 // copies from every thread rather than bulk copies (at b = 2^20 the k = 7
@@ -659,60 +512,24 @@ __device__ __forceinline__ bool merge_tile(const FoldSources& src, uint64_t tota
   }
 
   // The element before the tile (for thread 0): only its key (and so its
-  // bin) matters; a key variable with the largest key before the co-ranks.
-  // Warp 0 reads it (lane j: source j's element before its co-rank) before
-  // the counting merge marks the windows' pad slots.
-  const bool counting = S >= kCountSources;
+  // bin) matters; a key variable with the largest key before the co-ranks
+  // (lane j of warp 0 reads source j's element before its co-rank).
   if (warp == 0) {
     const bool has = lane < uint32_t(S) && ((sh.prev_mask >> lane) & 1u);
     uint32_t mx = has ? key_of(sk[sh.rstart[lane] - 1]) : 0u;
-    // the tile's key range (first and last element of every non-empty run)
-    const bool run = lane < uint32_t(S) && sh.rlen[lane] > 0;
-    uint32_t lo = run ? key_of(sk[sh.rstart[lane]]) : 0xFFFFFFFFu;
-    uint32_t hi = run ? key_of(sk[sh.rstart[lane] + sh.rlen[lane] - 1]) : 0u;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    }
-    if (counting) {
-      __syncwarp();
-      // pad slots of the windows (the element before the co-rank and the
-      // 16-byte alignment) hold no element of the tile
-      for (uint32_t i = lane; i < uint32_t(S) * 8u; i += 32u) {
-        const uint32_t r = i >> 3, p = i & 7u;
-        if (!sh.span[r]) continue;
-        const uint32_t pre = sh.rstart[r] - sh.slot[r];
-        const uint32_t end = sh.rstart[r] + sh.rlen[r];
-        const uint32_t post = sh.slot[r] + sh.span[r] - end;
-        if (p < pre) sk[sh.slot[r] + p] = kPadMark;
-        else if (p - pre < post) sk[end + (p - pre)] = kPadMark;
-      }
-    }
-    if (lane == 0) {
-      sh.prev0 = mx << 1;
-      const uint32_t klo = lo <= hi ? lo : 0u;
-      const uint64_t cmax = (uint64_t(hi - klo) << 12) | 4095u;
-      const int bits = 64 - __clzll(cmax);
-      constexpr int kSubLog = G::kTile == 2048u ? 11 : 10;
-      static_assert(G::kTile == 2048u || G::kTile == 1024u, "sub-bins of a 1024- or 2048-output tile");
-      sh.kmin = klo;
-      sh.csh = uint32_t(bits > kSubLog ? bits - kSubLog : 0);
-      sh.crowded = 0u;
-    }
-  }
-  uint32_t* Y0 = Yk;  // the Y chain buffer's region, where the counting merge keeps its counters
-  if (counting) {
-    for (uint32_t i = tid; i < G::kTile; i += kThreads) Y0[i] = 0u;
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) sh.prev0 = mx << 1;
   }
   __syncthreads();
   const uint32_t prev0 = sh.prev0;
 
+  // Left-deep merge order: X = run 0 + run 1, then X = X + run r for each
+  // further rank; the last step keeps its E outputs per thread in registers.
+  // Runs grow with their rank (the batch and level 0 are the smallest), so
+  // every element moves about twice in all.
   uint2 out[E];
-  if (counting && count_merge<E>(sk, sv, Xk, Xi, Y0, sh, S, tile_n, out)) {
-    // done: out[] holds this thread's outputs
-  } else if (S <= 2) {
+  if (S <= 2) {
     merge_step<E, true, true>(sk, sv, nullptr, nullptr, nullptr, nullptr, sh.rstart[0], sh.rlen[0],
                               S == 2 ? sh.rstart[1] : 0u, S == 2 ? sh.rlen[1] : 0u, out);
   } else {
