@@ -151,14 +151,46 @@ __device__ __forceinline__ uint32_t corank_lane(bool act, const uint32_t* a, con
   const uint32_t bminj = __shfl_sync(0xffffffffu, bmin, int(j)), bmaxj = __shfl_sync(0xffffffffu, bmax, int(j));
   const uint32_t nj = __shfl_sync(0xffffffffu, n, int(j));
   // 1. The bin at shift fc: largest P with C(P) <= p (C(0) = 0 <= p <
-  //    C(nbins) = total).
-  uint32_t bin = group_search(0u, 1u << (32 - fc), p, lg, [&](uint32_t P) -> uint32_t {
+  //    C(nbins) = total).  First a bracket of 2 delta bins around the
+  //    proportional guess over the sources' populated bin range (exact for
+  //    evenly spread keys), checked with one probe at each end; the search
+  //    runs inside it when it holds the answer, else over all bins.
+  auto coarse = [&](uint32_t P) -> uint32_t {
     if (!jact) return 0u;
     const uint32_t Pj = P << csj;
     // an entry inside the populated range is always loaded, then selected
     const uint32_t v = __ldg(fj + (Pj <= bminj ? bminj : (Pj > bmaxj ? bmaxj : Pj)));
     return Pj <= bminj ? 0u : (Pj > bmaxj ? nj : min(v, nj));
-  });
+  };
+  const uint32_t nbins = 1u << (32 - fc);
+  uint32_t rlo = act ? (bmin >> cs) : 0xFFFFFFFFu, rhi = act ? (bmax >> cs) : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rlo = min(rlo, __shfl_xor_sync(0xffffffffu, rlo, o));
+    rhi = max(rhi, __shfl_xor_sync(0xffffffffu, rhi, o));
+  }
+  const uint32_t guess = rlo + uint32_t((p * uint64_t(rhi - rlo + 1u)) / total);
+  const uint32_t delta = max(8u, nbins >> 7);
+  const uint32_t lo0 = guess > delta ? guess - delta : 0u;
+  const uint32_t hi0 = (nbins - guess) > delta ? guess + delta : nbins;
+  // C(lo0) by group 0 and C(hi0) by group 1 in one round (a warp of a
+  // single group, S > 16, takes two)
+  uint32_t c_lo = 0, c_hi = 0;
+  for (int e = 0; e < (lg < 5 ? 1 : 2); ++e) {
+    const uint32_t q = lg < 5 ? (lane >> lg) : uint32_t(e);
+    uint32_t c = q < 2 && (lg < 5 || e == int(q)) ? coarse(q ? hi0 : lo0) : 0u;
+    for (uint32_t o = (1u << lg) >> 1; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, int(o));
+    if (lg < 5) {
+      c_lo = __shfl_sync(0xffffffffu, c, 0);
+      c_hi = __shfl_sync(0xffffffffu, c, int(1u << lg));
+    } else if (e == 0) {
+      c_lo = __shfl_sync(0xffffffffu, c, 0);
+    } else {
+      c_hi = __shfl_sync(0xffffffffu, c, 0);
+    }
+  }
+  const bool inside = c_lo <= p && p < c_hi;
+  uint32_t bin = group_search(inside ? lo0 : 0u, inside ? hi0 : nbins, p, lg, coarse);
   int bs = fc;  // shift of the bin found
   // 2. The bin's elements: [blo, bhi) of each source, need = p - C(bin) of
   //    them precede p.
