@@ -629,16 +629,39 @@ __device__ __forceinline__ bool merge_tile(const FoldSources& src, uint64_t tota
       // Prefix index of the new level: the element at position pos owns the
       // entries between the previous element's bin and its own; the first and
       // last elements record the populated bin range instead of the edges.
+      // At about 8 elements per bin an output crosses one bin boundary or
+      // none, so every output writes at most the entry after the previous
+      // bin (one predicated store, no branch a warp would diverge on); a
+      // thread that met a wider gap (empty bins) writes the rest of its
+      // gaps afterwards.
       const uint32_t nb = fence_bins(fshift);
-      uint32_t pb = has_prev ? fence_bin(prev_kv, fshift) : 0u;
+      const uint32_t pb0 = has_prev ? fence_bin(prev_kv, fshift) : 0u;
+      uint32_t pb = pb0;
+      bool wide = false;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         if (uint32_t(e) < cnt) {
           const uint32_t bin = fence_bin(out[e].x, fshift);
-          const uint64_t pos = obase + q0 + e;
-          if (pos == 0) out_fence[nb + 2] = bin;
-          else if (bin > pb) fence_write_gap(out_fence, pb, bin, uint32_t(pos), sh.gaps, &sh.ngap);
+          const uint32_t pos = uint32_t(obase) + q0 + uint32_t(e);
+          const bool first = obase + q0 + e == 0;
+          if (first) out_fence[nb + 2] = bin;
+          if (!first && bin > pb) {
+            out_fence[pb + 1] = pos;
+            wide |= bin > pb + 1;
+          }
           pb = bin;
+        }
+      }
+      if (wide) {
+        uint32_t qb = pb0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          if (uint32_t(e) < cnt) {
+            const uint32_t bin = fence_bin(out[e].x, fshift);
+            const uint64_t pos = obase + q0 + e;
+            if (pos != 0 && bin > qb + 1) fence_write_gap(out_fence, qb + 1, bin, uint32_t(pos), sh.gaps, &sh.ngap);
+            qb = bin;
+          }
         }
       }
       if (cnt && obase + q0 + cnt == total) out_fence[nb + 3] = pb;
