@@ -58,11 +58,14 @@ struct Loader {
     }
     uint64_t s = uint64_t(n) - 1 - p;
     if (s >= n_in) s = n_in - 1;
+    // the key, delete flag and value loads are independent (insert and
+    // update calls always pass values), so they are in flight together
     const uint32_t k = __ldg(keys + s);
+    const uint32_t v0 = mode != kSortDelete ? __ldg(vals + s) : 0u;
     const bool is_del = (mode == kSortDelete) || (mode == kSortUpdate && __ldg(del + s) != 0);
     bad = k > kMaxUserKey;
     kv = bad ? kPlaceboKv : ((k << 1) | (is_del ? 0u : 1u));
-    v = (is_del || bad) ? 0u : __ldg(vals + s);
+    v = (is_del || bad) ? 0u : v0;
   }
 
   // Leading positions of the reversed padded batch that are padding (copies
@@ -591,8 +594,18 @@ __device__ __forceinline__ void bucket_body(const uint32_t* src_k, const uint32_
           const uint16_t ix = bi[x];
           const uint32_t b = (k >> sh) & (kSubBins - 1);
           const uint32_t s0 = cnt[b], s1 = b + 1 < kSubBins ? cnt[b + 1] : m;
+          // The first four members without a branch (a sub-bin rarely holds
+          // more for spread keys, and a loop made each warp run as long as
+          // its fullest sub-bin), then the rest.
           uint32_t r = 0;
-          for (uint32_t y = s0; y < s1; ++y) {
+#pragma unroll
+          for (uint32_t u = 0; u < 4; ++u) {
+            if (s0 + u < s1) {
+              const uint32_t ky = bk[s0 + u];
+              r += (ky < k || (ky == k && bi[s0 + u] < ix)) ? 1u : 0u;
+            }
+          }
+          for (uint32_t y = s0 + 4; y < s1; ++y) {
             const uint32_t ky = bk[y];
             r += (ky < k || (ky == k && bi[y] < ix)) ? 1u : 0u;
           }
