@@ -352,7 +352,8 @@ lsm_status lsm_get_option(lsm_t* h, lsm_option opt, int64_t* value);
  * group, the number of launches, their total device time and the ALGORITHMIC
  * bytes they had to move (the bytes an ideal implementation reads and writes
  * in HBM; scratch traffic excluded):
- *   LSM_PROF_SORT       batch sort (histogram + 4 passes), 16 B per element
+ *   LSM_PROF_SORT       batch sort (two kernels up to 2^20 elements, else a
+ *                       histogram and four passes), 16 B per element
  *   LSM_PROF_PARTITION  fold co-rank search, 0 B (pure overhead)
  *   LSM_PROF_MERGE      fold merge into level k, 16 * 2^k * b B
  *   LSM_PROF_LOOKUP     lookup kernels, 9 B per query + 32 B per level probed
@@ -361,9 +362,14 @@ lsm_status lsm_get_option(lsm_t* h, lsm_option opt, int64_t* value);
  *   LSM_PROF_EMIT       range output, 8 B per result + 8 B per query
  *   LSM_PROF_CLEANUP    cleanup merge + distribute, 8 B read per resident
  *                       element + 8 B written per element of r' * b
- * lsm_profile(h, 1) enables and zeroes the counters, lsm_profile(h, 0)
- * disables.  lsm_profile_read synchronises the device and fills `out`
- * (LSM_PROF_COUNT_ entries).  Profiling adds two event records per group.
+ * lsm_profile(h, 1) enables every group and zeroes the counters,
+ * lsm_profile(h, 2 + g) enables group g alone (and zeroes the counters),
+ * lsm_profile(h, 0) disables; any other value is LSM_ERR_ARG.
+ * lsm_profile_read synchronises the device and fills `out` (LSM_PROF_COUNT_
+ * entries).  Profiling adds two event records per launch of a profiled group;
+ * an event between two kernels also ends the programmatic launch overlap of
+ * the second with the first, so profiling one group (for instance the merge
+ * while an insert phase is timed) perturbs the timing less than profiling all.
  */
 typedef enum {
   LSM_PROF_SORT = 0,

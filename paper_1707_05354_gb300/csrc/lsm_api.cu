@@ -101,7 +101,7 @@ struct lsm_t {
   int lookup_mode = 0;
   bool key_check_deferred = false;  // LSM_OPT_KEY_CHECK
   // kernel profiler
-  bool prof = false;
+  uint32_t prof = 0;  // profiled groups: bit g for lsm_prof_group g
   struct ProfRec {
     int group;
     cudaEvent_t a, b;
@@ -194,10 +194,10 @@ struct ProfScope {
     return e;
   }
   ProfScope(lsm_t* h_, int g, double by, cudaStream_t s) : h(h_), group(g), bytes(by), st(s) {
-    if (h->prof && (a = get(h))) cudaEventRecord(a, st);
+    if (((h->prof >> group) & 1u) && (a = get(h))) cudaEventRecord(a, st);
   }
   ~ProfScope() {
-    if (!h->prof || !a) return;
+    if (!((h->prof >> group) & 1u) || !a) return;
     cudaEvent_t b = get(h);
     if (!b) return;
     cudaEventRecord(b, st);
@@ -873,7 +873,7 @@ lsm_status lsm_stream_wait(lsm_t* h, void* stream) {
 }
 
 lsm_status lsm_profile(lsm_t* h, int enable) {
-  if (!h) return LSM_ERR_ARG;
+  if (!h || enable < 0 || enable >= 2 + LSM_PROF_COUNT_) return LSM_ERR_ARG;
   DeviceGuard g(h->device);
   LSM_TRY(cudaDeviceSynchronize());
   for (auto& p : h->prof_pending) {
@@ -882,7 +882,7 @@ lsm_status lsm_profile(lsm_t* h, int enable) {
   }
   h->prof_pending.clear();
   memset(h->prof_acc, 0, sizeof(h->prof_acc));
-  h->prof = enable != 0;
+  h->prof = enable == 0 ? 0u : (enable == 1 ? (1u << LSM_PROF_COUNT_) - 1u : 1u << (enable - 2));
   return LSM_OK;
 }
 

@@ -283,7 +283,12 @@ def lsm_stream_wait(h, stream=None):
 
 
 def lsm_profile(h, enable):
-    return _check(_lib.lsm_profile(h, 1 if enable else 0), "lsm_profile")
+    """enable: False / True (every group), or one group's name (that group alone)."""
+    if isinstance(enable, str):
+        code = 2 + PROF_GROUPS.index(enable)
+    else:
+        code = 1 if enable else 0
+    return _check(_lib.lsm_profile(h, code), "lsm_profile")
 
 
 def lsm_profile_read(h):

@@ -612,3 +612,33 @@ def test_successor_predecessor(g, b, key_space, ncalls, cleanup):
         np.testing.assert_array_equal(u32(k), ek)
         np.testing.assert_array_equal(u32(v), ev)
     assert lsm.device_errors() == 0
+
+
+def test_profile_one_group(g):
+    """lsm_profile(h, 2 + group) brackets that group alone; 1 brackets every
+    group; out-of-range codes are refused.  The levels are the same either
+    way (profiling only adds events)."""
+    b = 4096
+    rng = np.random.default_rng(11)
+    batches = [(rng.integers(0, 1 << 20, size=b).astype(np.uint32),
+                rng.integers(0, 1 << 32, size=b, dtype=np.uint64).astype(np.uint32)) for _ in range(7)]
+    lsm = g.LSM(b, 8 * b)
+    g.lsm_profile(lsm.h, "merge")
+    for k, v in batches:
+        lsm.insert(k, v)
+    prof = g.lsm_profile_read(lsm.h)
+    assert prof["merge"]["launches"] == 3          # the batches at r = 1, 3, 5 fold (k = 1, 2, 1)
+    assert all(prof[n]["launches"] == 0 for n in g.PROF_GROUPS if n != "merge")
+    assert prof["merge"]["ms"] > 0
+    g.lsm_profile(lsm.h, True)
+    lsm.insert(*batches[0])
+    prof = g.lsm_profile_read(lsm.h)                # r = 7: a fold into level 3
+    assert [prof[n]["launches"] for n in ("sort", "partition", "merge")] == [1, 1, 1]
+    g.lsm_profile(lsm.h, False)
+    for bad in (-1, 2 + len(g.PROF_GROUPS)):
+        with pytest.raises(g.LSMError):
+            g._check(g._lib.lsm_profile(lsm.h, bad), "lsm_profile")
+    s = oracle.StructuralOracle(b)
+    for k, v in batches + [batches[0]]:
+        s.call("insert", k, v)
+    assert_levels(lsm, s)
