@@ -176,7 +176,10 @@ __device__ __forceinline__ uint32_t corank_lane(bool act, const uint32_t* a, con
     rhi = max(rhi, __shfl_xor_sync(0xffffffffu, rhi, o));
   }
   const uint32_t guess = rlo + uint32_t((p * uint64_t(rhi - rlo + 1u)) / total);
-  const uint32_t delta = max(8u, nbins >> 7);
+  // half-width 1/2048 of the bins: for evenly spread keys the guess is off by
+  // a few bins (the spread of a count is about its square root); a bracket
+  // that misses costs one round more than a full search
+  const uint32_t delta = max(8u, nbins >> 11);
   const uint32_t lo0 = guess > delta ? guess - delta : 0u;
   const uint32_t hi0 = (nbins - guess) > delta ? guess + delta : nbins;
   // C(lo0) by group 0 and C(hi0) by group 1 in one round (a warp of a
