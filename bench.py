@@ -509,9 +509,9 @@ def run_e2e(args, G, h, torch, dev, keys, vals, q, c1, c2, r1, r2, world):
     st = torch.cuda.current_stream(dev)
     cs = torch.cuda.Stream(dev)
     sp = st.cuda_stream
-    nbuf = 4  # device staging buffers: copies run up to three batches ahead of the inserts
-    buf = [(torch.empty(b, dtype=torch.int32, device=dev), torch.empty(b, dtype=torch.int32, device=dev))
-           for _ in range(nbuf)]
+    G4 = 4  # batches per copy: two device staging groups of four batches, one group ahead of the inserts
+    gbuf = [(torch.empty(G4 * b, dtype=torch.int32, device=dev), torch.empty(G4 * b, dtype=torch.int32, device=dev))
+            for _ in range(2)]
     dq = torch.empty(len(q), dtype=torch.int32, device=dev)
     dc1, dc2 = torch.empty_like(dq[:len(c1)]), torch.empty_like(dq[:len(c1)])
     dr1, dr2 = torch.empty_like(dq[:len(r1)]), torch.empty_like(dq[:len(r1)])
@@ -528,35 +528,40 @@ def run_e2e(args, G, h, torch, dev, keys, vals, q, c1, c2, r1, r2, world):
     h_off = torch.empty(len(r1) + 1, dtype=torch.int64).pin_memory()
     h_rk = torch.empty(cap, dtype=torch.int32).pin_memory()
     h_rv = torch.empty(cap, dtype=torch.int32).pin_memory()
-    copied = [torch.cuda.Event() for _ in range(nbuf)]
-    consumed = [torch.cuda.Event() for _ in range(nbuf)]
+    copied = [torch.cuda.Event() for _ in range(2)]
+    consumed = [torch.cuda.Event() for _ in range(2)]
     looked, counted_in = torch.cuda.Event(), torch.cuda.Event()
 
-    def issue_copy(t):
-        # batch t into staging buffer t % nbuf, once the insert of batch
-        # t - nbuf (whose sort read that buffer) is done with it
-        j = t % nbuf
+    ngroups = (nb + G4 - 1) // G4
+
+    def issue_group(g):
+        # batches 4g .. 4g + 3 into staging group g % 2 in one copy per array,
+        # once the inserts of group g - 2 (whose sorts read it) are done
+        j = g % 2
+        lo = g * G4 * b
+        n = min(G4 * b, nb * b - lo)
         with torch.cuda.stream(cs):
-            if t >= nbuf:
+            if g >= 2:
                 cs.wait_event(consumed[j])
-            buf[j][0].copy_(hk[t * b:(t + 1) * b], non_blocking=True)
-            buf[j][1].copy_(hv[t * b:(t + 1) * b], non_blocking=True)
+            gbuf[j][0][:n].copy_(hk[lo:lo + n], non_blocking=True)
+            gbuf[j][1][:n].copy_(hv[lo:lo + n], non_blocking=True)
             copied[j].record(cs)
 
     def step():
         G.lsm_reset(h)
         t0 = time.perf_counter()
-        # the copies run nbuf - 1 batches ahead of the inserts (an insert call
-        # returns once its batch is sorted, so a copy issued just before its
-        # insert would not overlap anything)
-        for t in range(min(nbuf - 1, nb)):
-            issue_copy(t)
-        for t in range(nb):
-            j = t % nbuf
-            if t + nbuf - 1 < nb:
-                issue_copy(t + nbuf - 1)
+        # the copies run a group (four batches) ahead of the inserts, a few
+        # host calls per four batches: with the default key check an insert
+        # call returns once its batch is sorted, so host work between two
+        # inserts leaves the device waiting
+        issue_group(0)
+        for g in range(ngroups):
+            j = g % 2
+            if g + 1 < ngroups:
+                issue_group(g + 1)
             st.wait_event(copied[j])
-            G.lsm_insert_batch(h, buf[j][0].data_ptr(), buf[j][1].data_ptr(), b, sp)
+            for u in range(min(G4, nb - g * G4)):
+                G.lsm_insert_batch(h, gbuf[j][0].data_ptr() + 4 * u * b, gbuf[j][1].data_ptr() + 4 * u * b, b, sp)
             consumed[j].record(st)
         torch.cuda.synchronize(dev)
         t1 = time.perf_counter()
@@ -603,7 +608,7 @@ def run_e2e(args, G, h, torch, dev, keys, vals, q, c1, c2, r1, r2, world):
             "lookup_and_count_M_per_s": world * K * (len(q) + len(c1)) / look_s / 1e6,
             "ms_per_step": 1000.0 * sum(r[2] for r in res) / K, "steps": K,
             "note": "wall clock on the host around each phase; update batches copied from pinned memory on a "
-                    "second stream, up to three batches ahead of the inserts, into four staging buffers"}
+                    "second stream, four batches per copy, one group ahead of the inserts, into two staging groups"}
 
 
 # ----------------------------------------------------------- batched form --
