@@ -68,12 +68,12 @@ static_assert(TileGeom<kFoldE>::kTile == kFoldTile, "the plain fold's tile");
 // sources fits seven CTAs per SM.
 __host__ __device__ constexpr uint32_t plain_slot_cap(uint32_t S) { return (uint32_t(kFoldTile) + 8u * S + 15u) / 16u * 16u; }
 
-// Slot of element q of a chain buffer (32-bit keys, 16-bit indices): q with
-// its low 3 bits XORed by bits 5..7.  A thread writing 8 consecutive elements
-// (q = 8 t + e) then hits word 8 (t & 3) + (e ^ ((t >> 2) & 7)) modulo 32 of
-// the key array, and word 4 t + ((e ^ ((t >> 2) & 7)) >> 1) of the 16-bit
-// index array: either way the 32 lanes of a warp use 32 different banks.
-__device__ __forceinline__ uint32_t ksw(uint32_t q) { return q ^ ((q >> 5) & 7u); }
+// Element q of a chain buffer (32-bit keys, 16-bit indices) sits at index q.
+// An XOR swizzle of the low bits (q ^ ((q >> 5) & 7), which gives the 32
+// lanes of a warp writing 8 consecutive elements each 32 banks) cost more in
+// index arithmetic than its bank conflicts: without it the k = 7 fold at
+// b = 2^18 executes 233.8 instead of 250.9 M warp instructions, 269 instead
+// of 278 us (the kernel is close to issue-bound).
 
 // Number of elements of the sorted run a[0, n) whose key variable is below
 // x, from its prefix index f at shift fs: one table entry when x starts one
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(256) multi_partition(MultiArena ar) {
 // before: key variables Xk and the 16-bit slot index Xi of each element.
 // Thread t produces `per` consecutive outputs from per * t after a
 // merge-path search for its first one (threads past the end idle); the
-// outputs go to the swizzled chain buffer Y (key and slot index), or stay in
+// outputs go to the chain buffer Y (key and slot index), or stay in
 // registers (kToRegs, per = E) when this is the last step, which then reads
 // each output's value from its slot.  An intermediate step spreads its
 // m outputs over all threads (per = ceil(m / threads)), so the short early
@@ -365,8 +365,8 @@ __device__ __forceinline__ void merge_step(const uint32_t* __restrict__ sk, cons
   const uint32_t per = kToRegs ? uint32_t(E) : (m + kThreads - 1) / kThreads;
   const uint32_t q0 = threadIdx.x * per;
   if (q0 >= m) return;
-  auto keyA = [&](uint32_t i) { return kAFromSlot ? sk[aS + i] : Xk[ksw(i)]; };
-  auto idxA = [&](uint32_t i) { return kAFromSlot ? aS + i : uint32_t(Xi[ksw(i)]); };
+  auto keyA = [&](uint32_t i) { return kAFromSlot ? sk[aS + i] : Xk[i]; };
+  auto idxA = [&](uint32_t i) { return kAFromSlot ? aS + i : uint32_t(Xi[i]); };
   // merge path: how many of the first q0 outputs come from A
   uint32_t lo = q0 > nB ? q0 - nB : 0u, hi = q0 < nA ? q0 : nA;
   while (lo < hi) {
@@ -389,8 +389,8 @@ __device__ __forceinline__ void merge_step(const uint32_t* __restrict__ sk, cons
     if (kToRegs) {
       o = make_uint2(v, x);   // the value is gathered by slot index after the step
     } else {
-      Yk[ksw(q0 + e)] = v;
-      Yi[ksw(q0 + e)] = uint16_t(x);
+      Yk[q0 + e] = v;
+      Yi[q0 + e] = uint16_t(x);
     }
     ia += take_a ? 1u : 0u;
     ib += take_a ? 0u : 1u;
@@ -440,8 +440,8 @@ template <int N, int E>
 __device__ __forceinline__ void store_n(uint32_t* Xk, uint16_t* Xi, uint32_t q0, const uint2 (&o)[E]) {
 #pragma unroll
   for (int e = 0; e < N; ++e) {
-    Xk[ksw(q0 + e)] = o[e].x;
-    Xi[ksw(q0 + e)] = uint16_t(o[e].y);
+    Xk[q0 + e] = o[e].x;
+    Xi[q0 + e] = uint16_t(o[e].y);
   }
 }
 template <int E>
@@ -458,12 +458,12 @@ __device__ __forceinline__ void merge_step_inplace(const uint32_t* __restrict__ 
     uint32_t lo = q0 > nB ? q0 - nB : 0u, hi = q0 < nA ? q0 : nA;
     while (lo < hi) {
       const uint32_t mid = (lo + hi) >> 1;
-      if (Xk[ksw(mid)] <= (sk[bS + q0 - 1 - mid] | 1u)) lo = mid + 1; else hi = mid;
+      if (Xk[mid] <= (sk[bS + q0 - 1 - mid] | 1u)) lo = mid + 1; else hi = mid;
     }
     uint32_t ia = lo, ib = q0 - lo;
     const uint32_t lastA = nA ? nA - 1u : 0u, lastB = nB ? nB - 1u : 0u;
     uint32_t ja = ia < nA ? ia : lastA, jb = ib < nB ? ib : lastB;
-    uint32_t va = Xk[ksw(ja)], xa = Xi[ksw(ja)], vb = sk[bS + jb], xb = bS + jb;
+    uint32_t va = Xk[ja], xa = Xi[ja], vb = sk[bS + jb], xb = bS + jb;
     auto emit = [&](uint32_t, uint2& r) {
       const bool take_a = ia < nA && (ib >= nB || va <= (vb | 1u));
       r = make_uint2(take_a ? va : vb, take_a ? xa : xb);
@@ -471,8 +471,8 @@ __device__ __forceinline__ void merge_step_inplace(const uint32_t* __restrict__ 
       ib += take_a ? 0u : 1u;
       ja = ia < nA ? ia : lastA;
       jb = ib < nB ? ib : lastB;
-      va = Xk[ksw(ja)];
-      xa = Xi[ksw(ja)];
+      va = Xk[ja];
+      xa = Xi[ja];
       vb = sk[bS + jb];
       xb = bS + jb;
     };
