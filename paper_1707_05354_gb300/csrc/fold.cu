@@ -58,8 +58,11 @@ struct TileGeom {
   static constexpr uint32_t kSlotCap = (kTile + 8 * kMaxSources + 15) / 16 * 16;  // TMA slots + slack
   // a chain buffer: kTile keys (u32) + kTile slot indices (u16)
   static constexpr size_t kChainBytes = size_t(kTile) * (sizeof(uint32_t) + sizeof(uint16_t));
-  static constexpr size_t kSmem = 2 * size_t(kSlotCap) * sizeof(uint32_t) + 2 * kChainBytes;
+  static constexpr size_t kSmem = 2 * size_t(kSlotCap) * sizeof(uint32_t) + 2 * kChainBytes + 16;  // + kChainPad
 };
+// Bytes after the last chain buffer: a merge cursor one past a full tile's
+// chain reads its 16-bit index there.
+constexpr size_t kChainPad = 16;
 constexpr int kFoldE = kFoldTile / kThreads;  // outputs per thread of the plain fold
 static_assert(TileGeom<kFoldE>::kTile == kFoldTile, "the plain fold's tile");
 // Slots of a plain-fold tile of S sources: the tile plus up to 8 elements a
@@ -374,13 +377,13 @@ __device__ __forceinline__ void merge_step(const uint32_t* __restrict__ sk, cons
     if (keyA(mid) <= (sk[bS + q0 - 1 - mid] | 1u)) lo = mid + 1; else hi = mid;
   }
   // Branch-free walk: after every output both heads are reloaded from their
-  // cursors clamped to the runs' last elements, and a run past its end is
-  // never taken.  A data-dependent branch on which run advanced would make
-  // every warp execute both sides (a warp's lanes take either).
+  // cursors, and a run past its end is never taken.  A cursor at most one past
+  // its run's end reads a word that is garbage but in bounds: the slots hold
+  // the windows' slack, the values follow the keys, and the launch adds
+  // kChainPad bytes after the last chain buffer.  A data-dependent branch on
+  // which run advanced would make every warp execute both sides.
   uint32_t ia = lo, ib = q0 - lo;
-  const uint32_t lastA = nA ? nA - 1u : 0u, lastB = nB ? nB - 1u : 0u;
-  uint32_t ja = ia < nA ? ia : lastA, jb = ib < nB ? ib : lastB;
-  uint32_t va = keyA(ja), xa = idxA(ja), vb = sk[bS + jb], xb = bS + jb;   // key variable, slot index
+  uint32_t va = keyA(ia), xa = idxA(ia), vb = sk[bS + ib], xb = bS + ib;   // key variable, slot index
   // one output: the smaller head (the newer run's on equal keys), then both
   // heads reloaded
   auto emit = [&](uint32_t e, uint2& o) {
@@ -394,12 +397,10 @@ __device__ __forceinline__ void merge_step(const uint32_t* __restrict__ sk, cons
     }
     ia += take_a ? 1u : 0u;
     ib += take_a ? 0u : 1u;
-    ja = ia < nA ? ia : lastA;
-    jb = ib < nB ? ib : lastB;
-    va = keyA(ja);
-    xa = idxA(ja);
-    vb = sk[bS + jb];
-    xb = bS + jb;
+    va = keyA(ia);
+    xa = idxA(ia);
+    vb = sk[bS + ib];
+    xb = bS + ib;
   };
   if (kToRegs) {
 #pragma unroll
@@ -465,20 +466,16 @@ __device__ __forceinline__ void merge_step_inplace(const uint32_t* __restrict__ 
       if (Xk[mid] <= (sk[bS + q0 - 1 - mid] | 1u)) lo = mid + 1; else hi = mid;
     }
     uint32_t ia = lo, ib = q0 - lo;
-    const uint32_t lastA = nA ? nA - 1u : 0u, lastB = nB ? nB - 1u : 0u;
-    uint32_t ja = ia < nA ? ia : lastA, jb = ib < nB ? ib : lastB;
-    uint32_t va = Xk[ja], xa = Xi[ja], vb = sk[bS + jb], xb = bS + jb;
+    uint32_t va = Xk[ia], xa = Xi[ia], vb = sk[bS + ib], xb = bS + ib;
     auto emit = [&](uint32_t, uint2& r) {
       const bool take_a = ia < nA && (ib >= nB || va <= (vb | 1u));
       r = make_uint2(take_a ? va : vb, take_a ? xa : xb);
       ia += take_a ? 1u : 0u;
       ib += take_a ? 0u : 1u;
-      ja = ia < nA ? ia : lastA;
-      jb = ib < nB ? ib : lastB;
-      va = Xk[ja];
-      xa = Xi[ja];
-      vb = sk[bS + jb];
-      xb = bS + jb;
+      va = Xk[ia];
+      xa = Xi[ia];
+      vb = sk[bS + ib];
+      xb = bS + ib;
     };
     switch (cnt) {
       case 1: emit_n<1, E>(emit, o); break;
@@ -1054,7 +1051,7 @@ cudaError_t fold_merge_launch(const FoldArgs& a, cudaStream_t st) {
   // sources): more CTAs fit per SM for the small folds
   using G = TileGeom<kFoldE>;
   const int S = a.src.count;
-  const size_t smem = 2 * size_t(plain_slot_cap(uint32_t(S))) * sizeof(uint32_t) + (S >= 3 ? G::kChainBytes : 0);
+  const size_t smem = 2 * size_t(plain_slot_cap(uint32_t(S))) * sizeof(uint32_t) + (S >= 3 ? G::kChainBytes + kChainPad : 0);
   const uint64_t ntiles = fold_tiles(a.total);
   if (a.cleanup) {
     if ((e = cudaMemsetAsync(a.out_count, 0, sizeof(uint64_t), st)) != cudaSuccess) return e;
