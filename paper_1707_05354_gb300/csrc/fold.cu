@@ -403,9 +403,14 @@ __device__ __forceinline__ void merge_step(const uint32_t* __restrict__ sk, cons
     xb = bS + ib;
   };
   if (kToRegs) {
+    if (q0 + E <= m) {  // a full thread (all but the ragged end of the last tile): no guards
 #pragma unroll
-    for (int e = 0; e < E; ++e)
-      if (q0 + e < m) emit(uint32_t(e), out[e]);
+      for (int e = 0; e < E; ++e) emit(uint32_t(e), out[e]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (q0 + e < m) emit(uint32_t(e), out[e]);
+    }
   } else {
     // an intermediate step has per <= E outputs per thread, most often one
     // or two: a loop over exactly those (an unrolled loop over E guarded
@@ -417,9 +422,14 @@ __device__ __forceinline__ void merge_step(const uint32_t* __restrict__ sk, cons
     for (uint32_t e = 0; e < cnt; ++e) emit(e, unused);
   }
   if (kToRegs) {
+    if (q0 + E <= m) {
 #pragma unroll
-    for (int e = 0; e < E; ++e)
-      if (q0 + e < m) out[e].y = sv[out[e].y];
+      for (int e = 0; e < E; ++e) out[e].y = sv[out[e].y];
+    } else {
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (q0 + e < m) out[e].y = sv[out[e].y];
+    }
   }
 }
 
@@ -736,6 +746,7 @@ __device__ __forceinline__ bool merge_tile(const FoldSources& src, uint64_t tota
       // gaps afterwards.
       const uint32_t nb = fence_bins(fshift);
       const uint32_t pb0 = has_prev ? fence_bin(prev_kv, fshift) : 0u;
+      const bool level_start = obase + q0 == 0;  // this thread holds the level's first element
       uint32_t pb = pb0;
       bool wide = false;
 #pragma unroll
@@ -743,7 +754,7 @@ __device__ __forceinline__ bool merge_tile(const FoldSources& src, uint64_t tota
         if (uint32_t(e) < cnt) {
           const uint32_t bin = fence_bin(out[e].x, fshift);
           const uint32_t pos = uint32_t(obase) + q0 + uint32_t(e);
-          const bool first = obase + q0 + e == 0;
+          const bool first = e == 0 && level_start;
           if (first) out_fence[nb + 2] = bin;
           if (!first && bin > pb) {
             out_fence[pb + 1] = pos;
