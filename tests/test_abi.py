@@ -159,3 +159,22 @@ def test_header_is_plain_c_and_links(lsm_lib, tmp_path):
                     str(cpp)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert out.returncode == 0 and out.stdout.strip() == "ok", (out.returncode, out.stdout, out.stderr)
+
+
+def test_profile_codes(lsm_lib, monkeypatch):
+    """lsm_profile: 0 off, 1 every group, 2 + g group g alone; the binding
+    maps a group's name to its code (the library checks the handle first)."""
+    assert lsm_lib._lib.lsm_profile(None, 1) == lsm_lib.LSM_ERR_ARG
+    seen = []
+
+    class Fake:
+        def lsm_profile(self, h, code):
+            seen.append(code)
+            return 0
+
+    monkeypatch.setattr(lsm_lib, "_lib", Fake())
+    for arg in (True, False, "merge", "sort", "cleanup"):
+        lsm_lib.lsm_profile(None, arg)
+    g = lsm_lib.PROF_GROUPS
+    assert seen == [1, 0, 2 + g.index("merge"), 2 + g.index("sort"), 2 + g.index("cleanup")]
+    assert g.index("merge") == 2 and len(g) == 7   # the header's lsm_prof_group order
